@@ -1,0 +1,351 @@
+"""Benchmark: Wiener-filter solve time to a certified 1e-6 residual on GB300.
+
+Workload (default): the multi-resolution full-sky model -- Ncomp = 3 (CMB L 2000,
+synchrotron beta -3.0 L 500, dust beta 1.6 L 3000), Nobs = 9 HEALPix bands at Nside
+256/512/1024 (L_nu = 3 Nside - 1), Gaussian beams 33' -> 5', noise rms varying x3 over
+the sky -- with seeded synthetic inputs (skygen).  One step is one Wiener filter from the
+band maps d: b = P^T N^-1 d (cmbws_rhs), then PCG with M_PI (cmbws_cg_solve) until
+||b - A x|| / ||b|| <= 1e-6, certified by an FP64 apply of A.  The default arithmetic is
+FP32 transforms with FP64 vectors, scalars and iterative refinement; --prec fp64 runs the
+plain FP64 solver.  One plain FP64 solve is also timed once and reported as fp64_plain.
+
+Timing: W untimed warm-up steps, then K steps bracketed by a barrier and a device
+synchronise on both sides, CUDA events on the launching stream, max over ranks.  Inputs
+(band maps 0.4 GB, vectors 0.1 GB each, tables) exceed the 129 MB L2, so no flush is done.
+The library's kernel-timing records (CUDA events on the launching stream) give the per-stage
+time and the roofline of the dominant kernel.  --gpus N runs N independent replicas (one
+per rank) and reports the max time over ranks; there is no data-path collective.
+
+--impl reference times the FP64 NumPy oracle on the host on a bounded sample (one SHT
+pair of the Nside-256 band grid) and scales it to the same solve.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import skygen  # noqa: E402
+
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # FP32 FMA lanes x 2 flops x max SM clock
+FP64_PEAK_TFLOPS = 1.25                               # GB300 FP64 (profiling recipe, nominal)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--scale", type=int, default=1, help="divide Nside and band-limits (debug)")
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--no-fp64-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def workload(scale):
+    return skygen.multires_fullsky(scale=scale)
+
+
+def dist_init(n):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def build_problem(work, prec, seed_offset=0):
+    """Library grids, seeded inputs, model and band maps d = P x_true + n on the device."""
+    import torch
+    import paper_1710_00621_gb300 as cw
+    grids = {}
+    band_grids = []
+    for b in work.bands:
+        key = (b.grid, b.n, b.lmax)
+        if key not in grids:
+            kind = cw.CMBWS_GRID_GL if b.grid == "gl" else cw.CMBWS_GRID_HEALPIX
+            grids[key] = cw.cmbws_plan_grid(kind, b.n + 1 if b.grid == "gl" else b.n, b.lmax)
+        band_grids.append(grids[key])
+    coords = [g.pixel_coords() for g in band_grids]
+    weights = [g.pixel_weights() for g in band_grids]
+    work.seed += seed_offset
+    inp = skygen.make_inputs(work, coords, weights)
+    dev = torch.device("cuda")
+    ninv = [torch.as_tensor(t, device=dev) for t in inp["tau"]]
+    lk = [c.lmax for c in work.comps]
+    m64 = cw.cmbws_model_create(lk, band_grids, inp["beams"], inp["cl"], ninv, inp["q"], cw.CMBWS_FP64)
+    m_run = m64 if prec == "fp64" else cw.cmbws_model_create(lk, band_grids, inp["beams"], inp["cl"],
+                                                              ninv, inp["q"], cw.CMBWS_FP32)
+    x_true = torch.as_tensor(inp["x_true"], device=dev)
+    d = [torch.empty(g.npix, dtype=torch.float64, device=dev) for g in band_grids]
+    cw.cmbws_project(m64, x_true, d)
+    for nu in range(len(d)):
+        d[nu] += torch.as_tensor(inp["noise"][nu], device=dev)
+    torch.cuda.synchronize()
+    return dict(grids=band_grids, inp=inp, m64=m64, model=m_run, d=d, x_true=x_true)
+
+
+def solve_step(P, model, tol, x, b):
+    import paper_1710_00621_gb300 as cw
+    cw.cmbws_rhs(model, P["d"], b)
+    x.zero_()
+    return cw.cmbws_cg_solve(model, b, x, tol=tol, maxiter=3000, precond=1, inner_tol=1e-3,
+                             max_outer=30)
+
+
+def roofline(prof):
+    """Dominant kernel (by summed time) among the Legendre stages, with its achieved rate."""
+    best = None
+    for (stage, prec), (ms, n, fl) in prof.items():
+        if stage not in ("legendre_synth", "legendre_adjoint") or n == 0:
+            continue
+        if best is None or ms > best[2]:
+            best = (stage, prec, ms, n, fl)
+    if best is None:
+        return None
+    stage, prec, ms, n, fl = best
+    achieved = fl / (ms * 1e-3) / 1e12
+    peak = FP32_PEAK_TFLOPS if prec == "fp32" else FP64_PEAK_TFLOPS
+    return {"bound": "alu", "kernel": f"{stage}_{prec}", "achieved": round(achieved, 3),
+            "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+            "traffic": None, "launches": n, "avg_launch_ms": round(ms / n, 4),
+            "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz"
+                            if prec == "fp32" else "profiling recipe nominal FP64")}
+
+
+def cpu_baseline(work, gpu_iters_fp64, sample_nside=256):
+    """Time the FP64 oracle on one SHT pair of one band grid and scale to the whole solve."""
+    from oracle import grids as og, sht as osht
+    nside = sample_nside // 1
+    L = 3 * nside - 1
+    g = og.healpix(nside)
+    a = np.random.default_rng(0).standard_normal((L + 1) ** 2)
+    t0 = time.perf_counter()
+    f = osht.synthesis(g, L, a)
+    osht.adjoint(g, L, f)
+    t_pair = time.perf_counter() - t0
+    unit_sample = (2 * nside) * (L + 1) * (L + 2) / 2          # ring pairs x (l, m) pairs
+    # one PCG iteration = A + M_PI = 2 SHT pairs per band
+    per_iter = 0.0
+    for b in work.bands:
+        npair = 2 * b.n
+        per_iter += 2 * npair * (b.lmax + 1) * (b.lmax + 2) / 2
+    iters = max(gpu_iters_fp64, 1) + 2                            # + RHS and certification
+    est = t_pair * per_iter * iters / unit_sample
+    return {"value": round(est, 1), "unit": "s", "cores": 1, "kind": "oracle",
+            "host_cpus": os.cpu_count(),
+            "sample": (f"one synthesis + adjoint-synthesis pair of the FP64 NumPy oracle on the "
+                       f"HEALPix Nside {nside} grid (L = {L}) took {t_pair:.2f} s; scaled by ring "
+                       f"pairs x (l, m) pairs to the {len(work.bands)} bands and to {iters} "
+                       f"iterations (the GPU FP64 solve's count + RHS + certification)")}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    work = workload(args.scale)
+    times = []
+    for _ in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        cb = cpu_baseline(work, 25)
+        times.append(cb["value"])
+    v = float(np.median(times[args.warmup:])) if args.steps else times[-1]
+    line = {"impl": "reference", "metric": "Wiener solve time to 1e-6 residual", "value": v,
+            "unit": "s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": work.name, "solve": "oracle PCG with M_PI (extrapolated)"},
+            "cpu_baseline": cb, "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0,
+                                         "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import paper_1710_00621_gb300 as cw
+    rank, world, local = dist_init(args.gpus)
+    work = workload(args.scale)
+    P = build_problem(work, args.prec, seed_offset=rank)
+    model = P["model"]
+    n = model.nvec
+    dev = torch.device("cuda")
+    x = torch.zeros(n, dtype=torch.float64, device=dev)
+    b = torch.zeros(n, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        solve_step(P, model, args.tol, x, b)
+    torch.cuda.synchronize()
+
+    # timed region
+    clocks = ClockSampler(local)
+    clocks.start()
+    cw.cmbws_profile_read(reset=True)
+    cw.cmbws_profile_enable(True)
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    reps = []
+    for _ in range(args.steps):
+        reps.append(solve_step(P, model, args.tol, x, b))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    cw.cmbws_profile_enable(False)
+    prof = cw.cmbws_profile_read(reset=True)
+    clk = clocks.stop()
+    t_step = ev0.elapsed_time(ev1) / 1e3 / max(args.steps, 1)
+    t_step = max_over_ranks(t_step, world)
+    launches = int(sum(v[1] for v in prof.values()))
+
+    # accuracy of the solution against the FP64 plain solve and x_true
+    rep = reps[-1]
+    out = {"iters": rep["iters"], "outer": rep["outer"], "rel_res_fp64": rep["rel_res"],
+           "n_sht": rep["n_sht"]}
+
+    # end to end through the public API from pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        d_host = [t.cpu().pin_memory() for t in P["d"]]
+        x_host = torch.empty(n, dtype=torch.float64).pin_memory()
+        d_dev = [torch.empty_like(t) for t in P["d"]]
+        Pe = dict(P)
+        Pe["d"] = d_dev
+        torch.cuda.synchronize()
+        barrier(world)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            for dd, hh in zip(d_dev, d_host):
+                dd.copy_(hh, non_blocking=True)
+            solve_step(Pe, model, args.tol, x, b)
+            x_host.copy_(x, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        te = max_over_ranks(e0.elapsed_time(e1) / 1e3 / max(args.steps, 1), world)
+        e2e = {"value": round(te, 4), "unit": "s",
+               "h2d_bytes_per_step": int(sum(t.numel() * 8 for t in P["d"])),
+               "d2h_bytes_per_step": int(n * 8)}
+
+    fp64 = None
+    if not args.no_fp64_plain and args.prec == "fp32":
+        m64 = P["m64"]
+        x64 = torch.zeros(n, dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r64 = solve_step(P, m64, args.tol, x64, b)
+        torch.cuda.synchronize()
+        t64 = time.perf_counter() - t0
+        diff = float(torch.linalg.vector_norm(x - x64) / torch.linalg.vector_norm(x64))
+        fp64 = {"s": round(t64, 3), "iters": r64["iters"], "rel_res_fp64": r64["rel_res"],
+                "mixed_vs_fp64_rel_diff": diff}
+        out["iters_fp64_plain"] = r64["iters"]
+
+    if rank != 0:
+        return
+    rl = roofline(prof)
+    cb = cpu_baseline(work, out.get("iters_fp64_plain", out["iters"])) if world == 1 else None
+    stages = {f"{k[0]}_{k[1]}": {"ms": round(v[0], 3), "launches": v[1]} for k, v in prof.items() if v[1]}
+    line = {"metric": "Wiener solve time to 1e-6 residual", "value": round(t_step, 4), "unit": "s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(t_step * 1e3, 2), "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64" if args.prec == "fp32" else "f64",
+            "data": "synthetic",
+            "config": {"workload": work.name, "ncomp": len(work.comps), "nobs": len(work.bands),
+                       "band_nside": [b.n for b in work.bands], "lmax_comp": [c.lmax for c in work.comps],
+                       "tol": args.tol, "precond": "M_PI",
+                       "arithmetic": ("FP32 transforms, FP64 vectors/scalars, FP64-certified "
+                                      "iterative refinement" if args.prec == "fp32" else "FP64"),
+                       "l2": "inputs larger than L2, no flush",
+                       "parallelism": f"replicas x{world}"},
+            "solve": out, "fp64_plain": fp64, "roofline": rl, "cpu_baseline": cb, "e2e": e2e,
+            "gpu_launches": launches, "stages": stages, "clocks": clk}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,224 @@
+/*
+ * cmbws -- GB300 (sm_103a) Wiener-filter / constrained-realization solver for
+ * multi-resolution CMB component separation with the pseudo-inverse
+ * preconditioner of Seljebotn, Baerland, Eriksen, Mardal & Wehus,
+ * "Multi-resolution Bayesian CMB component separation through
+ * Wiener-filtering with a pseudo-inverse preconditioner" (arXiv:1710.00621).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Status: every function returns an int, CMBWS_OK (0) on success or a
+ *   negative CMBWS_ERR_* code.  cmbws_last_error() returns a message for the
+ *   last failure on the calling host thread.  No C++ exception crosses this
+ *   boundary.  When a call fails, the contents of its output buffers are
+ *   unspecified.
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  Calls that take a stream enqueue their kernels on it and return
+ *   without synchronising, except where noted.  A grid or model object owns
+ *   workspace that every call on it reuses, so calls on one object must not
+ *   overlap in time (serialise them on one stream).
+ * Memory: buffers passed as `const double*` / `double*` data arguments are
+ *   DEVICE pointers on the current CUDA device, contiguous, FP64, owned by
+ *   the caller.  Pointers documented as host pointers are host memory.
+ * Harmonic layout (CMBWS_ALM): a field with band-limit L has (L+1)^2 real
+ *   coefficients of the real orthonormal basis
+ *       Y_l0 = lambda_l0(theta),
+ *       Y^c_lm = sqrt(2) lambda_lm(theta) cos(m phi),
+ *       Y^s_lm = sqrt(2) lambda_lm(theta) sin(m phi)   (m > 0),
+ *   lambda_lm the orthonormal associated Legendre function without the
+ *   Condon-Shortley phase; stored m-major: m = 0 (l = 0..L), then for each
+ *   m = 1..L the cos block (l = m..L) followed by the sin block (l = m..L).
+ *   (L+1)^2 matches the paper's count of columns of U per component (Sec. 3.3).
+ * Pixel layout: rings north to south, pixels of a ring in increasing azimuth
+ *   phi_j = phi0_r + 2 pi j / nphi_r.
+ * Stacked component vectors (x, b, r, z of the solver) hold the components
+ *   k = 0..Ncomp-1 one after the other, each in CMBWS_ALM order with its own
+ *   band-limit L_k (Sec. 2.2: s_lm = 0 for l > L_k).
+ */
+#ifndef CMBWS_H
+#define CMBWS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  CMBWS_OK = 0,
+  CMBWS_ERR_ARG = -1,           /* invalid argument or unsupported size */
+  CMBWS_ERR_CUDA = -2,          /* a CUDA runtime call failed */
+  CMBWS_ERR_NOMEM = -3,         /* device or host allocation failed */
+  CMBWS_ERR_SINGULAR = -4,      /* a U block has a column with zero norm */
+  CMBWS_ERR_BREAKDOWN = -5,     /* CG: p.Ap <= 0 or a non-finite scalar */
+  CMBWS_ERR_NOT_CONVERGED = -6, /* CG: iteration cap reached (x holds the last iterate) */
+  CMBWS_ERR_TIMEOUT = -7        /* wall-clock budget of a solve exhausted */
+};
+
+typedef enum { CMBWS_GRID_GL = 0, CMBWS_GRID_HEALPIX = 1 } cmbws_grid_kind;
+
+/* Arithmetic of the transform stages (Legendre recurrence and contraction,
+ * ring FFTs, pixel multiplies).  Vectors at the boundary and CG scalars are
+ * always FP64. */
+typedef enum { CMBWS_FP64 = 0, CMBWS_FP32 = 1 } cmbws_prec;
+
+typedef struct cmbws_grid_s* cmbws_grid;    /* opaque, library-owned */
+typedef struct cmbws_model_s* cmbws_model;  /* opaque, library-owned */
+
+/* Message for the last failing call on this host thread ("" if none). */
+const char* cmbws_last_error(void);
+/* Library version string. */
+const char* cmbws_version(void);
+
+/*
+ * Plan a ring grid and its transform tables on the current CUDA device
+ * (Sec. 2.1: Y, Y^T W and Y^T are defined per grid).
+ *   kind = CMBWS_GRID_GL:      n = lmax + 1 rings at the Gauss-Legendre nodes,
+ *                              2 lmax + 1 pixels per ring, phi0 = 0, weights
+ *                              g_r * 2 pi / nphi (Y^T W Y = I exactly, Sec. 2.1).
+ *   kind = CMBWS_GRID_HEALPIX: n = Nside; 4 Nside - 1 rings of the HEALPix ring
+ *                              scheme, uniform weights 4 pi / Npix (Sec. 3.2,
+ *                              App. A.1 accept Y^T W Y ~ I there).
+ *   lmax: band-limit of the transforms on this grid (>= 0).
+ * Limits: FP64 transforms need every ring length n <= 4096 after padding
+ *   (ring FFTs run in shared memory); FP32 n <= 8192.  Larger grids return
+ *   CMBWS_ERR_ARG from the transform calls of the precision they exceed.
+ * Synchronises the device.  *out is released with cmbws_grid_destroy.
+ */
+int cmbws_plan_grid(cmbws_grid_kind kind, int n, int lmax, cmbws_grid* out);
+
+/* Host pointers into the grid (valid until destroy): ring colatitudes theta[nring],
+ * per-pixel quadrature weight of each ring weight[nring]. */
+int cmbws_grid_info(cmbws_grid g, int64_t* npix, int* nring, const double** theta,
+                    const double** weight);
+/* Host pointers: first-pixel azimuth phi0[nring], pixels per ring nphi[nring],
+ * first pixel of each ring offset[nring + 1]; and the band-limit. */
+int cmbws_grid_rings(cmbws_grid g, const double** phi0, const int** nphi,
+                     const int64_t** offset, int* lmax);
+int cmbws_grid_destroy(cmbws_grid g);
+
+/*
+ * Spherical harmonic synthesis map = Y alm (Sec. 2.1).
+ *   alm: device, nmaps x (lmax+1)^2 FP64, CMBWS_ALM order, map after map.
+ *   map: device, nmaps x npix FP64, written.
+ */
+int cmbws_sht_synth(cmbws_grid g, cmbws_prec prec, const double* alm, double* map, int nmaps,
+                    void* stream);
+/*
+ * weighted = 1: analysis alm = Y^T W map (Sec. 2.1);
+ * weighted = 0: adjoint synthesis alm = Y^T map (Sec. 3.2).
+ *   map: device, nmaps x npix FP64.  alm: device, nmaps x (lmax+1)^2 FP64, written.
+ */
+int cmbws_sht_analysis(cmbws_grid g, cmbws_prec prec, const double* map, double* alm, int nmaps,
+                       int weighted, void* stream);
+
+/*
+ * Model description (Sec. 2.2, Eqs. block-data-model, P, Q; Sec. 2.3, Eq. A).
+ * All pointers are host pointers except ninv[nu], which are device pointers.
+ * The library copies everything it keeps; the caller may free the inputs
+ * after cmbws_model_create returns.
+ */
+typedef struct {
+  int ncomp;                     /* Ncomp >= 1 */
+  int nobs;                      /* Nobs >= 1 */
+  const int* lmax_comp;          /* [ncomp] L_k */
+  const cmbws_grid* band_grid;   /* [nobs] grid of d_nu; L_nu = that grid's lmax. Bands
+                                    sharing a grid handle are transformed together. */
+  const double* const* beam;     /* [nobs] host arrays b_{nu,l}, l = 0..L_nu (B_nu) */
+  const double* const* cl;       /* [ncomp] host arrays C_{k,l}, l = 0..L_k, or NULL for no
+                                    prior; a non-finite or non-positive entry means
+                                    C^-1 = 0 at that l (Sec. 3.3) */
+  const double* const* ninv;     /* [nobs] device maps tau_nu = diag(N_nu^-1), npix_nu, > 0 */
+  const double* mix_scalar;      /* [nobs * ncomp] q_{nu,k}, row nu (spatially constant
+                                    mixing, Q~ = q I) */
+} cmbws_model_desc;
+
+/*
+ * Build a model: copies tau, computes alpha_nu (Eq. optimal-alpha), the per-l
+ * blocks of U (Eqs. U-data, U-prior) and U^+ (Sec. 3.1, pseudo-inverse with a
+ * singular-value cut-off of 1e-12 relative), and the pixel factors of A
+ * (tau) and of T^+ (alpha^2 w^2 / tau, Sec. 3.3).  `prec` selects the
+ * arithmetic of the transform stages of cmbws_apply_A / cmbws_apply_precond.
+ * Synchronises `stream`.
+ * Errors: CMBWS_ERR_SINGULAR if, at some l <= L_k, component k has neither
+ * data nor a prior (a zero column of U).
+ */
+int cmbws_model_create(const cmbws_model_desc* desc, cmbws_prec prec, void* stream,
+                       cmbws_model* out);
+int cmbws_model_destroy(cmbws_model m);
+
+/* Length of a stacked component vector, sum_k (L_k+1)^2; SHTs per apply of A and of
+ * M_PI as the paper counts them (Sec. 3.3: 2(2 Nmix + Nobs) and 2 Nobs). */
+int cmbws_model_info(cmbws_model m, int64_t* nvec, int* nsht_A, int* nsht_M);
+
+/* y = A x = S^-1 x + P^T N^-1 P x (Eq. A).  x, y: device stacked vectors, distinct. */
+int cmbws_apply_A(cmbws_model m, const double* x, double* y, void* stream);
+
+/* z = M_PI r = U^+ T^+ (U^+)^T r (Eq. fullmodel-preconditioner).  r, z distinct. */
+int cmbws_apply_precond(cmbws_model m, const double* r, double* z, void* stream);
+
+/*
+ * b = P^T N^-1 d + P^T N^-1/2 omega1 + S^-1/2 omega2 (Sec. 2.3; the printed S^-1 omega2
+ * is read as S^-1/2 omega2, for which Var(b) = A).
+ *   d, omega1: host arrays [nobs] of device maps (npix_nu FP64); omega1 may be NULL.
+ *   omega2: device stacked vector or NULL.  b: device stacked vector, written.
+ */
+int cmbws_rhs(cmbws_model m, const double* const* d, const double* const* omega1,
+              const double* omega2, double* b, void* stream);
+
+/*
+ * Data-model projection d_nu = P_nu x = Y_nu B_nu sum_k Q~_{nu,k} x_k (Eq. P), e.g. to
+ * simulate d = P s + n (Eq. block-data-model).
+ *   x: device stacked vector.  d: host array [nobs] of device maps (npix_nu FP64), written.
+ * Uses the model's transform precision.
+ */
+int cmbws_project(cmbws_model m, const double* x, double* const* d, void* stream);
+
+/*
+ * Kernel timing.  While enabled, the library brackets each of its kernel launches with
+ * CUDA events on the launching stream.  Records are kept per slot = stage + 6 * fp64,
+ * stages 0 Legendre synthesis, 1 Legendre adjoint, 2 adjoint partial-sum reduction,
+ * 3 ring FFT, 4 harmonic-space kernels, 5 CG vector kernels; fp64 = 1 for launches in
+ * FP64 arithmetic.  cmbws_profile_read synchronises the recorded events and writes, per
+ * slot (host arrays of 12, any may be NULL), the summed milliseconds, the launch count
+ * and the summed algorithmic flops (Legendre stages: 4 flops per (l, m, ring pair) for
+ * the recurrence plus 4 per map for the contraction, over the full (l, m) triangle;
+ * 0 elsewhere) since the last reset; reset = 1 clears the record.
+ */
+int cmbws_profile_enable(int on);
+int cmbws_profile_read(double* ms, int64_t* launches, double* flops, int reset);
+
+typedef struct {
+  double tol;         /* stop when ||b - A x||_2 / ||b||_2 <= tol, certified by an FP64 apply */
+  int maxiter;        /* cap on CG iterations (all inner iterations counted) */
+  int precond;        /* 0 = none, 1 = M_PI */
+  double inner_tol;   /* FP32 models: relative reduction per refinement pass (e.g. 1e-3) */
+  int max_outer;      /* FP32 models: cap on refinement passes */
+  double timeout_s;   /* wall-clock budget, <= 0 for none */
+} cmbws_cg_opts;
+
+typedef struct {
+  int status;         /* CMBWS_OK or the error returned */
+  int iters;          /* CG iterations (sum over refinement passes) */
+  int outer;          /* refinement passes (1 for FP64 models) */
+  double rel_res;     /* certified ||b - A x|| / ||b|| with A in FP64 */
+  int n_sht;          /* SHTs executed, counted as the paper counts them */
+  double ms;          /* wall time of the solve on the host clock */
+} cmbws_cg_report;
+
+/*
+ * Solve A x = b by preconditioned CG (Sec. 2.3) with M_PI (Sec. 3.3).
+ *   b: device stacked vector.  x: device stacked vector; in: initial guess, out: solution.
+ * FP64 models run plain PCG in FP64 and certify the final residual with one FP64 apply.
+ * FP32 models run iterative refinement: each pass solves A d = r with FP32 transforms
+ * (FP64 vectors and scalars) to a relative reduction inner_tol, then x += d and
+ * r = b - A x with FP64 transforms, until r certifies tol.
+ * Synchronises `stream` (the host reads one scalar per iteration).  `report` may be NULL.
+ */
+int cmbws_cg_solve(cmbws_model m, const double* b, double* x, const cmbws_cg_opts* opts,
+                   cmbws_cg_report* report, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CMBWS_H */

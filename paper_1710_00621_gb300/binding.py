@@ -1,0 +1,343 @@
+"""ctypes binding of libcmbws (argument marshalling only; every step runs in the library).
+
+Tensors passed as vectors or maps must be CUDA, float64 and contiguous; the library
+reads and writes them in place on the given stream (default: torch's current stream).
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+LIB_PATH = os.path.join(HERE, "libcmbws.so")
+HEADER = os.path.join(ROOT, "include", "cmbws.h")
+
+CMBWS_GRID_GL = 0
+CMBWS_GRID_HEALPIX = 1
+CMBWS_FP64 = 0
+CMBWS_FP32 = 1
+
+_ERRORS = {-1: "CMBWS_ERR_ARG", -2: "CMBWS_ERR_CUDA", -3: "CMBWS_ERR_NOMEM",
+           -4: "CMBWS_ERR_SINGULAR", -5: "CMBWS_ERR_BREAKDOWN", -6: "CMBWS_ERR_NOT_CONVERGED",
+           -7: "CMBWS_ERR_TIMEOUT"}
+
+_lib = None
+
+
+class CmbwsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class ModelDesc(ctypes.Structure):
+    _fields_ = [("ncomp", ctypes.c_int), ("nobs", ctypes.c_int),
+                ("lmax_comp", ctypes.POINTER(ctypes.c_int)),
+                ("band_grid", ctypes.POINTER(ctypes.c_void_p)),
+                ("beam", ctypes.POINTER(ctypes.POINTER(ctypes.c_double))),
+                ("cl", ctypes.POINTER(ctypes.POINTER(ctypes.c_double))),
+                ("ninv", ctypes.POINTER(ctypes.c_void_p)),
+                ("mix_scalar", ctypes.POINTER(ctypes.c_double))]
+
+
+class CgOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("maxiter", ctypes.c_int), ("precond", ctypes.c_int),
+                ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int),
+                ("timeout_s", ctypes.c_double)]
+
+
+class CgReport(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("outer", ctypes.c_int),
+                ("rel_res", ctypes.c_double), ("n_sht", ctypes.c_int), ("ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+def library_path():
+    return LIB_PATH
+
+
+def load_library(path=None):
+    """Load libcmbws.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"libcmbws.so not found at {p}; run __graft_entry__.build() first")
+    lib = ctypes.CDLL(p)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    lib.cmbws_last_error.restype = ctypes.c_char_p
+    lib.cmbws_version.restype = ctypes.c_char_p
+    lib.cmbws_plan_grid.argtypes = [i, i, i, ctypes.POINTER(vp)]
+    lib.cmbws_grid_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(i),
+                                    ctypes.POINTER(ctypes.POINTER(d)), ctypes.POINTER(ctypes.POINTER(d))]
+    lib.cmbws_grid_rings.argtypes = [vp, ctypes.POINTER(ctypes.POINTER(d)),
+                                     ctypes.POINTER(ctypes.POINTER(i)),
+                                     ctypes.POINTER(ctypes.POINTER(ctypes.c_int64)), ctypes.POINTER(i)]
+    lib.cmbws_grid_destroy.argtypes = [vp]
+    lib.cmbws_sht_synth.argtypes = [vp, i, vp, vp, i, vp]
+    lib.cmbws_sht_analysis.argtypes = [vp, i, vp, vp, i, i, vp]
+    lib.cmbws_model_create.argtypes = [ctypes.POINTER(ModelDesc), i, vp, ctypes.POINTER(vp)]
+    lib.cmbws_model_destroy.argtypes = [vp]
+    lib.cmbws_model_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(i),
+                                     ctypes.POINTER(i)]
+    lib.cmbws_apply_A.argtypes = [vp, vp, vp, vp]
+    lib.cmbws_apply_precond.argtypes = [vp, vp, vp, vp]
+    lib.cmbws_rhs.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp, vp, vp]
+    lib.cmbws_project.argtypes = [vp, vp, ctypes.POINTER(vp), vp]
+    lib.cmbws_profile_enable.argtypes = [i]
+    lib.cmbws_profile_read.argtypes = [ctypes.POINTER(d), ctypes.POINTER(ctypes.c_int64),
+                                       ctypes.POINTER(d), i]
+    lib.cmbws_cg_solve.argtypes = [vp, vp, vp, ctypes.POINTER(CgOpts), ctypes.POINTER(CgReport), vp]
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    """Names of the functions declared in include/cmbws.h."""
+    src = open(HEADER).read()
+    return sorted(set(re.findall(r"\b(cmbws_[A-Za-z_0-9]+)\s*\(", src)))
+
+
+def _check(code):
+    if code != 0:
+        raise CmbwsError(code, load_library().cmbws_last_error().decode())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _dptr(t, n=None, name="tensor"):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA float64 tensor")
+    if n is not None and t.numel() < n:
+        raise ValueError(f"{name} has {t.numel()} elements, needs {n}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Grid:
+    """A planned ring grid (owns the library handle)."""
+
+    def __init__(self, handle, kind, n, lmax):
+        self.handle = handle
+        self.kind, self.n, self.lmax = kind, n, lmax
+        npix = ctypes.c_int64()
+        nring = ctypes.c_int()
+        th = ctypes.POINTER(ctypes.c_double)()
+        w = ctypes.POINTER(ctypes.c_double)()
+        _check(load_library().cmbws_grid_info(handle, ctypes.byref(npix), ctypes.byref(nring),
+                                              ctypes.byref(th), ctypes.byref(w)))
+        self.npix, self.nring = npix.value, nring.value
+        self.theta = np.ctypeslib.as_array(th, (self.nring,)).copy()
+        self.weight = np.ctypeslib.as_array(w, (self.nring,)).copy()
+        ph = ctypes.POINTER(ctypes.c_double)()
+        nphi = ctypes.POINTER(ctypes.c_int)()
+        off = ctypes.POINTER(ctypes.c_int64)()
+        L = ctypes.c_int()
+        _check(load_library().cmbws_grid_rings(handle, ctypes.byref(ph), ctypes.byref(nphi),
+                                               ctypes.byref(off), ctypes.byref(L)))
+        self.phi0 = np.ctypeslib.as_array(ph, (self.nring,)).copy()
+        self.nphi = np.ctypeslib.as_array(nphi, (self.nring,)).copy()
+        self.offset = np.ctypeslib.as_array(off, (self.nring + 1,)).copy()
+
+    def pixel_coords(self):
+        """(cos theta, phi) of every pixel, ring order."""
+        z = np.repeat(np.cos(self.theta), self.nphi)
+        ph = np.concatenate([self.phi0[r] + 2 * np.pi * np.arange(self.nphi[r]) / self.nphi[r]
+                             for r in range(self.nring)])
+        return z, ph
+
+    def pixel_weights(self):
+        return np.repeat(self.weight, self.nphi)
+
+    def close(self):
+        if self.handle:
+            load_library().cmbws_grid_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cmbws_plan_grid(kind, n, lmax):
+    h = ctypes.c_void_p()
+    _check(load_library().cmbws_plan_grid(int(kind), int(n), int(lmax), ctypes.byref(h)))
+    return Grid(h, kind, n, lmax)
+
+
+def cmbws_grid_info(grid):
+    return grid.npix, grid.nring, grid.theta, grid.weight
+
+
+def cmbws_grid_rings(grid):
+    return grid.phi0, grid.nphi, grid.offset, grid.lmax
+
+
+def cmbws_grid_destroy(grid):
+    grid.close()
+
+
+def cmbws_sht_synth(grid, prec, alm, map_out, nmaps=1, stream=None):
+    nalm = (grid.lmax + 1) ** 2
+    _check(load_library().cmbws_sht_synth(grid.handle, int(prec), _dptr(alm, nmaps * nalm, "alm"),
+                                          _dptr(map_out, nmaps * grid.npix, "map"), int(nmaps),
+                                          _stream(stream)))
+
+
+def cmbws_sht_analysis(grid, prec, map_in, alm, nmaps=1, weighted=1, stream=None):
+    nalm = (grid.lmax + 1) ** 2
+    _check(load_library().cmbws_sht_analysis(grid.handle, int(prec),
+                                             _dptr(map_in, nmaps * grid.npix, "map"),
+                                             _dptr(alm, nmaps * nalm, "alm"), int(nmaps),
+                                             int(weighted), _stream(stream)))
+
+
+class Model:
+    """A model handle (owns it); keeps its grids alive."""
+
+    def __init__(self, handle, grids, lmax_comp):
+        self.handle = handle
+        self.grids = grids
+        self.lmax_comp = list(lmax_comp)
+        nvec = ctypes.c_int64()
+        na = ctypes.c_int()
+        nm = ctypes.c_int()
+        _check(load_library().cmbws_model_info(handle, ctypes.byref(nvec), ctypes.byref(na),
+                                               ctypes.byref(nm)))
+        self.nvec, self.nsht_A, self.nsht_M = nvec.value, na.value, nm.value
+
+    def close(self):
+        if self.handle:
+            load_library().cmbws_model_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cmbws_model_create(lmax_comp, band_grids, beams, cls, ninv, mix_scalar, prec=CMBWS_FP64,
+                       stream=None):
+    """lmax_comp: [ncomp] ints; band_grids: [nobs] Grid; beams: [nobs] arrays b_l (l <= L_nu);
+    cls: [ncomp] arrays C_l or None; ninv: [nobs] CUDA float64 maps; mix_scalar: [nobs, ncomp]."""
+    ncomp, nobs = len(lmax_comp), len(band_grids)
+    q = np.ascontiguousarray(np.asarray(mix_scalar, dtype=np.float64).reshape(nobs, ncomp))
+    lk = (ctypes.c_int * ncomp)(*[int(v) for v in lmax_comp])
+    gh = (ctypes.c_void_p * nobs)(*[g.handle.value if isinstance(g.handle, ctypes.c_void_p) else g.handle
+                                    for g in band_grids])
+    keep = []
+    bp = (ctypes.POINTER(ctypes.c_double) * nobs)()
+    for nu in range(nobs):
+        b = np.ascontiguousarray(np.asarray(beams[nu], dtype=np.float64))
+        if b.size < band_grids[nu].lmax + 1:
+            raise ValueError(f"beam {nu} needs {band_grids[nu].lmax + 1} entries")
+        keep.append(b)
+        bp[nu] = b.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    cp = (ctypes.POINTER(ctypes.c_double) * ncomp)()
+    for k in range(ncomp):
+        if cls[k] is None:
+            cp[k] = ctypes.POINTER(ctypes.c_double)()
+        else:
+            c = np.ascontiguousarray(np.asarray(cls[k], dtype=np.float64))
+            if c.size < lmax_comp[k] + 1:
+                raise ValueError(f"C_l of component {k} needs {lmax_comp[k] + 1} entries")
+            keep.append(c)
+            cp[k] = c.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    nv = (ctypes.c_void_p * nobs)(*[_dptr(ninv[nu], band_grids[nu].npix, f"ninv[{nu}]").value
+                                    for nu in range(nobs)])
+    desc = ModelDesc(ncomp, nobs, lk, gh, bp, cp, nv, q.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    h = ctypes.c_void_p()
+    _check(load_library().cmbws_model_create(ctypes.byref(desc), int(prec), _stream(stream),
+                                             ctypes.byref(h)))
+    return Model(h, list(band_grids), lmax_comp)
+
+
+def cmbws_model_destroy(model):
+    model.close()
+
+
+def cmbws_model_info(model):
+    return model.nvec, model.nsht_A, model.nsht_M
+
+
+def cmbws_apply_A(model, x, y, stream=None):
+    _check(load_library().cmbws_apply_A(model.handle, _dptr(x, model.nvec, "x"),
+                                        _dptr(y, model.nvec, "y"), _stream(stream)))
+
+
+def cmbws_apply_precond(model, r, z, stream=None):
+    _check(load_library().cmbws_apply_precond(model.handle, _dptr(r, model.nvec, "r"),
+                                               _dptr(z, model.nvec, "z"), _stream(stream)))
+
+
+def cmbws_rhs(model, d, b, omega1=None, omega2=None, stream=None):
+    nobs = len(model.grids)
+    dp = (ctypes.c_void_p * nobs)(*[_dptr(d[nu], model.grids[nu].npix, f"d[{nu}]").value
+                                    for nu in range(nobs)])
+    if omega1 is not None:
+        w1 = (ctypes.c_void_p * nobs)(*[_dptr(omega1[nu], model.grids[nu].npix, f"omega1[{nu}]").value
+                                        for nu in range(nobs)])
+    else:
+        w1 = ctypes.POINTER(ctypes.c_void_p)()
+    w2 = _dptr(omega2, model.nvec, "omega2") if omega2 is not None else ctypes.c_void_p()
+    _check(load_library().cmbws_rhs(model.handle, dp, w1, w2, _dptr(b, model.nvec, "b"),
+                                    _stream(stream)))
+
+
+def cmbws_project(model, x, d, stream=None):
+    """d[nu] = P_nu x for every band (d: list of CUDA float64 maps, written)."""
+    nobs = len(model.grids)
+    dp = (ctypes.c_void_p * nobs)(*[_dptr(d[nu], model.grids[nu].npix, f"d[{nu}]").value
+                                    for nu in range(nobs)])
+    _check(load_library().cmbws_project(model.handle, _dptr(x, model.nvec, "x"), dp, _stream(stream)))
+
+
+PROFILE_STAGES = ("legendre_synth", "legendre_adjoint", "adjoint_reduce", "ring_fft", "harmonic",
+                  "cg_vector")
+
+
+def cmbws_profile_enable(on=True):
+    _check(load_library().cmbws_profile_enable(1 if on else 0))
+
+
+def cmbws_profile_read(reset=True):
+    """{(stage, "fp32"|"fp64"): (milliseconds, launches, algorithmic flops)} since the last reset."""
+    ns = len(PROFILE_STAGES)
+    ms = (ctypes.c_double * (2 * ns))()
+    n = (ctypes.c_int64 * (2 * ns))()
+    fl = (ctypes.c_double * (2 * ns))()
+    _check(load_library().cmbws_profile_read(ms, n, fl, 1 if reset else 0))
+    out = {}
+    for i in range(2 * ns):
+        out[(PROFILE_STAGES[i % ns], "fp64" if i >= ns else "fp32")] = (ms[i], n[i], fl[i])
+    return out
+
+
+def cmbws_cg_solve(model, b, x, tol=1e-6, maxiter=1000, precond=1, inner_tol=1e-3, max_outer=20,
+                   timeout_s=0.0, stream=None, check=True):
+    """Solve A x = b in place (x holds the initial guess). Returns the report as a dict."""
+    opts = CgOpts(float(tol), int(maxiter), int(precond), float(inner_tol), int(max_outer),
+                  float(timeout_s))
+    rep = CgReport()
+    code = load_library().cmbws_cg_solve(model.handle, _dptr(b, model.nvec, "b"),
+                                         _dptr(x, model.nvec, "x"), ctypes.byref(opts),
+                                         ctypes.byref(rep), _stream(stream))
+    if check:
+        _check(code)
+    out = rep.as_dict()
+    out["code"] = code
+    return out

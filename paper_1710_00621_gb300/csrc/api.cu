@@ -1,0 +1,199 @@
+// Error state, device buffers and the SHT entry points of the C ABI
+// (synthesis Y, analysis Y^T W and adjoint synthesis Y^T; Sec. 2.1, Sec. 3.2).
+#include <cstdarg>
+#include <cstdio>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "common.h"
+
+namespace cmbws {
+
+static thread_local std::string t_err;
+
+void set_error(const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  t_err = buf;
+}
+
+void clear_error() { t_err.clear(); }
+
+int DevMem::alloc(size_t n) {
+  release();
+  if (n == 0) n = 16;
+  cudaError_t e = cudaMalloc(&p, n);
+  if (e != cudaSuccess) {
+    p = nullptr;
+    cudaGetLastError();
+    set_error("cudaMalloc(%zu) failed: %s", n, cudaGetErrorString(e));
+    return CMBWS_ERR_NOMEM;
+  }
+  bytes = n;
+  return CMBWS_OK;
+}
+
+int DevMem::ensure(size_t n) {
+  if (p && bytes >= n) return CMBWS_OK;
+  return alloc(n);
+}
+
+int DevMem::upload(const void* src, size_t n) {
+  CMBWS_TRY(alloc(n));
+  if (n) CMBWS_CUDA(cudaMemcpy(p, src, n, cudaMemcpyHostToDevice));
+  return CMBWS_OK;
+}
+
+namespace {
+struct ProfRec {
+  int slot;
+  double flops;
+  cudaEvent_t a, b;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfRec> g_prof;
+std::vector<cudaEvent_t> g_pool;
+
+cudaEvent_t pool_get() {
+  if (!g_pool.empty()) {
+    cudaEvent_t e = g_pool.back();
+    g_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+}  // namespace
+
+ProfScope::ProfScope(int stage, cudaStream_t s_, int fp64, double flops_)
+    : slot(stage + (fp64 ? PROF_N : 0)), flops(flops_), s(s_) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (!g_prof_on) return;
+  a = pool_get();
+  if (a) cudaEventRecord(a, s);
+}
+
+ProfScope::~ProfScope() {
+  if (!a) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  cudaEvent_t b = pool_get();
+  if (!b) {
+    g_pool.push_back(a);
+    return;
+  }
+  cudaEventRecord(b, s);
+  g_prof.push_back({slot, flops, a, b});
+}
+
+static int check_device(const Grid& g) {
+  int dev = -1;
+  CMBWS_CUDA(cudaGetDevice(&dev));
+  if (dev != g.device) {
+    set_error("grid was planned on device %d, current device is %d", g.device, dev);
+    return CMBWS_ERR_ARG;
+  }
+  return CMBWS_OK;
+}
+
+}  // namespace cmbws
+
+using namespace cmbws;
+
+extern "C" const char* cmbws_last_error(void) { return t_err.c_str(); }
+
+extern "C" const char* cmbws_version(void) { return "cmbws 0.1 (sm_103a)"; }
+
+extern "C" int cmbws_profile_enable(int on) {
+  clear_error();
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof_on = on != 0;
+  return CMBWS_OK;
+}
+
+extern "C" int cmbws_profile_read(double* ms, int64_t* launches, double* flops, int reset) {
+  clear_error();
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  double t[2 * PROF_N] = {0}, f[2 * PROF_N] = {0};
+  int64_t c[2 * PROF_N] = {0};
+  for (const ProfRec& r : g_prof) {
+    CMBWS_CUDA(cudaEventSynchronize(r.b));
+    float dt = 0.f;
+    CMBWS_CUDA(cudaEventElapsedTime(&dt, r.a, r.b));
+    t[r.slot] += dt;
+    f[r.slot] += r.flops;
+    c[r.slot] += 1;
+  }
+  for (int i = 0; i < 2 * PROF_N; ++i) {
+    if (ms) ms[i] = t[i];
+    if (launches) launches[i] = c[i];
+    if (flops) flops[i] = f[i];
+  }
+  if (reset) {
+    for (const ProfRec& r : g_prof) {
+      g_pool.push_back(r.a);
+      g_pool.push_back(r.b);
+    }
+    g_prof.clear();
+  }
+  return CMBWS_OK;
+}
+
+extern "C" int cmbws_sht_synth(cmbws_grid gh, cmbws_prec prec, const double* alm, double* map,
+                               int nmaps, void* stream) {
+  clear_error();
+  Grid* g = reinterpret_cast<Grid*>(gh);
+  if (!g || !alm || !map || nmaps < 1 || (prec != CMBWS_FP64 && prec != CMBWS_FP32)) {
+    set_error("cmbws_sht_synth: invalid arguments");
+    return CMBWS_ERR_ARG;
+  }
+  CMBWS_TRY(check_device(*g));
+  if (!ringfft_smem_ok(*g, prec)) {
+    set_error("cmbws_sht_synth: ring length %d too large for this precision", g->max_n);
+    return CMBWS_ERR_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t es = prec_size(prec);
+  const int64_t nlm = nlm_of(g->lmax);
+  CMBWS_TRY(g->ws_alm.ensure((size_t)nmaps * nlm * 2 * es));
+  CMBWS_TRY(g->ws_F.ensure((size_t)nmaps * g->nring * (g->lmax + 1) * 2 * es));
+  CMBWS_TRY(pack_alm(*g, prec, nmaps, alm, g->ws_alm.p, s));
+  CMBWS_TRY(legendre_synth(*g, prec, nmaps, g->ws_alm.p, g->ws_F.p, s));
+  CMBWS_TRY(ringfft_synth(*g, prec, nmaps, g->ws_F.p, map, s));
+  return CMBWS_OK;
+}
+
+extern "C" int cmbws_sht_analysis(cmbws_grid gh, cmbws_prec prec, const double* map, double* alm,
+                                  int nmaps, int weighted, void* stream) {
+  clear_error();
+  Grid* g = reinterpret_cast<Grid*>(gh);
+  if (!g || !alm || !map || nmaps < 1 || (prec != CMBWS_FP64 && prec != CMBWS_FP32)) {
+    set_error("cmbws_sht_analysis: invalid arguments");
+    return CMBWS_ERR_ARG;
+  }
+  CMBWS_TRY(check_device(*g));
+  if (!ringfft_smem_ok(*g, prec)) {
+    set_error("cmbws_sht_analysis: ring length %d too large for this precision", g->max_n);
+    return CMBWS_ERR_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t es = prec_size(prec);
+  const int64_t nlm = nlm_of(g->lmax);
+  CMBWS_TRY(g->ws_F.ensure((size_t)nmaps * g->nring * (g->lmax + 1) * 2 * es));
+  const size_t pb = legendre_adjoint_part_bytes(*g, prec, nmaps);
+  CMBWS_TRY(g->ws_part.ensure(pb));
+  CMBWS_TRY(g->ws_out.ensure((size_t)nmaps * nlm * 16));
+  CMBWS_TRY(ringfft_analysis(*g, prec, nmaps, map, weighted, g->ws_F.p, s));
+  CMBWS_TRY(legendre_adjoint(*g, prec, nmaps, g->ws_F.p, g->ws_part.p, g->ws_part.bytes,
+                             g->ws_out.as<double>(), s));
+  CMBWS_TRY(unpack_alm(*g, nmaps, g->ws_out.as<double>(), alm, s));
+  return CMBWS_OK;
+}

@@ -1,0 +1,322 @@
+// Preconditioned conjugate gradients for A x = b (Sec. 2.3) with M_PI (Sec. 3.3).
+//
+// Vectors are FP64 on the device.  Dot products are deterministic: a fixed
+// grid writes per-block partial sums, one block adds them in a fixed order.
+// The host reads one or two scalars per iteration (alpha and beta are
+// computed on the host in FP64).
+//
+// FP64 models: plain PCG, then one FP64 apply certifies ||b - A x|| / ||b||.
+// FP32 models: iterative refinement.  Each pass solves A d = r by PCG with
+// the FP32 transform chain (FP64 vectors and scalars) until the inner
+// residual falls by inner_tol, then x += d and r = b - A x with the FP64
+// chain; the loop ends when that FP64 residual certifies tol.
+#include <chrono>
+#include <cmath>
+
+#include "model.h"
+
+namespace cmbws {
+
+namespace {
+
+constexpr int kRedBlocks = 1024;
+constexpr int kRedThreads = 256;
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sh[i];
+  return t;
+}
+
+// partial[b] = sum_{i in block-stride range} a[i] * b[i]
+__global__ void k_dot_partial(const double* __restrict__ a, const double* __restrict__ b, int64_t n,
+                              double* __restrict__ partial) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    s += a[i] * b[i];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// x += alpha p; r -= alpha q; partial sums of r.r
+__global__ void k_update_xr(double* __restrict__ x, double* __restrict__ r,
+                            const double* __restrict__ p, const double* __restrict__ q, double alpha,
+                            int64_t n, double* __restrict__ partial) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] += alpha * p[i];
+    const double ri = r[i] - alpha * q[i];
+    r[i] = ri;
+    s += ri * ri;
+  }
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// p = z + beta p
+__global__ void k_xpby(const double* __restrict__ z, double* __restrict__ p, double beta, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = z[i] + beta * p[i];
+}
+
+// r = b - y; partial sums of r.r
+__global__ void k_resid(const double* __restrict__ b, const double* __restrict__ y,
+                        double* __restrict__ r, int64_t n, double* __restrict__ partial) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double ri = b[i] - y[i];
+    r[i] = ri;
+    s += ri * ri;
+  }
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// y += x
+__global__ void k_axpy1(const double* __restrict__ x, double* __restrict__ y, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] += x[i];
+}
+
+__global__ void k_finish(const double* __restrict__ partial, int nb, double* __restrict__ out) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) s += partial[i];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) *out = s;
+}
+
+struct Clock {
+  std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+  double s() const {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+};
+
+struct Solver {
+  Model& M;
+  cudaStream_t s;
+  int64_t n;
+  double* red;     // [kRedBlocks + 1]
+  double* hscal;   // pinned host scalar
+
+  int finish(double* out) {
+    {
+      ProfScope ps_(PROF_CG, s);
+      k_finish<<<1, kRedThreads, 0, s>>>(red, kRedBlocks, red + kRedBlocks);
+      CMBWS_LAUNCH_CHECK();
+    }
+    CMBWS_CUDA(cudaMemcpyAsync(hscal, red + kRedBlocks, 8, cudaMemcpyDeviceToHost, s));
+    CMBWS_CUDA(cudaStreamSynchronize(s));
+    *out = *hscal;
+    return CMBWS_OK;
+  }
+  int dot(const double* a, const double* b, double* out) {
+    {
+      ProfScope ps_(PROF_CG, s);
+      k_dot_partial<<<kRedBlocks, kRedThreads, 0, s>>>(a, b, n, red);
+      CMBWS_LAUNCH_CHECK();
+    }
+    return finish(out);
+  }
+  // r = b - A x (FP64 chain), returns ||r||^2
+  int true_residual(const double* b, const double* x, double* r, double* tmp, double* rr) {
+    CMBWS_TRY(M.apply_A(x, tmp, CMBWS_FP64, s));
+    {
+      ProfScope ps_(PROF_CG, s);
+      k_resid<<<kRedBlocks, kRedThreads, 0, s>>>(b, tmp, r, n, red);
+      CMBWS_LAUNCH_CHECK();
+    }
+    return finish(rr);
+  }
+};
+
+}  // namespace
+
+// PCG on A d = r0 (d starts at zero), operator precision `prec`; stops when
+// ||r|| <= stop_abs or after maxit iterations.  r0 is overwritten with the final residual.
+static int pcg_core(Solver& S, int prec, int use_M, double* d, double* r, double stop_abs, int maxit,
+                    int* iters, double* rr_out, const Clock& clk, double timeout) {
+  Model& M = S.M;
+  double* z = M.cg_z.as<double>();
+  double* p = M.cg_p.as<double>();
+  double* q = M.cg_q.as<double>();
+  const int64_t n = S.n;
+  CMBWS_CUDA(cudaMemsetAsync(d, 0, n * 8, S.s));
+  double rr;
+  CMBWS_TRY(S.dot(r, r, &rr));
+  *rr_out = rr;
+  *iters = 0;
+  if (std::sqrt(rr) <= stop_abs) return CMBWS_OK;
+  if (use_M) CMBWS_TRY(M.apply_precond(r, z, prec, S.s));
+  else CMBWS_CUDA(cudaMemcpyAsync(z, r, n * 8, cudaMemcpyDeviceToDevice, S.s));
+  CMBWS_CUDA(cudaMemcpyAsync(p, z, n * 8, cudaMemcpyDeviceToDevice, S.s));
+  double rz;
+  CMBWS_TRY(S.dot(r, z, &rz));
+  for (int it = 0; it < maxit; ++it) {
+    CMBWS_TRY(M.apply_A(p, q, prec, S.s));
+    double pq;
+    CMBWS_TRY(S.dot(p, q, &pq));
+    if (!(pq > 0.0) || !std::isfinite(pq) || !std::isfinite(rz)) {
+      set_error("CG breakdown: p.Ap = %g, r.z = %g at iteration %d", pq, rz, it);
+      return CMBWS_ERR_BREAKDOWN;
+    }
+    const double alpha = rz / pq;
+    {
+      ProfScope ps_(PROF_CG, S.s);
+      k_update_xr<<<kRedBlocks, kRedThreads, 0, S.s>>>(d, r, p, q, alpha, n, S.red);
+      CMBWS_LAUNCH_CHECK();
+    }
+    CMBWS_TRY(S.finish(&rr));
+    *iters = it + 1;
+    *rr_out = rr;
+    if (!std::isfinite(rr)) {
+      set_error("CG breakdown: non-finite residual at iteration %d", it);
+      return CMBWS_ERR_BREAKDOWN;
+    }
+    if (std::sqrt(rr) <= stop_abs) return CMBWS_OK;
+    if (timeout > 0 && clk.s() > timeout) {
+      set_error("CG: wall-clock budget of %g s exhausted", timeout);
+      return CMBWS_ERR_TIMEOUT;
+    }
+    if (use_M) CMBWS_TRY(M.apply_precond(r, z, prec, S.s));
+    else CMBWS_CUDA(cudaMemcpyAsync(z, r, n * 8, cudaMemcpyDeviceToDevice, S.s));
+    double rz_new;
+    CMBWS_TRY(S.dot(r, z, &rz_new));
+    const double beta = rz_new / rz;
+    rz = rz_new;
+    {
+      ProfScope ps_(PROF_CG, S.s);
+      k_xpby<<<kRedBlocks, kRedThreads, 0, S.s>>>(z, p, beta, n);
+      CMBWS_LAUNCH_CHECK();
+    }
+  }
+  return CMBWS_ERR_NOT_CONVERGED;
+}
+
+static int cg_solve_impl(Model& M, const double* b, double* x, const cmbws_cg_opts& o,
+                         cmbws_cg_report& rep, cudaStream_t s) {
+  const Clock clk;
+  const int64_t n = M.nvec;
+  CMBWS_TRY(M.cg_r.ensure(n * 8));
+  CMBWS_TRY(M.cg_z.ensure(n * 8));
+  CMBWS_TRY(M.cg_p.ensure(n * 8));
+  CMBWS_TRY(M.cg_q.ensure(n * 8));
+  CMBWS_TRY(M.cg_d.ensure(n * 8));
+  CMBWS_TRY(M.cg_x.ensure(n * 8));
+  CMBWS_TRY(M.cg_red.ensure((kRedBlocks + 1) * 8));
+  double* hscal = nullptr;
+  CMBWS_CUDA(cudaMallocHost(&hscal, 8));
+  struct Free {
+    double* p;
+    ~Free() { cudaFreeHost(p); }
+  } fr{hscal};
+  Solver S{M, s, n, M.cg_red.as<double>(), hscal};
+  const long long sht0 = M.n_sht;
+
+  double bb;
+  CMBWS_TRY(S.dot(b, b, &bb));
+  const double bnorm = std::sqrt(bb);
+  double* r = M.cg_r.as<double>();
+  double* tmp = M.cg_x.as<double>();
+  double* d = M.cg_d.as<double>();
+  if (bnorm == 0.0) {
+    CMBWS_CUDA(cudaMemsetAsync(x, 0, n * 8, s));
+    rep.rel_res = 0.0;
+    return CMBWS_OK;
+  }
+  double rr;
+  CMBWS_TRY(S.true_residual(b, x, r, tmp, &rr));
+  int status = CMBWS_ERR_NOT_CONVERGED;
+  int total = 0, outer = 0;
+  const double target = o.tol * bnorm;
+  while (true) {
+    if (std::sqrt(rr) <= target) {
+      status = CMBWS_OK;
+      break;
+    }
+    if (total >= o.maxiter) {
+      set_error("CG: %d iterations without reaching tol (rel. residual %g)", total,
+                std::sqrt(rr) / bnorm);
+      status = CMBWS_ERR_NOT_CONVERGED;
+      break;
+    }
+    if (o.timeout_s > 0 && clk.s() > o.timeout_s) {
+      set_error("CG: wall-clock budget of %g s exhausted", o.timeout_s);
+      status = CMBWS_ERR_TIMEOUT;
+      break;
+    }
+    if (M.prec == CMBWS_FP32 && outer >= o.max_outer) {
+      set_error("CG: %d refinement passes without reaching tol", outer);
+      status = CMBWS_ERR_NOT_CONVERGED;
+      break;
+    }
+    // inner solve A d = r; FP64 models aim directly at the target (plus a small
+    // margin for the gap between recursive and true residuals)
+    const double stop = M.prec == CMBWS_FP64 ? 0.5 * target
+                                             : std::max(o.inner_tol * std::sqrt(rr), 0.5 * target);
+    int it = 0;
+    double rr_in;
+    const int st = pcg_core(S, M.prec, o.precond, d, r, stop, o.maxiter - total, &it, &rr_in, clk,
+                            o.timeout_s);
+    total += it;
+    ++outer;
+    if (st != CMBWS_OK && st != CMBWS_ERR_NOT_CONVERGED) {
+      status = st;
+      break;
+    }
+    {
+      ProfScope ps_(PROF_CG, s);
+      k_axpy1<<<kRedBlocks, kRedThreads, 0, s>>>(d, x, n);
+      CMBWS_LAUNCH_CHECK();
+    }
+    CMBWS_TRY(S.true_residual(b, x, r, tmp, &rr));
+    if (st == CMBWS_ERR_NOT_CONVERGED && std::sqrt(rr) > target) {
+      set_error("CG: iteration cap %d reached (rel. residual %g)", o.maxiter, std::sqrt(rr) / bnorm);
+      status = CMBWS_ERR_NOT_CONVERGED;
+      break;
+    }
+  }
+  rep.iters = total;
+  rep.outer = outer;
+  rep.rel_res = std::sqrt(rr) / bnorm;
+  rep.n_sht = (int)(M.n_sht - sht0);
+  return status;
+}
+
+}  // namespace cmbws
+
+using namespace cmbws;
+
+extern "C" int cmbws_cg_solve(cmbws_model mh, const double* b, double* x, const cmbws_cg_opts* opts,
+                              cmbws_cg_report* report, void* stream) {
+  clear_error();
+  Model* M = reinterpret_cast<Model*>(mh);
+  if (!M || !b || !x || !opts || b == x || !(opts->tol > 0.0) || opts->maxiter < 1) {
+    set_error("cmbws_cg_solve: invalid arguments");
+    return CMBWS_ERR_ARG;
+  }
+  cmbws_cg_opts o = *opts;
+  if (!(o.inner_tol > 0.0 && o.inner_tol < 1.0)) o.inner_tol = 1e-3;
+  if (o.max_outer < 1) o.max_outer = 20;
+  cmbws_cg_report rep{};
+  const auto t0 = std::chrono::steady_clock::now();
+  int st = cg_solve_impl(*M, b, x, o, rep, (cudaStream_t)stream);
+  rep.ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  rep.status = st;
+  if (report) *report = rep;
+  return st;
+}

@@ -1,0 +1,193 @@
+// Internal declarations shared by the translation units of libcmbws.
+//
+// Data layout in device memory
+// ----------------------------
+// * Internal harmonic layout ("lm"): for band-limit L, complex pairs
+//   (cos part, sin part) of coefficient (l, m), m-major, l contiguous:
+//   lm(m, l) = m (L+1) - m (m-1) / 2 + (l - m), nlm = (L+1)(L+2)/2.
+//   The synthesis Legendre kernel consumes coefficients multiplied by the
+//   recurrence normalisation c_lm (setup.cu); the adjoint returns final values.
+// * Ring spectra F[map][ring][m] (complex, m = 0..L): output of the synthesis
+//   Legendre stage / input of the adjoint Legendre stage; the ring FFT stage
+//   reads and writes them.
+// * Ring pairs: pair p joins ring p (north) and ring nring-1-p (south); an
+//   equator ring (odd nring) is a pair with no south ring.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/cmbws.h"
+
+namespace cmbws {
+
+void set_error(const char* fmt, ...);
+void clear_error();
+
+#define CMBWS_CUDA(expr)                                                                     \
+  do {                                                                                       \
+    cudaError_t e_ = (expr);                                                                 \
+    if (e_ != cudaSuccess) {                                                                 \
+      ::cmbws::set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__,   \
+                         __LINE__);                                                          \
+      return CMBWS_ERR_CUDA;                                                                 \
+    }                                                                                        \
+  } while (0)
+
+#define CMBWS_LAUNCH_CHECK()                                                                 \
+  do {                                                                                       \
+    cudaError_t e_ = cudaGetLastError();                                                     \
+    if (e_ != cudaSuccess) {                                                                 \
+      ::cmbws::set_error("kernel launch failed: %s (%s:%d)", cudaGetErrorString(e_),         \
+                         __FILE__, __LINE__);                                                \
+      return CMBWS_ERR_CUDA;                                                                 \
+    }                                                                                        \
+  } while (0)
+
+#define CMBWS_TRY(expr)            \
+  do {                             \
+    int s_ = (expr);               \
+    if (s_ != CMBWS_OK) return s_; \
+  } while (0)
+
+// Owning device allocation.
+struct DevMem {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevMem() = default;
+  DevMem(const DevMem&) = delete;
+  DevMem& operator=(const DevMem&) = delete;
+  DevMem(DevMem&& o) noexcept : p(o.p), bytes(o.bytes) {
+    o.p = nullptr;
+    o.bytes = 0;
+  }
+  DevMem& operator=(DevMem&& o) noexcept {
+    if (this != &o) {
+      release();
+      p = o.p;
+      bytes = o.bytes;
+      o.p = nullptr;
+      o.bytes = 0;
+    }
+    return *this;
+  }
+  ~DevMem() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  int alloc(size_t n);                  // exact size, contents undefined
+  int ensure(size_t n);                 // grow if needed (contents lost on growth)
+  int upload(const void* src, size_t n);
+  template <typename T> T* as() const { return static_cast<T*>(p); }
+};
+
+inline __host__ __device__ int64_t lm_off(int L, int m) {
+  return (int64_t)m * (L + 1) - (int64_t)m * (m - 1) / 2;
+}
+inline __host__ __device__ int64_t nlm_of(int L) { return (int64_t)(L + 1) * (L + 2) / 2; }
+// offset of the m block in the packed CMBWS_ALM layout
+inline __host__ __device__ int64_t packed_off(int L, int m) {
+  return m == 0 ? 0 : (int64_t)(L + 1) + (int64_t)(m - 1) * (2 * L + 2 - m);
+}
+
+// Per ring length: how the ring DFT is done.
+struct FftPlan {
+  int n;          // ring length
+  int n2;         // power-of-two transform size (n itself, or the Bluestein size)
+  int bluestein;  // 1 if n is not a power of two
+  int pad;
+  int64_t chirp;  // offset (complex entries) of b_t = exp(i pi t^2 / n), t < n
+  int64_t filt;   // offset of the Bluestein filter spectrum (n2 entries, includes 1/n2)
+};
+
+struct Grid {
+  int device = 0;
+  int kind = 0, n = 0, lmax = 0, nring = 0, npair = 0;
+  int64_t npix = 0;
+  std::vector<double> theta, weight, phi0;
+  std::vector<int> nphi;
+  std::vector<int64_t> offset;
+
+  // per ring pair (device)
+  DevMem y64, y32;        // 1 - cos(theta) of the north ring [npair] (see setup.cu)
+  DevMem pair_ring;       // int2 {north, south or -1} [npair]
+  DevMem pair_plan;       // int plan index [npair]
+  DevMem pair_phase;      // int: 1 if phi0 = pi / nphi, 0 if phi0 = 0 [npair]
+  DevMem ring_off;        // int64 first pixel of each ring [nring + 1]
+  DevMem ring_w64, ring_w32;  // per-pixel weight of each ring [nring]
+
+  // Legendre recurrence tables (device), index lm(m, l)
+  DevMem A64, A32;        // A_lm of the rescaled recurrence mu_l = A_l x mu_{l-1} - mu_{l-2}
+  DevMem c64;             // lambda_lm = c_lm mu_lm
+  DevMem ls;              // int [L+1][npair] first l (same parity as m) that is injected
+  DevMem st64, st32;      // {mu_ls, mu_ls+1} [L+1][npair]
+
+  // ring FFT tables (device)
+  std::vector<FftPlan> plans;
+  DevMem plans_d;
+  DevMem fft64, fft32;    // complex tables: chirps, filters, twiddles
+  int64_t tw_off = 0;     // offset of exp(-2 pi i k / nmax2), k < nmax2 / 2
+  int nmax2 = 1;          // largest power-of-two transform size
+  int max_n = 1;
+
+  // workspace for cmbws_sht_* calls
+  DevMem ws_alm, ws_F, ws_part, ws_out;
+};
+
+// ---- launchers (legendre.cu) ----
+// alm: [nmaps][nlm] complex coefficients multiplied by c_lm; F: [nmaps][nring][L+1]
+int legendre_synth(const Grid& g, int prec, int nmaps, const void* alm, void* F, cudaStream_t s);
+// F -> per-CTA partial sums -> out[nmaps][nlm] complex FP64 (final coefficients)
+int legendre_adjoint(const Grid& g, int prec, int nmaps, const void* F, void* part, size_t part_bytes,
+                     double* out, cudaStream_t s);
+size_t legendre_adjoint_part_bytes(const Grid& g, int prec, int nmaps);
+
+// ---- launchers (ringfft.cu) ----
+// F (ring spectra) -> pixel maps map[nmaps][npix] (FP64 out)
+int ringfft_synth(const Grid& g, int prec, int nmaps, const void* F, double* map, cudaStream_t s);
+// map[nmaps][npix] (FP64 in) -> F; weighted: multiply by quadrature weights
+int ringfft_analysis(const Grid& g, int prec, int nmaps, const double* map, int weighted, void* F,
+                     cudaStream_t s);
+// F -> pixels -> * pix[map] -> F, in place. pix: [nmaps] device pointers (prec type) of npix.
+int ringfft_fused(const Grid& g, int prec, int nmaps, void* F, const void* const* pix,
+                  cudaStream_t s);
+int ringfft_smem_ok(const Grid& g, int prec);
+
+// ---- grid setup (setup.cu) ----
+int grid_build_tables(Grid& g);
+
+// ---- pack / unpack (setup.cu) ----
+// packed CMBWS_ALM FP64 [nmaps][(L+1)^2] -> internal lm complex (prec), multiplied by c_lm
+int pack_alm(const Grid& g, int prec, int nmaps, const double* packed, void* alm, cudaStream_t s);
+// internal lm complex FP64 [nmaps][nlm] -> packed FP64
+int unpack_alm(const Grid& g, int nmaps, const double* lmc, double* packed, cudaStream_t s);
+
+inline size_t prec_size(int prec) { return prec == CMBWS_FP64 ? 8 : 4; }
+
+// ---- kernel timing (api.cu): CUDA events around launches while enabled ----
+// Stages; a record's slot is stage + PROF_N * (FP64 ? 1 : 0).  `flops` is the algorithmic
+// count of the launch (full (l, m) triangle), 0 for stages without one.
+enum {
+  PROF_LEG_SYNTH = 0,
+  PROF_LEG_ADJ = 1,
+  PROF_LEG_RED = 2,
+  PROF_FFT = 3,
+  PROF_HARM = 4,
+  PROF_CG = 5,
+  PROF_N = 6
+};
+struct ProfScope {
+  int slot;
+  double flops;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  ProfScope(int stage, cudaStream_t s_, int fp64 = 1, double flops_ = 0.0);
+  ~ProfScope();
+};
+
+}  // namespace cmbws

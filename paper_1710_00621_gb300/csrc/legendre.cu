@@ -1,0 +1,449 @@
+// Associated-Legendre stage of the spherical harmonic transform (Sec. 2.1),
+// the dominant cost of every apply of A and M_PI (Sec. 3.3 counts SHTs).
+//
+// Synthesis, per m and ring pair (theta, pi - theta):
+//   F_m(theta) = sum_l lambda_lm(theta) a_lm,  with lambda_lm(pi - theta) = (-1)^(l+m) lambda_lm(theta),
+// so E = sum over l+m even and O = sum over l+m odd give F_north = E + O and
+// F_south = E - O from one recurrence.  Adjoint synthesis is the transpose:
+//   a_lm = sum_pairs lambda_lm(theta) (E-part or O-part of the ring spectra).
+//
+// Design (CUDA cores; the recurrence costs two operations per (l, m, pair),
+// the contraction two FMAs per map):
+// * one CTA per (m, block of ring pairs); each thread owns R pairs, walks l
+//   upwards two steps at a time (even/odd partners) and starts each pair at
+//   its precomputed first significant l (start values injected there);
+// * synthesis: the coefficients of the current l-chunk are staged in shared
+//   memory and read as broadcasts; every map of the grid group shares one
+//   recurrence (NM maps per launch);
+// * adjoint: for a chunk of CH values of l each thread forms per-l products
+//   summed over its R pairs, a warp reduce-scatter sums them over 32 lanes,
+//   and the warps of the CTA are summed in shared memory; each CTA writes its
+//   partial sums, which a second kernel adds in a fixed order (deterministic)
+//   and scales by c_lm.
+#include <climits>
+#include <type_traits>
+
+#include "common.h"
+
+namespace cmbws {
+
+namespace {
+
+template <typename T> struct V2;
+template <> struct V2<double> { using t = double2; };
+template <> struct V2<float> { using t = float2; };
+
+constexpr unsigned kFull = 0xffffffffu;
+
+template <typename T, int NM, int R, int NT, int CH>
+__global__ void __launch_bounds__(NT)
+k_leg_synth(const typename V2<T>::t* __restrict__ alm, int64_t alm_stride,
+            const T* __restrict__ Acoef, const int* __restrict__ ls_tab,
+            const typename V2<T>::t* __restrict__ st, const T* __restrict__ yr,
+            const int2* __restrict__ pring, typename V2<T>::t* __restrict__ F, int64_t F_stride,
+            int L, int npair, int nring) {
+  using T2 = typename V2<T>::t;
+  __shared__ __align__(16) T sA[CH];
+  __shared__ __align__(16) T2 sa[NM][CH];
+  __shared__ int s_lo;
+
+  const int m = blockIdx.y;
+  const int64_t lmo = lm_off(L, m) - m;  // index of (m, l) is lmo + l
+  const int pbase = blockIdx.x * NT * R + threadIdx.x;
+
+  int ls[R];
+  T y[R], mu1[R], mu2[R];
+  T2 inj[R];
+  T eR[R][NM], eI[R][NM], oR[R][NM], oI[R][NM];
+  int mylo = INT_MAX;
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    const int p = pbase + i * NT;
+    if (p < npair) {
+      ls[i] = ls_tab[(int64_t)m * npair + p];
+      y[i] = yr[p];
+      inj[i] = st[(int64_t)m * npair + p];
+    } else {
+      ls[i] = INT_MAX;
+      y[i] = 0;
+      inj[i].x = inj[i].y = 0;
+    }
+    mylo = min(mylo, ls[i]);
+    mu1[i] = mu2[i] = 0;
+#pragma unroll
+    for (int k = 0; k < NM; ++k) eR[i][k] = eI[i][k] = oR[i][k] = oI[i][k] = 0;
+  }
+  if (threadIdx.x == 0) s_lo = INT_MAX;
+  __syncthreads();
+  atomicMin(&s_lo, mylo);
+  __syncthreads();
+  const int lo = s_lo;
+  int nxt = mylo;  // next l at which one of this thread's pairs starts
+
+  for (int c0 = lo; c0 <= L; c0 += CH) {
+    __syncthreads();
+    for (int j = threadIdx.x; j < CH; j += NT) {
+      const int l = c0 + j;
+      const bool ok = l <= L;
+      sA[j] = ok ? Acoef[lmo + l] : T(0);
+#pragma unroll
+      for (int k = 0; k < NM; ++k) {
+        T2 v;
+        v.x = v.y = 0;
+        if (ok) v = alm[k * alm_stride + lmo + l];
+        sa[k][j] = v;
+      }
+    }
+    __syncthreads();
+#pragma unroll 2
+    for (int j = 0; j < CH; j += 2) {
+      const int l = c0 + j;
+      const T A0 = sA[j], A1 = sA[j + 1];
+      T ma[R], mb[R];
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+        ma[i] = fma(-A0, y[i], A0) * mu1[i] - mu2[i];
+        mb[i] = fma(-A1, y[i], A1) * ma[i] - mu1[i];
+      }
+      if (l == nxt) {
+        int nn = INT_MAX;
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+          if (ls[i] == l) {
+            ma[i] = inj[i].x;
+            mb[i] = inj[i].y;
+          }
+          if (ls[i] > l) nn = min(nn, ls[i]);
+        }
+        nxt = nn;
+      }
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+        mu2[i] = ma[i];
+        mu1[i] = mb[i];
+      }
+#pragma unroll
+      for (int k = 0; k < NM; ++k) {
+        const T2 a0 = sa[k][j], a1 = sa[k][j + 1];
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+          eR[i][k] += ma[i] * a0.x;
+          eI[i][k] += ma[i] * a0.y;
+          oR[i][k] += mb[i] * a1.x;
+          oI[i][k] += mb[i] * a1.y;
+        }
+      }
+    }
+  }
+
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    const int p = pbase + i * NT;
+    if (p >= npair) continue;
+    const int2 rr = pring[p];
+#pragma unroll
+    for (int k = 0; k < NM; ++k) {
+      T2 fn, fs;
+      fn.x = eR[i][k] + oR[i][k];
+      fn.y = eI[i][k] + oI[i][k];
+      F[k * F_stride + (int64_t)rr.x * (L + 1) + m] = fn;
+      if (rr.y >= 0) {
+        fs.x = eR[i][k] - oR[i][k];
+        fs.y = eI[i][k] - oI[i][k];
+        F[k * F_stride + (int64_t)rr.y * (L + 1) + m] = fs;
+      }
+    }
+  }
+}
+
+// Sum NV values over the 32 lanes of a warp; afterwards lane q holds the
+// sums of flat indices [q * NV/32, (q+1) * NV/32) in v[0 .. NV/32).
+template <typename T, int NV>
+__device__ __forceinline__ void warp_reduce_scatter(T (&v)[NV], int lane) {
+  static_assert(NV % 32 == 0, "NV must be a multiple of 32");
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    const int o = 16 >> s;
+    const int h = (NV >> s) / 2;
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const T send = up ? v[i] : v[i + h];
+      const T keep = up ? v[i + h] : v[i];
+      v[i] = keep + __shfl_xor_sync(kFull, send, o);
+    }
+  }
+}
+
+template <typename T, int NM, int R, int NT, int CH>
+__global__ void __launch_bounds__(NT)
+k_leg_adj(const typename V2<T>::t* __restrict__ F, int64_t F_stride, const T* __restrict__ Acoef,
+          const int* __restrict__ ls_tab, const typename V2<T>::t* __restrict__ st,
+          const T* __restrict__ yr, const int2* __restrict__ pring, T* __restrict__ part,
+          int64_t nlm, int L, int npair, int nring) {
+  using T2 = typename V2<T>::t;
+  constexpr int P = 2 * NM;
+  constexpr int NV0 = CH * P;
+  constexpr int NV = (NV0 + 31) / 32 * 32;
+  constexpr int NW = NT / 32;
+  constexpr int PER = NV / 32;
+  __shared__ T red[NW][NV];
+  __shared__ int s_lo;
+
+  const int m = blockIdx.y;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t lmo = lm_off(L, m) - m;
+  const T* Am = Acoef + lmo;
+  T* pout = part + (int64_t)blockIdx.x * P * nlm + lmo;  // pout[pp * nlm + l]
+  const int pbase = blockIdx.x * NT * R + threadIdx.x;
+
+  int ls[R];
+  T y[R], mu1[R], mu2[R];
+  T2 inj[R];
+  T eR[R][NM], eI[R][NM], oR[R][NM], oI[R][NM];
+  int mylo = INT_MAX;
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    const int p = pbase + i * NT;
+    mu1[i] = mu2[i] = 0;
+    if (p < npair) {
+      ls[i] = ls_tab[(int64_t)m * npair + p];
+      y[i] = yr[p];
+      inj[i] = st[(int64_t)m * npair + p];
+      const int2 rr = pring[p];
+#pragma unroll
+      for (int k = 0; k < NM; ++k) {
+        const T2 gn = F[k * F_stride + (int64_t)rr.x * (L + 1) + m];
+        T2 gs;
+        if (rr.y >= 0) {
+          gs = F[k * F_stride + (int64_t)rr.y * (L + 1) + m];
+        } else {
+          gs.x = gs.y = 0;
+        }
+        eR[i][k] = gn.x + gs.x;
+        eI[i][k] = gn.y + gs.y;
+        oR[i][k] = rr.y >= 0 ? gn.x - gs.x : gn.x;
+        oI[i][k] = rr.y >= 0 ? gn.y - gs.y : gn.y;
+      }
+    } else {
+      ls[i] = INT_MAX;
+      y[i] = 0;
+      inj[i].x = inj[i].y = 0;
+#pragma unroll
+      for (int k = 0; k < NM; ++k) eR[i][k] = eI[i][k] = oR[i][k] = oI[i][k] = 0;
+    }
+    mylo = min(mylo, ls[i]);
+  }
+  if (threadIdx.x == 0) s_lo = INT_MAX;
+  __syncthreads();
+  atomicMin(&s_lo, mylo);
+  __syncthreads();
+  const int lo = s_lo;
+  int nxt = mylo;
+
+  // coefficients below the first significant l of every pair in this block are zero
+  {
+    const int lend = min(lo, L + 1);
+    for (int l = m + threadIdx.x; l < lend; l += NT) {
+#pragma unroll
+      for (int pp = 0; pp < P; ++pp) pout[pp * nlm + l] = T(0);
+    }
+  }
+
+  for (int c0 = lo; c0 <= L; c0 += CH) {
+    T v[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) v[q] = 0;
+#pragma unroll
+    for (int j = 0; j < CH; j += 2) {
+      const int l = c0 + j;
+      const T A0 = (l <= L) ? Am[l] : T(0);
+      const T A1 = (l + 1 <= L) ? Am[l + 1] : T(0);
+      T ma[R], mb[R];
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+        ma[i] = fma(-A0, y[i], A0) * mu1[i] - mu2[i];
+        mb[i] = fma(-A1, y[i], A1) * ma[i] - mu1[i];
+      }
+      if (l == nxt) {
+        int nn = INT_MAX;
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+          if (ls[i] == l) {
+            ma[i] = inj[i].x;
+            mb[i] = inj[i].y;
+          }
+          if (ls[i] > l) nn = min(nn, ls[i]);
+        }
+        nxt = nn;
+      }
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+        mu2[i] = ma[i];
+        mu1[i] = mb[i];
+#pragma unroll
+        for (int k = 0; k < NM; ++k) {
+          v[j * P + 2 * k] += ma[i] * eR[i][k];
+          v[j * P + 2 * k + 1] += ma[i] * eI[i][k];
+          v[(j + 1) * P + 2 * k] += mb[i] * oR[i][k];
+          v[(j + 1) * P + 2 * k + 1] += mb[i] * oI[i][k];
+        }
+      }
+    }
+    warp_reduce_scatter<T, NV>(v, lane);
+#pragma unroll
+    for (int q = 0; q < PER; ++q) red[warp][lane * PER + q] = v[q];
+    __syncthreads();
+    for (int f = threadIdx.x; f < NV0; f += NT) {
+      T sum = 0;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) sum += red[w][f];
+      const int l = c0 + f / P;
+      if (l <= L) pout[(f % P) * nlm + l] = sum;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void k_adj_reduce(const T* __restrict__ part, int nblk, int64_t nlm, int nm,
+                             const double* __restrict__ c, double2* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blockIdx.y;
+  if (i >= nlm) return;
+  double re = 0.0, im = 0.0;
+  for (int b = 0; b < nblk; ++b) {
+    const T* pb = part + ((int64_t)b * 2 * nm + 2 * k) * nlm;
+    re += (double)pb[i];
+    im += (double)pb[nlm + i];
+  }
+  const double cc = c[i];
+  out[(int64_t)k * nlm + i] = make_double2(cc * re, cc * im);
+}
+
+// Launch configuration per precision.
+template <typename T> struct Cfg;
+template <> struct Cfg<float> {
+  static constexpr int SR = 2, SNT = 128, SCH = 256;  // synthesis
+  static constexpr int AR = 2, ANT = 256;             // adjoint
+  template <int NM> static constexpr int ACH() { return NM >= 4 ? 8 : 16; }
+};
+template <> struct Cfg<double> {
+  static constexpr int SR = 2, SNT = 128, SCH = 256;
+  static constexpr int AR = 2, ANT = 256;
+  template <int NM> static constexpr int ACH() { return NM == 1 ? 16 : 8; }
+};
+
+template <typename T, int NM>
+int launch_synth(const Grid& g, const void* alm, int64_t alm_stride, void* F, int64_t F_stride,
+                 cudaStream_t s) {
+  using C = Cfg<T>;
+  using T2 = typename V2<T>::t;
+  const int L = g.lmax;
+  dim3 grd((g.npair + C::SNT * C::SR - 1) / (C::SNT * C::SR), L + 1);
+  const T* A = std::is_same<T, double>::value ? (const T*)g.A64.p : (const T*)g.A32.p;
+  const T2* st = std::is_same<T, double>::value ? (const T2*)g.st64.p : (const T2*)g.st32.p;
+  const T* yr = std::is_same<T, double>::value ? (const T*)g.y64.p : (const T*)g.y32.p;
+  ProfScope ps(PROF_LEG_SYNTH, s, sizeof(T) == 8, 4.0 * g.npair * (double)nlm_of(L) * (NM + 1));
+  k_leg_synth<T, NM, C::SR, C::SNT, C::SCH><<<grd, C::SNT, 0, s>>>(
+      (const T2*)alm, alm_stride, A, g.ls.as<int>(), st, yr, g.pair_ring.as<int2>(), (T2*)F,
+      F_stride, L, g.npair, g.nring);
+  CMBWS_LAUNCH_CHECK();
+  return CMBWS_OK;
+}
+
+template <typename T>
+int adj_nblk(const Grid& g) {
+  using C = Cfg<T>;
+  return (g.npair + C::ANT * C::AR - 1) / (C::ANT * C::AR);
+}
+
+template <typename T, int NM>
+int launch_adj(const Grid& g, const void* F, int64_t F_stride, T* part, double* out, cudaStream_t s) {
+  using C = Cfg<T>;
+  using T2 = typename V2<T>::t;
+  const int L = g.lmax;
+  const int64_t nlm = nlm_of(L);
+  const int nblk = adj_nblk<T>(g);
+  dim3 grd(nblk, L + 1);
+  const T* A = std::is_same<T, double>::value ? (const T*)g.A64.p : (const T*)g.A32.p;
+  const T2* st = std::is_same<T, double>::value ? (const T2*)g.st64.p : (const T2*)g.st32.p;
+  const T* yr = std::is_same<T, double>::value ? (const T*)g.y64.p : (const T*)g.y32.p;
+  {
+    ProfScope ps(PROF_LEG_ADJ, s, sizeof(T) == 8, 4.0 * g.npair * (double)nlm * (NM + 1));
+    k_leg_adj<T, NM, C::AR, C::ANT, C::template ACH<NM>()><<<grd, C::ANT, 0, s>>>(
+        (const T2*)F, F_stride, A, g.ls.as<int>(), st, yr, g.pair_ring.as<int2>(), part, nlm, L,
+        g.npair, g.nring);
+    CMBWS_LAUNCH_CHECK();
+  }
+  dim3 rg((unsigned)((nlm + 255) / 256), NM);
+  ProfScope ps(PROF_LEG_RED, s, sizeof(T) == 8);
+  k_adj_reduce<T><<<rg, 256, 0, s>>>(part, nblk, nlm, NM, g.c64.as<double>(), (double2*)out);
+  CMBWS_LAUNCH_CHECK();
+  return CMBWS_OK;
+}
+
+template <typename T>
+int synth_dispatch(const Grid& g, int nmaps, const void* alm, void* F, cudaStream_t s) {
+  using T2 = typename V2<T>::t;
+  const int64_t as = nlm_of(g.lmax), fs = (int64_t)g.nring * (g.lmax + 1);
+  for (int k0 = 0; k0 < nmaps; k0 += 4) {
+    const int nm = nmaps - k0 < 4 ? nmaps - k0 : 4;
+    const void* a = (const T2*)alm + k0 * as;
+    void* f = (T2*)F + k0 * fs;
+    int st = CMBWS_OK;
+    switch (nm) {
+      case 1: st = launch_synth<T, 1>(g, a, as, f, fs, s); break;
+      case 2: st = launch_synth<T, 2>(g, a, as, f, fs, s); break;
+      case 3: st = launch_synth<T, 3>(g, a, as, f, fs, s); break;
+      default: st = launch_synth<T, 4>(g, a, as, f, fs, s); break;
+    }
+    if (st != CMBWS_OK) return st;
+  }
+  return CMBWS_OK;
+}
+
+template <typename T>
+int adj_dispatch(const Grid& g, int nmaps, const void* F, void* part, double* out, cudaStream_t s) {
+  using T2 = typename V2<T>::t;
+  const int64_t nlm = nlm_of(g.lmax), fs = (int64_t)g.nring * (g.lmax + 1);
+  for (int k0 = 0; k0 < nmaps; k0 += 4) {
+    const int nm = nmaps - k0 < 4 ? nmaps - k0 : 4;
+    const void* f = (const T2*)F + k0 * fs;
+    double* o = out + 2 * k0 * nlm;
+    int st = CMBWS_OK;
+    switch (nm) {
+      case 1: st = launch_adj<T, 1>(g, f, fs, (T*)part, o, s); break;
+      case 2: st = launch_adj<T, 2>(g, f, fs, (T*)part, o, s); break;
+      case 3: st = launch_adj<T, 3>(g, f, fs, (T*)part, o, s); break;
+      default: st = launch_adj<T, 4>(g, f, fs, (T*)part, o, s); break;
+    }
+    if (st != CMBWS_OK) return st;
+  }
+  return CMBWS_OK;
+}
+
+}  // namespace
+
+int legendre_synth(const Grid& g, int prec, int nmaps, const void* alm, void* F, cudaStream_t s) {
+  if (prec == CMBWS_FP64) return synth_dispatch<double>(g, nmaps, alm, F, s);
+  return synth_dispatch<float>(g, nmaps, alm, F, s);
+}
+
+size_t legendre_adjoint_part_bytes(const Grid& g, int prec, int nmaps) {
+  const int nm = nmaps < 4 ? nmaps : 4;
+  const int nblk = prec == CMBWS_FP64 ? adj_nblk<double>(g) : adj_nblk<float>(g);
+  return (size_t)nblk * 2 * nm * nlm_of(g.lmax) * prec_size(prec);
+}
+
+int legendre_adjoint(const Grid& g, int prec, int nmaps, const void* F, void* part,
+                     size_t part_bytes, double* out, cudaStream_t s) {
+  if (part_bytes < legendre_adjoint_part_bytes(g, prec, nmaps)) {
+    set_error("legendre_adjoint: partial-sum buffer too small");
+    return CMBWS_ERR_ARG;
+  }
+  if (prec == CMBWS_FP64) return adj_dispatch<double>(g, nmaps, F, part, out, s);
+  return adj_dispatch<float>(g, nmaps, F, part, out, s);
+}
+
+}  // namespace cmbws

@@ -1,0 +1,85 @@
+// Model object behind cmbws_model: the description of Sec. 2.2 resident on the
+// device, the U^+ blocks of Sec. 3.3 and the workspaces of the apply chains.
+#pragma once
+
+#include <memory>
+
+#include "common.h"
+
+namespace cmbws {
+
+constexpr int kMaxComp = 8;    // components
+constexpr int kMaxBands = 16;  // observations
+constexpr int kMaxMaps = 8;    // bands transformed together on one grid
+
+// Device view of the harmonic-space model tables (kernel argument by value).
+struct HarmDev {
+  int ncomp, nobs, Lup;
+  const int* compL;        // [ncomp] L_k
+  const int64_t* compOff;  // [ncomp] offset of component k in a stacked vector
+  const double* q;         // [nobs][ncomp]
+  const double* beam;      // b_{nu,l} at beam[beamOff[nu] + l]
+  const int64_t* beamOff;
+  const double* cinv;      // C_{k,l}^-1 at cinv[clOff[k] + l] (0 = no prior)
+  const double* cisq;      // C_{k,l}^-1/2
+  const int64_t* clOff;
+  const double* Up;        // U^+ [Lup+1][ncomp][nobs+ncomp]
+};
+
+struct GroupDev {
+  int L, nmaps;
+  int bands[kMaxMaps];
+  const double* c;         // c_lm of the group's grid
+  void* alm;               // group input, internal layout (T2)
+  int64_t nlm;
+};
+
+struct BandDev {
+  int L[kMaxBands];
+  const double2* out[kMaxBands];  // adjoint-chain result of band nu (internal layout, FP64)
+  const double* c[kMaxBands];     // c_lm of band nu's grid
+  void* alm[kMaxBands];           // chain input slot of band nu (T2)
+};
+
+struct Group {
+  Grid* grid = nullptr;
+  int nmaps = 0;
+  int bands[kMaxMaps] = {0};
+  DevMem alm;  // [nmaps][nlm] complex, sized for FP64
+  DevMem F;    // [nmaps][nring][L+1] complex, sized for FP64
+  DevMem out;  // [nmaps][nlm] complex FP64
+};
+
+struct Model {
+  int ncomp = 0, nobs = 0, prec = 0;
+  std::vector<int> Lk, Lnu;
+  std::vector<int64_t> compOff;
+  int64_t nvec = 0;
+  int Lcomp = 0, Lall = 0, Lup = 0;
+  std::vector<Grid*> grids;
+  std::vector<Group> groups;
+  std::vector<int> band_group, band_slot;
+  std::vector<double> alpha;
+  std::vector<DevMem> pixA64, pixA32, pixM64, pixM32, tausq;
+  DevMem d_compL, d_compOff, d_q, d_beam, d_beamOff, d_cinv, d_cisq, d_clOff, d_Up;
+  DevMem part, tprior, zero, pixtmp;
+  int nsht_A = 0, nsht_M = 0;
+  long long n_sht = 0;  // SHTs executed since creation (paper's counting)
+
+  // CG workspace (cg.cu)
+  DevMem cg_r, cg_z, cg_p, cg_q, cg_d, cg_x, cg_red;
+
+  HarmDev harm() const;
+  BandDev bands_dev(int prec) const;
+  int group_chain(Group& G, int prec, int which, cudaStream_t s);
+  int mix_forward(Group& G, int prec, const double* x, cudaStream_t s);
+  int project(const double* x, double* const* d, int prec, cudaStream_t s);
+  int apply_A(const double* x, double* y, int prec, cudaStream_t s);
+  int apply_precond(const double* r, double* z, int prec, cudaStream_t s);
+  int rhs(const double* const* d, const double* const* w1, const double* w2, double* b,
+          cudaStream_t s);
+};
+
+int model_create(const cmbws_model_desc* desc, int prec, cudaStream_t s, Model** out);
+
+}  // namespace cmbws

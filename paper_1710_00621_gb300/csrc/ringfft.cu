@@ -1,0 +1,324 @@
+// Ring FFT stage of the SHT (Sec. 2.1) and the pixel-space multiplies of A
+// (N^-1 = diag(tau), Eq. A) and of T^+ (alpha^2 W N W, Sec. 3.3).
+//
+// Synthesis of one ring with spectrum F_m = (Fc_m, Fs_m), m = 0..L:
+//   f(phi_j) = Fc_0 + sqrt(2) sum_{m>=1} [Fc_m cos(m phi_j) + Fs_m sin(m phi_j)],
+//   phi_j = phi0 + 2 pi j / n.
+// Written as f_j = sum_k H_k exp(2 pi i k j / n) with the Hermitian spectrum
+// H folded modulo n from frequencies -L..L (aliasing included), so f is the
+// length-n inverse DFT of H.  The north and south rings of a pair share n
+// and phi0 and are packed into one complex transform z = f_N + i f_S.  The
+// adjoint (analysis, optionally quadrature-weighted) runs the forward DFT and
+// unfolds Z back to m = 0..L with the exact transposes of these steps.
+//
+// One CTA per (ring pair, map); the DFT runs in shared memory: radix-2 for
+// power-of-two n (equatorial HEALPix rings, polar rings 4i with i a power of
+// two), Bluestein's chirp-z algorithm (a power-of-two convolution of size
+// >= 2n - 1) for every other n (GL rings of 2L+1 pixels, most polar rings).
+// The fused mode goes synthesis -> pixel multiply -> analysis without the
+// pixel map leaving shared memory.
+#include "common.h"
+
+namespace cmbws {
+
+namespace {
+
+template <typename T> struct V2;
+template <> struct V2<double> { using t = double2; };
+template <> struct V2<float> { using t = float2; };
+
+template <typename T2>
+__device__ __forceinline__ T2 cmul(T2 a, T2 b) {
+  T2 r;
+  r.x = a.x * b.x - a.y * b.y;
+  r.y = a.x * b.y + a.y * b.x;
+  return r;
+}
+template <typename T2>
+__device__ __forceinline__ T2 cconj(T2 a) {
+  a.y = -a.y;
+  return a;
+}
+
+__device__ __forceinline__ void sincospi_t(double x, double* s, double* c) { sincospi(x, s, c); }
+__device__ __forceinline__ void sincospi_t(float x, float* s, float* c) { sincospif(x, s, c); }
+
+// In-place radix-2 transform of size N (power of two >= 1) in shared memory.
+// tw[k] = exp(-2 pi i k / NMAX), k < NMAX/2.  inverse: exp(+2 pi i ...), unnormalised.
+template <typename T2>
+__device__ void smem_fft(T2* buf, int N, const T2* __restrict__ tw, int nmax, bool inverse) {
+  if (N < 2) return;
+  const int logN = 31 - __clz(N);
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const int j = (int)(__brev((unsigned)i) >> (32 - logN));
+    if (i < j) {
+      T2 t = buf[i];
+      buf[i] = buf[j];
+      buf[j] = t;
+    }
+  }
+  __syncthreads();
+  for (int lg = 1; lg <= logN; ++lg) {
+    const int half = 1 << (lg - 1);
+    const int tstride = nmax >> lg;
+    for (int b = threadIdx.x; b < N / 2; b += blockDim.x) {
+      const int pos = b & (half - 1);
+      const int i = ((b >> (lg - 1)) << lg) + pos;
+      const int j = i + half;
+      T2 w = tw[pos * tstride];
+      if (inverse) w.y = -w.y;
+      const T2 u = buf[i];
+      const T2 v = cmul(buf[j], w);
+      buf[i].x = u.x + v.x;
+      buf[i].y = u.y + v.y;
+      buf[j].x = u.x - v.x;
+      buf[j].y = u.y - v.y;
+    }
+    __syncthreads();
+  }
+}
+
+enum { MODE_SYNTH = 0, MODE_ANALYSIS = 1, MODE_FUSED = 2 };
+constexpr int kMaxPix = 8;
+
+template <typename T>
+struct PixPtrs {
+  const T* p[kMaxPix];
+};
+
+// Forward DFT of z[0..n) held in buf (Bluestein needs buf of n2); result Z[0..n) in buf.
+template <typename T2>
+__device__ void dft_forward(T2* buf, const FftPlan& P, const T2* __restrict__ tab, int64_t tw_off,
+                            int nmax) {
+  if (!P.bluestein) {
+    smem_fft(buf, P.n, tab + tw_off, nmax, false);
+    return;
+  }
+  const T2* b = tab + P.chirp;
+  const T2* V = tab + P.filt;
+  for (int t = threadIdx.x; t < P.n2; t += blockDim.x) {
+    if (t < P.n) buf[t] = cmul(buf[t], cconj(b[t]));
+    else buf[t].x = buf[t].y = 0;
+  }
+  __syncthreads();
+  smem_fft(buf, P.n2, tab + tw_off, nmax, false);
+  for (int t = threadIdx.x; t < P.n2; t += blockDim.x) buf[t] = cmul(buf[t], V[t]);
+  __syncthreads();
+  smem_fft(buf, P.n2, tab + tw_off, nmax, true);
+  for (int t = threadIdx.x; t < P.n; t += blockDim.x) buf[t] = cmul(buf[t], cconj(b[t]));
+  __syncthreads();
+}
+
+// Inverse (unnormalised) DFT of Z[0..n) in buf; result z[0..n) in buf.
+template <typename T2>
+__device__ void dft_inverse(T2* buf, const FftPlan& P, const T2* __restrict__ tab, int64_t tw_off,
+                            int nmax) {
+  if (!P.bluestein) {
+    smem_fft(buf, P.n, tab + tw_off, nmax, true);
+    return;
+  }
+  // z = conj(DFT(conj(Z)))
+  for (int t = threadIdx.x; t < P.n; t += blockDim.x) buf[t] = cconj(buf[t]);
+  __syncthreads();
+  dft_forward(buf, P, tab, tw_off, nmax);
+  for (int t = threadIdx.x; t < P.n; t += blockDim.x) buf[t] = cconj(buf[t]);
+  __syncthreads();
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256)
+k_ringfft(typename V2<T>::t* __restrict__ F, int64_t F_stride, double* __restrict__ map_out,
+          const double* __restrict__ map_in, int64_t npix, const T* __restrict__ ring_w,
+          PixPtrs<T> pix, const FftPlan* __restrict__ plans, const int* __restrict__ pair_plan,
+          const int2* __restrict__ pring, const int* __restrict__ pphase,
+          const int64_t* __restrict__ roff, const typename V2<T>::t* __restrict__ tab,
+          int64_t tw_off, int nmax, int L) {
+  using T2 = typename V2<T>::t;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T2* buf = reinterpret_cast<T2*>(smem_raw);
+
+  const int p = blockIdx.x;
+  const int k = blockIdx.y;
+  const FftPlan P = plans[pair_plan[p]];
+  const int n = P.n;
+  const int2 rr = pring[p];
+  const bool has_s = rr.y >= 0;
+  const int ph = pphase[p];
+  T2* FN = F + k * F_stride + (int64_t)rr.x * (L + 1);
+  T2* FS = has_s ? F + k * F_stride + (int64_t)rr.y * (L + 1) : nullptr;
+  const int64_t offN = roff[rr.x];
+  const int64_t offS = has_s ? roff[rr.y] : 0;
+  const T rs2 = T(0.70710678118654752440);  // 1/sqrt(2)
+  const T sq2 = T(1.41421356237309504880);
+
+  if (MODE == MODE_SYNTH || MODE == MODE_FUSED) {
+    // fold the two-sided spectrum modulo n
+    for (int kk = threadIdx.x; kk < n; kk += blockDim.x) {
+      T hnx = 0, hny = 0, hsx = 0, hsy = 0;
+      if (kk == 0) {
+        hnx = FN[0].x;
+        if (has_s) hsx = FS[0].x;
+      }
+      // +m frequencies, m = kk (mod n), m >= 1
+      for (int m = (kk == 0 ? n : kk); m <= L; m += n) {
+        T c = 1, s = 0;
+        if (ph) sincospi_t(T(m % (2 * n)) / T(n), &s, &c);
+        const T2 a = FN[m];
+        // q = (Fc - i Fs) e^{i m phi0} / sqrt(2)
+        hnx += rs2 * (a.x * c + a.y * s);
+        hny += rs2 * (a.x * s - a.y * c);
+        if (has_s) {
+          const T2 b = FS[m];
+          hsx += rs2 * (b.x * c + b.y * s);
+          hsy += rs2 * (b.x * s - b.y * c);
+        }
+      }
+      // -m frequencies: m = -kk (mod n), m >= 1, conj(q)
+      for (int m = (kk == 0 ? n : n - kk); m <= L; m += n) {
+        T c = 1, s = 0;
+        if (ph) sincospi_t(T(m % (2 * n)) / T(n), &s, &c);
+        const T2 a = FN[m];
+        hnx += rs2 * (a.x * c + a.y * s);
+        hny -= rs2 * (a.x * s - a.y * c);
+        if (has_s) {
+          const T2 b = FS[m];
+          hsx += rs2 * (b.x * c + b.y * s);
+          hsy -= rs2 * (b.x * s - b.y * c);
+        }
+      }
+      T2 z;
+      z.x = hnx - hsy;
+      z.y = hny + hsx;
+      buf[kk] = z;
+    }
+    __syncthreads();
+    dft_inverse(buf, P, tab, tw_off, nmax);
+    if (MODE == MODE_SYNTH) {
+      double* mo = map_out + k * npix;
+      for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const T2 z = buf[j];
+        mo[offN + j] = (double)z.x;
+        if (has_s) mo[offS + j] = (double)z.y;
+      }
+      return;
+    }
+    // pixel multiply in place
+    const T* pk = pix.p[k];
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      T2 z = buf[j];
+      z.x *= pk[offN + j];
+      z.y = has_s ? z.y * pk[offS + j] : T(0);
+      buf[j] = z;
+    }
+    __syncthreads();
+  } else {
+    // analysis: load (optionally weighted) pixels
+    const double* mi = map_in + k * npix;
+    const T wN = ring_w ? ring_w[rr.x] : T(1);
+    const T wS = (ring_w && has_s) ? ring_w[rr.y] : T(1);
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      T2 z;
+      z.x = (T)mi[offN + j] * wN;
+      z.y = has_s ? (T)mi[offS + j] * wS : T(0);
+      buf[j] = z;
+    }
+    __syncthreads();
+  }
+
+  dft_forward(buf, P, tab, tw_off, nmax);
+
+  // unfold: G_m = exp(-i m phi0) X_{m mod n}; (Fc^T, Fs^T) = c_m (Re G, -Im G)
+  for (int m = threadIdx.x; m <= L; m += blockDim.x) {
+    const int kk = m % n;
+    const int kc = (kk == 0) ? 0 : n - kk;
+    const T2 zk = buf[kk];
+    const T2 zc = cconj(buf[kc]);
+    T xnx = T(0.5) * (zk.x + zc.x), xny = T(0.5) * (zk.y + zc.y);
+    T xsx = T(0.5) * (zk.y - zc.y), xsy = T(-0.5) * (zk.x - zc.x);
+    T c = 1, s = 0;
+    if (ph) sincospi_t(T(m % (2 * n)) / T(n), &s, &c);
+    const T cm = m == 0 ? T(1) : sq2;
+    // G = (c - i s) X
+    T gx = c * xnx + s * xny, gy = c * xny - s * xnx;
+    T2 o;
+    o.x = cm * gx;
+    o.y = -cm * gy;
+    if (m == 0) o.y = 0;
+    FN[m] = o;
+    if (has_s) {
+      gx = c * xsx + s * xsy;
+      gy = c * xsy - s * xsx;
+      o.x = cm * gx;
+      o.y = m == 0 ? T(0) : -cm * gy;
+      FS[m] = o;
+    }
+  }
+}
+
+template <typename T>
+size_t smem_bytes(const Grid& g) {
+  return (size_t)g.nmax2 * sizeof(typename V2<T>::t);
+}
+
+template <typename T, int MODE>
+int launch(const Grid& g, int nmaps, void* F, double* map_out, const double* map_in, int weighted,
+           const void* const* pix, cudaStream_t s) {
+  using T2 = typename V2<T>::t;
+  const size_t sm = smem_bytes<T>(g);
+  if (sm > 227 * 1024) {
+    set_error("ring FFT needs %zu bytes of shared memory (ring length %d) at this precision",
+              sm, g.max_n);
+    return CMBWS_ERR_ARG;
+  }
+  auto kern = k_ringfft<T, MODE>;
+  CMBWS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  const int64_t fs = (int64_t)g.nring * (g.lmax + 1);
+  const bool dbl = sizeof(T) == 8;
+  const T* rw = nullptr;
+  if (MODE == MODE_ANALYSIS && weighted) rw = dbl ? (const T*)g.ring_w64.p : (const T*)g.ring_w32.p;
+  const T2* tab = dbl ? (const T2*)g.fft64.p : (const T2*)g.fft32.p;
+  for (int k0 = 0; k0 < nmaps; k0 += kMaxPix) {
+    const int nm = nmaps - k0 < kMaxPix ? nmaps - k0 : kMaxPix;
+    PixPtrs<T> pp{};
+    if (MODE == MODE_FUSED)
+      for (int i = 0; i < nm; ++i) pp.p[i] = (const T*)pix[k0 + i];
+    dim3 grd(g.npair, nm);
+    ProfScope ps(PROF_FFT, s, dbl);
+    kern<<<grd, 256, sm, s>>>((T2*)F + k0 * fs, fs, map_out ? map_out + k0 * g.npix : nullptr,
+                              map_in ? map_in + k0 * g.npix : nullptr, g.npix, rw, pp,
+                              g.plans_d.as<FftPlan>(), g.pair_plan.as<int>(),
+                              g.pair_ring.as<int2>(), g.pair_phase.as<int>(), g.ring_off.as<int64_t>(),
+                              tab, g.tw_off, g.nmax2, g.lmax);
+    CMBWS_LAUNCH_CHECK();
+  }
+  return CMBWS_OK;
+}
+
+}  // namespace
+
+int ringfft_smem_ok(const Grid& g, int prec) {
+  const size_t sm = prec == CMBWS_FP64 ? smem_bytes<double>(g) : smem_bytes<float>(g);
+  return sm <= 227 * 1024;
+}
+
+int ringfft_synth(const Grid& g, int prec, int nmaps, const void* F, double* map, cudaStream_t s) {
+  if (prec == CMBWS_FP64)
+    return launch<double, MODE_SYNTH>(g, nmaps, const_cast<void*>(F), map, nullptr, 0, nullptr, s);
+  return launch<float, MODE_SYNTH>(g, nmaps, const_cast<void*>(F), map, nullptr, 0, nullptr, s);
+}
+
+int ringfft_analysis(const Grid& g, int prec, int nmaps, const double* map, int weighted, void* F,
+                     cudaStream_t s) {
+  if (prec == CMBWS_FP64)
+    return launch<double, MODE_ANALYSIS>(g, nmaps, F, nullptr, map, weighted, nullptr, s);
+  return launch<float, MODE_ANALYSIS>(g, nmaps, F, nullptr, map, weighted, nullptr, s);
+}
+
+int ringfft_fused(const Grid& g, int prec, int nmaps, void* F, const void* const* pix,
+                  cudaStream_t s) {
+  if (prec == CMBWS_FP64)
+    return launch<double, MODE_FUSED>(g, nmaps, F, nullptr, nullptr, 0, pix, s);
+  return launch<float, MODE_FUSED>(g, nmaps, F, nullptr, nullptr, 0, pix, s);
+}
+
+}  // namespace cmbws

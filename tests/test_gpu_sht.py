@@ -1,0 +1,145 @@
+"""GPU parity of the SHT stages (Legendre + ring FFT) against the oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+import paper_1710_00621_gb300 as cw
+from oracle import grids as og, sht as osht
+from tests._gpu import rel_err, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+TOL = {cw.CMBWS_FP64: 1e-11, cw.CMBWS_FP32: 3e-5}
+
+# (kind, n, lmax): tiny, ragged, several CTAs of the Legendre kernels, folded spectra
+CASES = [
+    ("gl", 0, 0), ("gl", 1, 1), ("gl", 63, 63), ("gl", 100, 100), ("gl", 40, 31),
+    ("hp", 1, 2), ("hp", 4, 11), ("hp", 8, 40), ("hp", 16, 47), ("hp", 64, 191),
+]
+
+
+def _grids(kind, n, lmax):
+    if kind == "gl":
+        return cw.cmbws_plan_grid(cw.CMBWS_GRID_GL, n + 1, lmax), og.gauss_legendre(n) if n >= lmax else None
+    return cw.cmbws_plan_grid(cw.CMBWS_GRID_HEALPIX, n, lmax), og.healpix(n)
+
+
+def _oracle_grid(kind, n, lmax, g):
+    if kind == "gl":
+        # GL ring count n+1 with 2 lmax + 1 pixels per ring
+        x, w = np.polynomial.legendre.leggauss(n + 1)
+        o = np.argsort(-x)
+        nphi = np.full(n + 1, 2 * lmax + 1)
+        return og.RingGrid("gl", n + 1, np.arccos(x[o]), np.zeros(n + 1), nphi,
+                           w[o] * 2 * np.pi / (2 * lmax + 1), np.concatenate([[0], np.cumsum(nphi)]))
+    return og.healpix(n)
+
+
+@pytest.mark.parametrize("kind,n,lmax", CASES)
+def test_grid_geometry_matches_oracle(kind, n, lmax):
+    g, _ = _grids(kind, n, lmax)
+    o = _oracle_grid(kind, n, lmax, g)
+    np.testing.assert_allclose(g.theta, o.theta, rtol=0, atol=2e-14)
+    np.testing.assert_allclose(g.weight, o.weight, rtol=1e-12)
+    np.testing.assert_allclose(g.phi0, o.phi0, atol=1e-15)
+    np.testing.assert_array_equal(g.nphi, o.nphi)
+    assert g.npix == o.npix
+
+
+@pytest.mark.parametrize("prec", [cw.CMBWS_FP64, cw.CMBWS_FP32])
+@pytest.mark.parametrize("kind,n,lmax", CASES)
+def test_synthesis_parity(kind, n, lmax, prec):
+    g, _ = _grids(kind, n, lmax)
+    o = _oracle_grid(kind, n, lmax, g)
+    rng = np.random.default_rng(lmax + 7 * n)
+    nmaps = 3
+    alm = rng.standard_normal((nmaps, (lmax + 1) ** 2))
+    out = to_dev(np.zeros((nmaps, g.npix)))
+    cw.cmbws_sht_synth(g, prec, to_dev(alm), out, nmaps)
+    got = to_host(out)
+    for k in range(nmaps):
+        ref = osht.synthesis(o, lmax, alm[k])
+        assert rel_err(got[k], ref) < TOL[prec], (k, rel_err(got[k], ref))
+
+
+@pytest.mark.parametrize("weighted", [0, 1])
+@pytest.mark.parametrize("prec", [cw.CMBWS_FP64, cw.CMBWS_FP32])
+@pytest.mark.parametrize("kind,n,lmax", CASES)
+def test_adjoint_parity(kind, n, lmax, prec, weighted):
+    g, _ = _grids(kind, n, lmax)
+    o = _oracle_grid(kind, n, lmax, g)
+    rng = np.random.default_rng(1000 + lmax + 7 * n)
+    nmaps = 2
+    maps = rng.standard_normal((nmaps, g.npix))
+    out = to_dev(np.zeros((nmaps, (lmax + 1) ** 2)))
+    cw.cmbws_sht_analysis(g, prec, to_dev(maps), out, nmaps, weighted)
+    got = to_host(out)
+    for k in range(nmaps):
+        ref = osht.adjoint(o, lmax, maps[k], weighted=bool(weighted))
+        assert rel_err(got[k], ref) < TOL[prec], (k, rel_err(got[k], ref))
+
+
+@pytest.mark.parametrize("nmaps", [1, 4, 5, 9])
+def test_map_batches_of_any_size(nmaps):
+    g = cw.cmbws_plan_grid(cw.CMBWS_GRID_HEALPIX, 8, 23)
+    o = og.healpix(8)
+    alm = np.random.default_rng(nmaps).standard_normal((nmaps, 24 ** 2))
+    out = to_dev(np.zeros((nmaps, g.npix)))
+    cw.cmbws_sht_synth(g, cw.CMBWS_FP64, to_dev(alm), out, nmaps)
+    got = to_host(out)
+    back = to_dev(np.zeros((nmaps, 24 ** 2)))
+    cw.cmbws_sht_analysis(g, cw.CMBWS_FP64, out, back, nmaps, 0)
+    gb = to_host(back)
+    for k in range(nmaps):
+        assert rel_err(got[k], osht.synthesis(o, 23, alm[k])) < 1e-11
+        assert rel_err(gb[k], osht.adjoint(o, 23, got[k])) < 1e-11
+
+
+@pytest.mark.parametrize("lmax", [31, 255, 1023])
+def test_gl_round_trip_exact_on_gpu(lmax):
+    # Sec. 2.1: Y^T W Y = I on the Gauss-Legendre grid
+    g = cw.cmbws_plan_grid(cw.CMBWS_GRID_GL, lmax + 1, lmax)
+    a = np.random.default_rng(lmax).standard_normal((lmax + 1) ** 2)
+    m = to_dev(np.zeros(g.npix))
+    back = to_dev(np.zeros((lmax + 1) ** 2))
+    cw.cmbws_sht_synth(g, cw.CMBWS_FP64, to_dev(a), m, 1)
+    cw.cmbws_sht_analysis(g, cw.CMBWS_FP64, m, back, 1, 1)
+    assert rel_err(to_host(back), a) < 1e-11
+    cw.cmbws_sht_synth(g, cw.CMBWS_FP32, to_dev(a), m, 1)
+    cw.cmbws_sht_analysis(g, cw.CMBWS_FP32, m, back, 1, 1)
+    assert rel_err(to_host(back), a) < 1e-4
+
+
+def test_adjointness_large_healpix():
+    # <Y a, f> = <a, Y^T f> at Nside 256, L = 767 (several CTAs per m in both Legendre kernels)
+    g = cw.cmbws_plan_grid(cw.CMBWS_GRID_HEALPIX, 256, 767)
+    rng = np.random.default_rng(5)
+    a = rng.standard_normal(768 ** 2)
+    f = rng.standard_normal(g.npix)
+    ya = to_dev(np.zeros(g.npix))
+    ytf = to_dev(np.zeros(768 ** 2))
+    cw.cmbws_sht_synth(g, cw.CMBWS_FP64, to_dev(a), ya, 1)
+    cw.cmbws_sht_analysis(g, cw.CMBWS_FP64, to_dev(f), ytf, 1, 0)
+    lhs = float(to_host(ya) @ f)
+    rhs = float(a @ to_host(ytf))
+    assert abs(lhs - rhs) <= 1e-10 * abs(lhs)
+
+
+def test_full_size_sampled_rings_nside1024():
+    # Nside 1024, L = 3071 (the largest band grid of the multi-resolution workload):
+    # the synthesis of a few rings recomputed by the oracle on a sub-grid of those rings
+    g = cw.cmbws_plan_grid(cw.CMBWS_GRID_HEALPIX, 1024, 3071)
+    o = og.healpix(1024)
+    L = 3071
+    rng = np.random.default_rng(11)
+    ell = np.concatenate([np.arange(L + 1)] + [np.r_[np.arange(m, L + 1), np.arange(m, L + 1)]
+                                               for m in range(1, L + 1)])
+    a = rng.standard_normal((L + 1) ** 2) / (1.0 + ell)
+    out = to_dev(np.zeros(g.npix))
+    cw.cmbws_sht_synth(g, cw.CMBWS_FP64, to_dev(a), out, 1)
+    got = to_host(out)
+    rings = np.array([0, 1, 5, 700, 1023, 1500, 2047, 2600, 4094])
+    sub = og.RingGrid("healpix", 1024, o.theta[rings], o.phi0[rings], o.nphi[rings], o.weight[rings],
+                      np.concatenate([[0], np.cumsum(o.nphi[rings])]))
+    ref = osht.synthesis(sub, L, a)
+    gsub = np.concatenate([got[o.offset[r]:o.offset[r + 1]] for r in rings])
+    assert rel_err(gsub, ref) < 1e-10

@@ -1,0 +1,144 @@
+"""GPU parity of A, M_PI, the RHS and the PCG solve against the oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+import paper_1710_00621_gb300 as cw
+import skygen
+from oracle import closed_form, model as om, precond as opc
+from oracle.cg import pcg
+from tests._gpu import GridCache, gpu_model, rel_err, to_dev, to_host
+from tests._models import multires_small, oracle_model, tiny_workload
+
+pytestmark = pytest.mark.gpu
+
+TOL = {cw.CMBWS_FP64: 1e-10, cw.CMBWS_FP32: 1e-4}
+
+
+def _setups():
+    out = {}
+    out["tiny15"] = tiny_workload(15)
+    out["multires64"] = multires_small(64)
+    out["multires16"] = multires_small(16)     # Nside 16/32/64, L_nu up to 191, comps 125/31/187
+    return out
+
+
+SETUPS = _setups()
+
+
+@pytest.fixture(scope="module")
+def models():
+    cache = {}
+    for name, work in SETUPS.items():
+        om_, inp = oracle_model(work)
+        cache[name] = (work, om_, inp)
+    return cache
+
+
+@pytest.mark.parametrize("prec", [cw.CMBWS_FP64, cw.CMBWS_FP32])
+@pytest.mark.parametrize("name", list(SETUPS))
+def test_apply_A_parity(models, name, prec):
+    work, m, inp = models[name]
+    g, _ = gpu_model(work, inp, prec)
+    x = np.random.default_rng(1).standard_normal(m.nvec())
+    y = to_dev(np.zeros(m.nvec()))
+    cw.cmbws_apply_A(g, to_dev(x), y)
+    assert rel_err(to_host(y), om.apply_A(m, x)) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [cw.CMBWS_FP64, cw.CMBWS_FP32])
+@pytest.mark.parametrize("name", list(SETUPS))
+def test_apply_precond_parity(models, name, prec):
+    work, m, inp = models[name]
+    g, _ = gpu_model(work, inp, prec)
+    r = np.random.default_rng(2).standard_normal(m.nvec())
+    z = to_dev(np.zeros(m.nvec()))
+    cw.cmbws_apply_precond(g, to_dev(r), z)
+    assert rel_err(to_host(z), opc.apply_precond(m, r)) < TOL[prec]
+
+
+def test_model_counts_shts_like_the_paper(models):
+    # Sec. 3.3: A costs 2 (2 Nmix + Nobs) SHTs, M_PI costs 2 Nobs; scalar mixing has Nmix = 0
+    work, m, inp = models["multires64"]
+    g, _ = gpu_model(work, inp)
+    assert g.nsht_A == 2 * 9 and g.nsht_M == 2 * 9
+    assert g.nvec == m.nvec()
+
+
+@pytest.mark.parametrize("name", ["tiny15", "multires64"])
+def test_rhs_parity(models, name):
+    work, m, inp = models[name]
+    g, grids = gpu_model(work, inp)
+    d = [mp + n for mp, n in zip(om.project(m, inp["x_true"]), inp["noise"])]
+    rng = np.random.default_rng(3)
+    w1 = [rng.standard_normal(x.size) for x in d]
+    w2 = rng.standard_normal(m.nvec())
+    b = to_dev(np.zeros(m.nvec()))
+    cw.cmbws_rhs(g, [to_dev(x) for x in d], b)
+    assert rel_err(to_host(b), om.rhs(m, d)) < 1e-10
+    cw.cmbws_rhs(g, [to_dev(x) for x in d], b, omega1=[to_dev(x) for x in w1], omega2=to_dev(w2))
+    assert rel_err(to_host(b), om.rhs(m, d, w1, w2)) < 1e-10
+
+
+def test_flat_noise_solve_is_closed_form_in_one_iteration():
+    work = tiny_workload(31)
+    m, inp = oracle_model(work, flat=True)
+    g, _ = gpu_model(work, inp)
+    sig = [b.sigma for b in work.bands]
+    b = np.random.default_rng(4).standard_normal(m.nvec())
+    ref = closed_form.solve(m.lmax_comp, m.lmax_band, m.beam, m.cl, m.q, sig, b)
+    x = to_dev(np.zeros(m.nvec()))
+    rep = cw.cmbws_cg_solve(g, to_dev(b), x, tol=1e-10, maxiter=50)
+    assert rep["iters"] == 1
+    assert rel_err(to_host(x), ref) < 1e-10
+
+
+def test_tiny_plain_workload_solve_matches_oracle():
+    # Ncomp 2, Nobs 3, GL L = 63 (64 x 127 px), tol 1e-8, b = A x_true (Sec. 2.3 error tracking)
+    work = skygen.tiny_plain()
+    m, inp = oracle_model(work)
+    g, _ = gpu_model(work, inp)
+    b = om.apply_A(m, inp["x_true"])
+    x = to_dev(np.zeros(m.nvec()))
+    rep = cw.cmbws_cg_solve(g, to_dev(b), x, tol=1e-8, maxiter=500)
+    assert rep["rel_res"] <= 1e-8
+    xo, info = pcg(lambda v: om.apply_A(m, v), b, lambda v: opc.apply_precond(m, v), tol=1e-12)
+    assert rel_err(to_host(x), xo) < 1e-6
+    assert abs(rep["iters"] - info["iters"]) <= 3 or rep["iters"] <= info["iters"]
+
+
+@pytest.mark.parametrize("name", ["multires64"])
+def test_wiener_solve_fp64_and_fp32_refined(models, name):
+    work, m, inp = models[name]
+    d = [mp + n for mp, n in zip(om.project(m, inp["x_true"]), inp["noise"])]
+    b = om.rhs(m, d)
+    xo, _ = pcg(lambda v: om.apply_A(m, v), b, lambda v: opc.apply_precond(m, v), tol=1e-12,
+                maxiter=2000)
+    for prec in (cw.CMBWS_FP64, cw.CMBWS_FP32):
+        g, _ = gpu_model(work, inp, prec)
+        x = to_dev(np.zeros(m.nvec()))
+        rep = cw.cmbws_cg_solve(g, to_dev(b), x, tol=1e-6, maxiter=2000, inner_tol=1e-3)
+        assert rep["rel_res"] <= 1e-6
+        # relative error vs the FP64 oracle solution, bounded by cond * tol
+        assert rel_err(to_host(x), xo) < 1e-4, (prec, rep)
+
+
+def test_invalid_calls_return_error_codes(models):
+    work, m, inp = models["tiny15"]
+    g, grids = gpu_model(work, inp)
+    x = to_dev(np.zeros(m.nvec()))
+    with pytest.raises(cw.CmbwsError) as e:
+        cw.cmbws_apply_A(g, x, x)
+    assert e.value.code == -1
+    with pytest.raises(cw.CmbwsError):
+        cw.cmbws_plan_grid(cw.CMBWS_GRID_GL, 3, 10)       # fewer rings than lmax + 1
+    # a component with neither prior nor data at some l is rejected (zero column of U)
+    inp2 = dict(inp)
+    inp2["cl"] = [None, None]
+    inp2["beams"] = [np.where(np.arange(b.size) > 10, 0.0, b) for b in inp["beams"]]
+    with pytest.raises(cw.CmbwsError) as e:
+        gpu_model(work, inp2)
+    assert e.value.code == -4
+    # iteration cap -> NOT_CONVERGED with the report filled
+    b = to_dev(np.random.default_rng(9).standard_normal(m.nvec()))
+    rep = cw.cmbws_cg_solve(g, b, x, tol=1e-14, maxiter=2, check=False)
+    assert rep["code"] == -6 and rep["iters"] == 2
