@@ -238,8 +238,15 @@ static int cg_solve_impl(Model& M, const double* b, double* x, const cmbws_cg_op
     rep.rel_res = 0.0;
     return CMBWS_OK;
   }
-  double rr;
-  CMBWS_TRY(S.true_residual(b, x, r, tmp, &rr));
+  double rr, xx;
+  CMBWS_TRY(S.dot(x, x, &xx));
+  if (xx == 0.0) {
+    // x0 = 0: r = b without an apply of A
+    CMBWS_CUDA(cudaMemcpyAsync(r, b, n * 8, cudaMemcpyDeviceToDevice, s));
+    rr = bb;
+  } else {
+    CMBWS_TRY(S.true_residual(b, x, r, tmp, &rr));
+  }
   int status = CMBWS_ERR_NOT_CONVERGED;
   int total = 0, outer = 0;
   const double target = o.tol * bnorm;

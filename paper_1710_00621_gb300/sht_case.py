@@ -1,0 +1,65 @@
+"""Run and time one transform case of the library (used for kernel profiling).
+
+    python -m paper_1710_00621_gb300.sht_case --grid healpix --n 1024 --lmax 3071 \
+        --nmaps 3 --prec fp32 --op both --reps 3
+
+Plans the grid, fills random band-limited coefficients / maps on the device, runs the
+requested transforms `reps` times and prints the per-call time from CUDA events and the
+library's per-stage kernel timing.
+"""
+import argparse
+import json
+import os
+import sys
+
+import numpy as np
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+
+def main():
+    import torch
+
+    import paper_1710_00621_gb300 as cw
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--grid", default="healpix", choices=["healpix", "gl"])
+    ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--lmax", type=int, default=3071)
+    ap.add_argument("--nmaps", type=int, default=3)
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--op", default="both", choices=["synth", "analysis", "both"])
+    ap.add_argument("--reps", type=int, default=3)
+    a = ap.parse_args()
+    kind = cw.CMBWS_GRID_HEALPIX if a.grid == "healpix" else cw.CMBWS_GRID_GL
+    g = cw.cmbws_plan_grid(kind, a.n if a.grid == "healpix" else a.n + 1, a.lmax)
+    prec = cw.CMBWS_FP32 if a.prec == "fp32" else cw.CMBWS_FP64
+    nalm = (a.lmax + 1) ** 2
+    dev = torch.device("cuda")
+    gen = torch.Generator(device=dev).manual_seed(0)
+    alm = torch.randn(a.nmaps * nalm, dtype=torch.float64, device=dev, generator=gen)
+    maps = torch.empty(a.nmaps * g.npix, dtype=torch.float64, device=dev)
+    back = torch.empty_like(alm)
+    cw.cmbws_sht_synth(g, prec, alm, maps, a.nmaps)
+    torch.cuda.synchronize()
+    cw.cmbws_profile_read(reset=True)
+    cw.cmbws_profile_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.reps):
+        if a.op in ("synth", "both"):
+            cw.cmbws_sht_synth(g, prec, alm, maps, a.nmaps)
+        if a.op in ("analysis", "both"):
+            cw.cmbws_sht_analysis(g, prec, maps, back, a.nmaps, 1)
+    e1.record()
+    torch.cuda.synchronize()
+    cw.cmbws_profile_enable(False)
+    prof = cw.cmbws_profile_read(reset=True)
+    out = {"case": vars(a), "ms_per_rep": e0.elapsed_time(e1) / a.reps,
+           "stages": {f"{k[0]}_{k[1]}": {"ms": round(v[0], 3), "launches": v[1],
+                                          "tflops": round(v[2] / (v[0] * 1e-3) / 1e12, 3) if v[0] else 0}
+                      for k, v in prof.items() if v[1]}}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()
