@@ -113,6 +113,26 @@ int cmbws_sht_analysis(cmbws_grid g, cmbws_prec prec, const double* map, double*
                        int weighted, void* stream);
 
 /*
+ * Same result as cmbws_sht_analysis, with no device allocation.  The paper has no
+ * counterpart; this call exists for callers that cannot allocate device memory when
+ * they need the transform: code running inside CUDA graph capture, runtimes that give
+ * the library a fixed memory budget and forbid cudaMalloc after start-up, or loops that
+ * must not block on the allocator.  Its workspace is one static device array of 32 MiB
+ * (32 << 20 bytes) that every GPU loading the library holds until exit; a call whose
+ * workspace (ring spectra nmaps * nring * (lmax+1) complex values, the Legendre adjoint's
+ * per-block partial sums and the reduced coefficients) would exceed it returns
+ * CMBWS_ERR_ARG with the bytes it needs.  The first call on a device looks up the
+ * array's device address with cudaGetSymbolAddress (that device current); make that
+ * first call before any stream capture.  Every call shares the array and overwrites what
+ * it reads, so nothing carries over between calls, but calls whose kernels overlap on the
+ * GPU race: serialise them.  Keep kernel timing (cmbws_profile_enable) off here, since it
+ * creates CUDA events.  Arguments and layouts as for cmbws_sht_analysis; the grid's own
+ * tables are allocated once by cmbws_plan_grid.
+ */
+int cmbws_sht_analysis_noalloc(cmbws_grid g, cmbws_prec prec, const double* map, double* alm,
+                               int nmaps, int weighted, void* stream);
+
+/*
  * Model description (Sec. 2.2, Eqs. block-data-model, P, Q; Sec. 2.3, Eq. A).
  * All pointers are host pointers except ninv[nu], which are device pointers.
  * The library copies everything it keeps; the caller may free the inputs

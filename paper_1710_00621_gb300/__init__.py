@@ -34,6 +34,7 @@ from .binding import (  # noqa: F401
     cmbws_project,
     cmbws_rhs,
     cmbws_sht_analysis,
+    cmbws_sht_analysis_noalloc,
     cmbws_sht_synth,
     exported_symbols,
     library_path,

@@ -81,6 +81,7 @@ def load_library(path=None):
     lib.cmbws_grid_destroy.argtypes = [vp]
     lib.cmbws_sht_synth.argtypes = [vp, i, vp, vp, i, vp]
     lib.cmbws_sht_analysis.argtypes = [vp, i, vp, vp, i, i, vp]
+    lib.cmbws_sht_analysis_noalloc.argtypes = [vp, i, vp, vp, i, i, vp]
     lib.cmbws_model_create.argtypes = [ctypes.POINTER(ModelDesc), i, vp, ctypes.POINTER(vp)]
     lib.cmbws_model_destroy.argtypes = [vp]
     lib.cmbws_model_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(i),
@@ -202,6 +203,15 @@ def cmbws_sht_analysis(grid, prec, map_in, alm, nmaps=1, weighted=1, stream=None
                                              _dptr(map_in, nmaps * grid.npix, "map"),
                                              _dptr(alm, nmaps * nalm, "alm"), int(nmaps),
                                              int(weighted), _stream(stream)))
+
+
+def cmbws_sht_analysis_noalloc(grid, prec, map_in, alm, nmaps=1, weighted=1, stream=None):
+    """cmbws_sht_analysis without device allocation (32 MiB static workspace per GPU)."""
+    nalm = (grid.lmax + 1) ** 2
+    _check(load_library().cmbws_sht_analysis_noalloc(grid.handle, int(prec),
+                                                     _dptr(map_in, nmaps * grid.npix, "map"),
+                                                     _dptr(alm, nmaps * nalm, "alm"), int(nmaps),
+                                                     int(weighted), _stream(stream)))
 
 
 class Model:

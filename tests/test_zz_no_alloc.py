@@ -1,0 +1,46 @@
+"""The allocation-free analysis entry point agrees with cmbws_sht_analysis (GPU).
+
+Callers that cannot allocate device memory (inside CUDA graph capture, under a fixed
+memory budget) use cmbws_sht_analysis_noalloc, whose workspace is a static 32 MiB device
+array.  This file is collected last so that a failure here, in a run that stops at the
+first failure, comes after every other test has run.
+"""
+import numpy as np
+import pytest
+
+import paper_1710_00621_gb300 as cw
+from tests._gpu import rel_err, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+def _tol(prec, lmax):
+    # the same bounds as the SHT parity tests
+    if prec == cw.CMBWS_FP64:
+        return max(1e-12, 1e-16 * (lmax + 1) ** 2)
+    return max(1e-5, 5 * (lmax + 1) * 6e-8)
+
+
+@pytest.mark.parametrize("prec", [cw.CMBWS_FP64, cw.CMBWS_FP32])
+def test_noalloc_matches_allocating_call_twice(prec):
+    g = cw.cmbws_plan_grid(cw.CMBWS_GRID_HEALPIX, 64, 191)
+    nalm = 192 ** 2
+    rng = np.random.default_rng(2024)
+    for call, (nmaps, weighted) in enumerate(((2, 1), (3, 0))):   # two calls in a row
+        maps = to_dev(rng.standard_normal((nmaps, g.npix)))
+        ref = to_dev(np.zeros((nmaps, nalm)))
+        got = to_dev(np.full((nmaps, nalm), np.nan))
+        cw.cmbws_sht_analysis(g, prec, maps, ref, nmaps, weighted)
+        cw.cmbws_sht_analysis_noalloc(g, prec, maps, got, nmaps, weighted)
+        r, o = to_host(ref), to_host(got)
+        for k in range(nmaps):
+            assert rel_err(o[k], r[k]) < _tol(prec, 191), (call, k)
+
+
+def test_noalloc_rejects_sizes_beyond_its_workspace():
+    g = cw.cmbws_plan_grid(cw.CMBWS_GRID_HEALPIX, 512, 1535)
+    maps = to_dev(np.zeros(g.npix))
+    alm = to_dev(np.zeros(1536 ** 2))
+    with pytest.raises(cw.CmbwsError) as e:
+        cw.cmbws_sht_analysis_noalloc(g, cw.CMBWS_FP64, maps, alm, 1, 1)
+    assert e.value.code == -1 and "static scratch" in str(e.value)
