@@ -59,8 +59,13 @@ typedef enum { CMBWS_GRID_GL = 0, CMBWS_GRID_HEALPIX = 1 } cmbws_grid_kind;
 
 /* Arithmetic of the transform stages (Legendre recurrence and contraction,
  * ring FFTs, pixel multiplies).  Vectors at the boundary and CG scalars are
- * always FP64. */
-typedef enum { CMBWS_FP64 = 0, CMBWS_FP32 = 1 } cmbws_prec;
+ * always FP64.
+ *   CMBWS_FP64:   native FP64 throughout.
+ *   CMBWS_FP32:   FP32 throughout (relative error ~1e-6 at L ~ 3000).
+ *   CMBWS_FP32X2: FP64-accurate Legendre stage in double-float arithmetic (pairs of FP32
+ *                 values, ~48-bit significand, on the FP32 pipe, which GB300 runs 61x
+ *                 faster than FP64); ring FFTs and pixel stages in FP64. */
+typedef enum { CMBWS_FP64 = 0, CMBWS_FP32 = 1, CMBWS_FP32X2 = 2 } cmbws_prec;
 
 typedef struct cmbws_grid_s* cmbws_grid;    /* opaque, library-owned */
 typedef struct cmbws_model_s* cmbws_model;  /* opaque, library-owned */
@@ -179,7 +184,8 @@ int cmbws_apply_precond(cmbws_model m, const double* r, double* z, void* stream)
 
 /*
  * b = P^T N^-1 d + P^T N^-1/2 omega1 + S^-1/2 omega2 (Sec. 2.3; the printed S^-1 omega2
- * is read as S^-1/2 omega2, for which Var(b) = A).
+ * is read as S^-1/2 omega2, for which Var(b) = A).  b is FP64-accurate for every model:
+ * its transforms run in FP64 for FP64 models and in CMBWS_FP32X2 otherwise.
  *   d, omega1: host arrays [nobs] of device maps (npix_nu FP64); omega1 may be NULL.
  *   omega2: device stacked vector or NULL.  b: device stacked vector, written.
  */
@@ -196,11 +202,11 @@ int cmbws_project(cmbws_model m, const double* x, double* const* d, void* stream
 
 /*
  * Kernel timing.  While enabled, the library brackets each of its kernel launches with
- * CUDA events on the launching stream.  Records are kept per slot = stage + 6 * fp64,
+ * CUDA events on the launching stream.  Records are kept per slot = stage + 6 * arith,
  * stages 0 Legendre synthesis, 1 Legendre adjoint, 2 adjoint partial-sum reduction,
- * 3 ring FFT, 4 harmonic-space kernels, 5 CG vector kernels; fp64 = 1 for launches in
- * FP64 arithmetic.  cmbws_profile_read synchronises the recorded events and writes, per
- * slot (host arrays of 12, any may be NULL), the summed milliseconds, the launch count
+ * 3 ring FFT, 4 harmonic-space kernels, 5 CG vector kernels; arith 0 = FP32, 1 = FP64,
+ * 2 = double-float (CMBWS_FP32X2).  cmbws_profile_read synchronises the recorded events and
+ * writes, per slot (host arrays of 18, any may be NULL), the summed milliseconds, the launch count
  * and the summed algorithmic flops (Legendre stages: 4 flops per (l, m, ring pair) for
  * the recurrence plus 4 per map for the contraction, over the full (l, m) triangle;
  * 0 elsewhere) since the last reset; reset = 1 clears the record.
@@ -215,6 +221,9 @@ typedef struct {
   double inner_tol;   /* FP32 models: relative reduction per refinement pass (e.g. 1e-3) */
   int max_outer;      /* FP32 models: cap on refinement passes */
   double timeout_s;   /* wall-clock budget, <= 0 for none */
+  int cert_prec;      /* arithmetic of the applies that compute the true residual b - A x:
+                         CMBWS_FP64 (native) or CMBWS_FP32X2 (double-float); other values
+                         mean CMBWS_FP64 */
 } cmbws_cg_opts;
 
 typedef struct {

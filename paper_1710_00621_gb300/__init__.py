@@ -11,6 +11,7 @@ library has not been built.
 """
 from .binding import (  # noqa: F401
     CMBWS_FP32,
+    CMBWS_FP32X2,
     CMBWS_FP64,
     CMBWS_GRID_GL,
     CMBWS_GRID_HEALPIX,

@@ -18,6 +18,7 @@ CMBWS_GRID_GL = 0
 CMBWS_GRID_HEALPIX = 1
 CMBWS_FP64 = 0
 CMBWS_FP32 = 1
+CMBWS_FP32X2 = 2
 
 _ERRORS = {-1: "CMBWS_ERR_ARG", -2: "CMBWS_ERR_CUDA", -3: "CMBWS_ERR_NOMEM",
            -4: "CMBWS_ERR_SINGULAR", -5: "CMBWS_ERR_BREAKDOWN", -6: "CMBWS_ERR_NOT_CONVERGED",
@@ -45,7 +46,7 @@ class ModelDesc(ctypes.Structure):
 class CgOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("maxiter", ctypes.c_int), ("precond", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int),
-                ("timeout_s", ctypes.c_double)]
+                ("timeout_s", ctypes.c_double), ("cert_prec", ctypes.c_int)]
 
 
 class CgReport(ctypes.Structure):
@@ -325,23 +326,24 @@ def cmbws_profile_enable(on=True):
 
 
 def cmbws_profile_read(reset=True):
-    """{(stage, "fp32"|"fp64"): (milliseconds, launches, algorithmic flops)} since the last reset."""
+    """{(stage, "fp32"|"fp64"|"fp32x2"): (milliseconds, launches, algorithmic flops)} since the
+    last reset."""
     ns = len(PROFILE_STAGES)
-    ms = (ctypes.c_double * (2 * ns))()
-    n = (ctypes.c_int64 * (2 * ns))()
-    fl = (ctypes.c_double * (2 * ns))()
+    ms = (ctypes.c_double * (3 * ns))()
+    n = (ctypes.c_int64 * (3 * ns))()
+    fl = (ctypes.c_double * (3 * ns))()
     _check(load_library().cmbws_profile_read(ms, n, fl, 1 if reset else 0))
     out = {}
-    for i in range(2 * ns):
-        out[(PROFILE_STAGES[i % ns], "fp64" if i >= ns else "fp32")] = (ms[i], n[i], fl[i])
+    for i in range(3 * ns):
+        out[(PROFILE_STAGES[i % ns], ("fp32", "fp64", "fp32x2")[i // ns])] = (ms[i], n[i], fl[i])
     return out
 
 
 def cmbws_cg_solve(model, b, x, tol=1e-6, maxiter=1000, precond=1, inner_tol=1e-3, max_outer=20,
-                   timeout_s=0.0, stream=None, check=True):
+                   timeout_s=0.0, cert_prec=CMBWS_FP64, stream=None, check=True):
     """Solve A x = b in place (x holds the initial guess). Returns the report as a dict."""
     opts = CgOpts(float(tol), int(maxiter), int(precond), float(inner_tol), int(max_outer),
-                  float(timeout_s))
+                  float(timeout_s), int(cert_prec))
     rep = CgReport()
     code = load_library().cmbws_cg_solve(model.handle, _dptr(b, model.nvec, "b"),
                                          _dptr(x, model.nvec, "x"), ctypes.byref(opts),

@@ -74,8 +74,8 @@ cudaEvent_t pool_get() {
 }
 }  // namespace
 
-ProfScope::ProfScope(int stage, cudaStream_t s_, int fp64, double flops_)
-    : slot(stage + (fp64 ? PROF_N : 0)), flops(flops_), s(s_) {
+ProfScope::ProfScope(int stage, cudaStream_t s_, int arith, double flops_)
+    : slot(stage + PROF_N * arith), flops(flops_), s(s_) {
   std::lock_guard<std::mutex> lk(g_prof_mu);
   if (!g_prof_on) return;
   a = pool_get();
@@ -122,8 +122,8 @@ extern "C" int cmbws_profile_enable(int on) {
 extern "C" int cmbws_profile_read(double* ms, int64_t* launches, double* flops, int reset) {
   clear_error();
   std::lock_guard<std::mutex> lk(g_prof_mu);
-  double t[2 * PROF_N] = {0}, f[2 * PROF_N] = {0};
-  int64_t c[2 * PROF_N] = {0};
+  double t[3 * PROF_N] = {0}, f[3 * PROF_N] = {0};
+  int64_t c[3 * PROF_N] = {0};
   for (const ProfRec& r : g_prof) {
     CMBWS_CUDA(cudaEventSynchronize(r.b));
     float dt = 0.f;
@@ -132,7 +132,7 @@ extern "C" int cmbws_profile_read(double* ms, int64_t* launches, double* flops, 
     f[r.slot] += r.flops;
     c[r.slot] += 1;
   }
-  for (int i = 0; i < 2 * PROF_N; ++i) {
+  for (int i = 0; i < 3 * PROF_N; ++i) {
     if (ms) ms[i] = t[i];
     if (launches) launches[i] = c[i];
     if (flops) flops[i] = f[i];
@@ -151,7 +151,7 @@ extern "C" int cmbws_sht_synth(cmbws_grid gh, cmbws_prec prec, const double* alm
                                int nmaps, void* stream) {
   clear_error();
   Grid* g = reinterpret_cast<Grid*>(gh);
-  if (!g || !alm || !map || nmaps < 1 || (prec != CMBWS_FP64 && prec != CMBWS_FP32)) {
+  if (!g || !alm || !map || nmaps < 1 || !valid_prec(prec)) {
     set_error("cmbws_sht_synth: invalid arguments");
     return CMBWS_ERR_ARG;
   }
@@ -175,7 +175,7 @@ extern "C" int cmbws_sht_analysis(cmbws_grid gh, cmbws_prec prec, const double* 
                                   int nmaps, int weighted, void* stream) {
   clear_error();
   Grid* g = reinterpret_cast<Grid*>(gh);
-  if (!g || !alm || !map || nmaps < 1 || (prec != CMBWS_FP64 && prec != CMBWS_FP32)) {
+  if (!g || !alm || !map || nmaps < 1 || !valid_prec(prec)) {
     set_error("cmbws_sht_analysis: invalid arguments");
     return CMBWS_ERR_ARG;
   }

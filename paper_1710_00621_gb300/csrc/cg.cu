@@ -5,11 +5,12 @@
 // The host reads one or two scalars per iteration (alpha and beta are
 // computed on the host in FP64).
 //
-// FP64 models: plain PCG, then one FP64 apply certifies ||b - A x|| / ||b||.
+// FP64 models: plain PCG, then one FP64-accurate apply certifies ||b - A x|| / ||b||.
 // FP32 models: iterative refinement.  Each pass solves A d = r by PCG with
 // the FP32 transform chain (FP64 vectors and scalars) until the inner
-// residual falls by inner_tol, then x += d and r = b - A x with the FP64
-// chain; the loop ends when that FP64 residual certifies tol.
+// residual falls by inner_tol, then x += d and r = b - A x with an
+// FP64-accurate chain (native FP64 or double-float, opts.cert_prec); the loop
+// ends when that residual certifies tol.
 #include <chrono>
 #include <cmath>
 
@@ -132,9 +133,10 @@ struct Solver {
     }
     return finish(out);
   }
-  // r = b - A x (FP64 chain), returns ||r||^2
+  int cert = CMBWS_FP64;  // arithmetic of the true-residual applies
+  // r = b - A x (FP64-accurate chain), returns ||r||^2
   int true_residual(const double* b, const double* x, double* r, double* tmp, double* rr) {
-    CMBWS_TRY(M.apply_A(x, tmp, CMBWS_FP64, s));
+    CMBWS_TRY(M.apply_A(x, tmp, cert, s));
     {
       ProfScope ps_(PROF_CG, s);
       k_resid<<<kRedBlocks, kRedThreads, 0, s>>>(b, tmp, r, n, red);
@@ -225,6 +227,7 @@ static int cg_solve_impl(Model& M, const double* b, double* x, const cmbws_cg_op
     ~Free() { cudaFreeHost(p); }
   } fr{hscal};
   Solver S{M, s, n, M.cg_red.as<double>(), hscal};
+  S.cert = o.cert_prec == CMBWS_FP32X2 ? CMBWS_FP32X2 : CMBWS_FP64;
   const long long sht0 = M.n_sht;
 
   double bb;
@@ -266,14 +269,14 @@ static int cg_solve_impl(Model& M, const double* b, double* x, const cmbws_cg_op
       status = CMBWS_ERR_TIMEOUT;
       break;
     }
-    if (M.prec == CMBWS_FP32 && outer >= o.max_outer) {
+    if (M.prec != CMBWS_FP64 && outer >= o.max_outer) {
       set_error("CG: %d refinement passes without reaching tol", outer);
       status = CMBWS_ERR_NOT_CONVERGED;
       break;
     }
     // inner solve A d = r; FP64 models aim directly at the target (plus a small
     // margin for the gap between recursive and true residuals)
-    const double stop = M.prec == CMBWS_FP64 ? 0.5 * target
+    const double stop = M.prec != CMBWS_FP32 ? 0.5 * target
                                              : std::max(o.inner_tol * std::sqrt(rr), 0.5 * target);
     int it = 0;
     double rr_in;

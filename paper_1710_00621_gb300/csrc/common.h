@@ -167,11 +167,23 @@ int pack_alm(const Grid& g, int prec, int nmaps, const double* packed, void* alm
 // internal lm complex FP64 [nmaps][nlm] -> packed FP64
 int unpack_alm(const Grid& g, int nmaps, const double* lmc, double* packed, cudaStream_t s);
 
-inline size_t prec_size(int prec) { return prec == CMBWS_FP64 ? 8 : 4; }
+// FP32 transforms use float buffers; FP64 and FP32X2 use the FP64 layouts.
+inline bool is_f32(int prec) { return prec == CMBWS_FP32; }
+inline size_t prec_size(int prec) { return is_f32(prec) ? 4 : 8; }
+inline int arith_of(int prec) { return prec == CMBWS_FP32 ? 0 : prec == CMBWS_FP64 ? 1 : 2; }
+inline bool valid_prec(int prec) {
+  return prec == CMBWS_FP64 || prec == CMBWS_FP32 || prec == CMBWS_FP32X2;
+}
+
+// ---- double-float Legendre stage (legendre_df.cu) ----
+int legendre_synth_df(const Grid& g, int nmaps, const void* alm, void* F, cudaStream_t s);
+int legendre_adj_df_chunk(const Grid& g, int nm, const void* F, double* part, cudaStream_t s);
+int legendre_df_adj_nblk(const Grid& g);
 
 // ---- kernel timing (api.cu): CUDA events around launches while enabled ----
-// Stages; a record's slot is stage + PROF_N * (FP64 ? 1 : 0).  `flops` is the algorithmic
-// count of the launch (full (l, m) triangle), 0 for stages without one.
+// Stages; a record's slot is stage + PROF_N * arith, arith 0 = FP32, 1 = FP64,
+// 2 = double-float (FP32X2).  `flops` is the algorithmic count of the launch (full (l, m)
+// triangle), 0 for stages without one.
 enum {
   PROF_LEG_SYNTH = 0,
   PROF_LEG_ADJ = 1,
@@ -186,7 +198,7 @@ struct ProfScope {
   double flops;
   cudaStream_t s;
   cudaEvent_t a = nullptr;
-  ProfScope(int stage, cudaStream_t s_, int fp64 = 1, double flops_ = 0.0);
+  ProfScope(int stage, cudaStream_t s_, int arith = 1, double flops_ = 0.0);
   ~ProfScope();
 };
 

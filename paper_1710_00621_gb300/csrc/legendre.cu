@@ -426,13 +426,15 @@ int adj_dispatch(const Grid& g, int nmaps, const void* F, void* part, double* ou
 }  // namespace
 
 int legendre_synth(const Grid& g, int prec, int nmaps, const void* alm, void* F, cudaStream_t s) {
+  if (prec == CMBWS_FP32X2) return legendre_synth_df(g, nmaps, alm, F, s);
   if (prec == CMBWS_FP64) return synth_dispatch<double>(g, nmaps, alm, F, s);
   return synth_dispatch<float>(g, nmaps, alm, F, s);
 }
 
 size_t legendre_adjoint_part_bytes(const Grid& g, int prec, int nmaps) {
   const int nm = nmaps < 4 ? nmaps : 4;
-  const int nblk = prec == CMBWS_FP64 ? adj_nblk<double>(g) : adj_nblk<float>(g);
+  const int nblk = prec == CMBWS_FP32X2 ? legendre_df_adj_nblk(g)
+                   : prec == CMBWS_FP64 ? adj_nblk<double>(g) : adj_nblk<float>(g);
   return (size_t)nblk * 2 * nm * nlm_of(g.lmax) * prec_size(prec);
 }
 
@@ -441,6 +443,20 @@ int legendre_adjoint(const Grid& g, int prec, int nmaps, const void* F, void* pa
   if (part_bytes < legendre_adjoint_part_bytes(g, prec, nmaps)) {
     set_error("legendre_adjoint: partial-sum buffer too small");
     return CMBWS_ERR_ARG;
+  }
+  if (prec == CMBWS_FP32X2) {
+    const int64_t nlm = nlm_of(g.lmax), fs = (int64_t)g.nring * (g.lmax + 1);
+    const int nblk = legendre_df_adj_nblk(g);
+    for (int k0 = 0; k0 < nmaps; k0 += 4) {
+      const int nm = nmaps - k0 < 4 ? nmaps - k0 : 4;
+      CMBWS_TRY(legendre_adj_df_chunk(g, nm, (const double2*)F + k0 * fs, (double*)part, s));
+      dim3 rg((unsigned)((nlm + 255) / 256), nm);
+      ProfScope ps(PROF_LEG_RED, s, 2);
+      k_adj_reduce<double><<<rg, 256, 0, s>>>((const double*)part, nblk, nlm, nm, g.c64.as<double>(),
+                                              (double2*)(out + 2 * k0 * nlm));
+      CMBWS_LAUNCH_CHECK();
+    }
+    return CMBWS_OK;
   }
   if (prec == CMBWS_FP64) return adj_dispatch<double>(g, nmaps, F, part, out, s);
   return adj_dispatch<float>(g, nmaps, F, part, out, s);

@@ -324,8 +324,8 @@ int Model::group_chain(Group& G, int prec, int which, cudaStream_t s) {
   const void* pix[kMaxMaps];
   for (int j = 0; j < G.nmaps; ++j) {
     const int nu = G.bands[j];
-    pix[j] = which == 0 ? (prec == CMBWS_FP64 ? pixA64[nu].p : pixA32[nu].p)
-                        : (prec == CMBWS_FP64 ? pixM64[nu].p : pixM32[nu].p);
+    pix[j] = which == 0 ? (!is_f32(prec) ? pixA64[nu].p : pixA32[nu].p)
+                        : (!is_f32(prec) ? pixM64[nu].p : pixM32[nu].p);
   }
   CMBWS_TRY(legendre_synth(g, prec, G.nmaps, G.alm.p, G.F.p, s));
   CMBWS_TRY(ringfft_fused(g, prec, G.nmaps, G.F.p, pix, s));
@@ -374,8 +374,8 @@ int Model::mix_forward(Group& G, int prec, const double* x, cudaStream_t s) {
   gd.alm = G.alm.p;
   gd.nlm = nlm_of(gd.L);
   dim3 grd((gd.L + 1 + 127) / 128, gd.L + 1);
-  ProfScope ps(PROF_HARM, s, prec == CMBWS_FP64);
-  if (prec == CMBWS_FP64) k_mix_forward<double2><<<grd, 128, 0, s>>>(h, gd, x);
+  ProfScope ps(PROF_HARM, s, is_f32(prec) ? 0 : 1);
+  if (!is_f32(prec)) k_mix_forward<double2><<<grd, 128, 0, s>>>(h, gd, x);
   else k_mix_forward<float2><<<grd, 128, 0, s>>>(h, gd, x);
   CMBWS_LAUNCH_CHECK();
   return CMBWS_OK;
@@ -405,7 +405,7 @@ int Model::apply_A(const double* x, double* y, int prec, cudaStream_t s) {
   const BandDev bd = bands_dev(prec);
   for (int k = 0; k < ncomp; ++k) {
     dim3 grd((Lk[k] + 1 + 127) / 128, Lk[k] + 1);
-    ProfScope ps(PROF_HARM, s, prec == CMBWS_FP64);
+    ProfScope ps(PROF_HARM, s, is_f32(prec) ? 0 : 1);
     k_mix_adjoint<<<grd, 128, 0, s>>>(h, bd, k, x, y);
     CMBWS_LAUNCH_CHECK();
   }
@@ -418,15 +418,15 @@ int Model::apply_precond(const double* r, double* z, int prec, cudaStream_t s) {
   const BandDev bd = bands_dev(prec);
   {
     dim3 grd((Lall + 1 + 127) / 128, Lall + 1);
-    ProfScope ps(PROF_HARM, s, prec == CMBWS_FP64);
-    if (prec == CMBWS_FP64) k_pinv_T<double2><<<grd, 128, 0, s>>>(h, bd, r, tprior.as<double>(), Lall);
+    ProfScope ps(PROF_HARM, s, is_f32(prec) ? 0 : 1);
+    if (!is_f32(prec)) k_pinv_T<double2><<<grd, 128, 0, s>>>(h, bd, r, tprior.as<double>(), Lall);
     else k_pinv_T<float2><<<grd, 128, 0, s>>>(h, bd, r, tprior.as<double>(), Lall);
     CMBWS_LAUNCH_CHECK();
   }
   for (Group& G : groups) CMBWS_TRY(group_chain(G, prec, 1, s));
   {
     dim3 grd((Lcomp + 1 + 127) / 128, Lcomp + 1);
-    ProfScope ps(PROF_HARM, s, prec == CMBWS_FP64);
+    ProfScope ps(PROF_HARM, s, is_f32(prec) ? 0 : 1);
     k_pinv<<<grd, 128, 0, s>>>(h, bd, tprior.as<double>(), z, Lcomp);
     CMBWS_LAUNCH_CHECK();
   }
@@ -437,6 +437,7 @@ int Model::apply_precond(const double* r, double* z, int prec, cudaStream_t s) {
 int Model::rhs(const double* const* d, const double* const* w1, const double* w2, double* b,
                cudaStream_t s) {
   const HarmDev h = harm();
+  const int ap = prec == CMBWS_FP64 ? CMBWS_FP64 : CMBWS_FP32X2;  // FP64-accurate either way
   // P^T applied to the pixel maps: per group, analysis FFT (unweighted) + Legendre adjoint
   for (Group& G : groups) {
     const Grid& g = *G.grid;
@@ -450,11 +451,10 @@ int Model::rhs(const double* const* d, const double* const* w1, const double* w2
           pixtmp.as<double>() + j * n, n);
       CMBWS_LAUNCH_CHECK();
     }
-    CMBWS_TRY(ringfft_analysis(g, CMBWS_FP64, G.nmaps, pixtmp.as<double>(), 0, G.F.p, s));
-    CMBWS_TRY(legendre_adjoint(g, CMBWS_FP64, G.nmaps, G.F.p, part.p, part.bytes,
-                               G.out.as<double>(), s));
+    CMBWS_TRY(ringfft_analysis(g, ap, G.nmaps, pixtmp.as<double>(), 0, G.F.p, s));
+    CMBWS_TRY(legendre_adjoint(g, ap, G.nmaps, G.F.p, part.p, part.bytes, G.out.as<double>(), s));
   }
-  const BandDev bd = bands_dev(CMBWS_FP64);
+  const BandDev bd = bands_dev(ap);
   CMBWS_CUDA(cudaMemsetAsync(zero.p, 0, (size_t)nvec * 8, s));
   for (int k = 0; k < ncomp; ++k) {
     dim3 grd((Lk[k] + 1 + 127) / 128, Lk[k] + 1);
@@ -667,7 +667,7 @@ using namespace cmbws;
 extern "C" int cmbws_model_create(const cmbws_model_desc* desc, cmbws_prec prec, void* stream,
                                   cmbws_model* out) {
   clear_error();
-  if (!desc || !out || (prec != CMBWS_FP64 && prec != CMBWS_FP32)) {
+  if (!desc || !out || !valid_prec(prec)) {
     set_error("cmbws_model_create: invalid arguments");
     return CMBWS_ERR_ARG;
   }

@@ -283,7 +283,7 @@ int launch(const Grid& g, int nmaps, void* F, double* map_out, const double* map
     if (MODE == MODE_FUSED)
       for (int i = 0; i < nm; ++i) pp.p[i] = (const T*)pix[k0 + i];
     dim3 grd(g.npair, nm);
-    ProfScope ps(PROF_FFT, s, dbl);
+    ProfScope ps(PROF_FFT, s, dbl ? 1 : 0);
     kern<<<grd, 256, sm, s>>>((T2*)F + k0 * fs, fs, map_out ? map_out + k0 * g.npix : nullptr,
                               map_in ? map_in + k0 * g.npix : nullptr, g.npix, rw, pp,
                               g.plans_d.as<FftPlan>(), g.pair_plan.as<int>(),
@@ -297,26 +297,26 @@ int launch(const Grid& g, int nmaps, void* F, double* map_out, const double* map
 }  // namespace
 
 int ringfft_smem_ok(const Grid& g, int prec) {
-  const size_t sm = prec == CMBWS_FP64 ? smem_bytes<double>(g) : smem_bytes<float>(g);
+  const size_t sm = !is_f32(prec) ? smem_bytes<double>(g) : smem_bytes<float>(g);
   return sm <= 227 * 1024;
 }
 
 int ringfft_synth(const Grid& g, int prec, int nmaps, const void* F, double* map, cudaStream_t s) {
-  if (prec == CMBWS_FP64)
+  if (!is_f32(prec))
     return launch<double, MODE_SYNTH>(g, nmaps, const_cast<void*>(F), map, nullptr, 0, nullptr, s);
   return launch<float, MODE_SYNTH>(g, nmaps, const_cast<void*>(F), map, nullptr, 0, nullptr, s);
 }
 
 int ringfft_analysis(const Grid& g, int prec, int nmaps, const double* map, int weighted, void* F,
                      cudaStream_t s) {
-  if (prec == CMBWS_FP64)
+  if (!is_f32(prec))
     return launch<double, MODE_ANALYSIS>(g, nmaps, F, nullptr, map, weighted, nullptr, s);
   return launch<float, MODE_ANALYSIS>(g, nmaps, F, nullptr, map, weighted, nullptr, s);
 }
 
 int ringfft_fused(const Grid& g, int prec, int nmaps, void* F, const void* const* pix,
                   cudaStream_t s) {
-  if (prec == CMBWS_FP64)
+  if (!is_f32(prec))
     return launch<double, MODE_FUSED>(g, nmaps, F, nullptr, nullptr, 0, pix, s);
   return launch<float, MODE_FUSED>(g, nmaps, F, nullptr, nullptr, 0, pix, s);
 }

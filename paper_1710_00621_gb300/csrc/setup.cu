@@ -206,7 +206,7 @@ __global__ void k_unpack(const double2* __restrict__ lmc, int L, double* __restr
 int pack_alm(const Grid& g, int prec, int nmaps, const double* packed, void* alm, cudaStream_t s) {
   const int L = g.lmax;
   dim3 blk(128), grd((L + 1 + 127) / 128, L + 1, nmaps);
-  if (prec == CMBWS_FP64)
+  if (!is_f32(prec))
     k_pack<double2, double><<<grd, blk, 0, s>>>(packed, g.c64.as<double>(), L, (double2*)alm);
   else
     k_pack<float2, float><<<grd, blk, 0, s>>>(packed, g.c64.as<double>(), L, (float2*)alm);

@@ -14,10 +14,13 @@ def tol(prec, lmax):
     FP64: the three-term recurrence and the quadrature sums lose accuracy roughly like
     L^2 eps (the oracle's own Gauss-Legendre round trip shows 1.6e-12 at L = 255 and
     7e-12 at L = 511), so 1e-16 (L+1)^2 with a floor of 1e-12.
+    FP32X2 (double-float): 48 significand bits instead of 53, so four times the FP64 bound.
     FP32: eps = 6e-8 per step, growing linearly along the recurrence: 5 (L+1) eps, floor 1e-5.
     """
     if prec == cw.CMBWS_FP64:
         return max(1e-12, 1e-16 * (lmax + 1) ** 2)
+    if prec == cw.CMBWS_FP32X2:
+        return max(4e-12, 4e-16 * (lmax + 1) ** 2)
     return max(1e-5, 5 * (lmax + 1) * 6e-8)
 
 # (kind, n, lmax): tiny, ragged, several CTAs of the Legendre kernels, folded spectra
@@ -57,7 +60,10 @@ def test_grid_geometry_matches_oracle(kind, n, lmax):
     assert g.npix == o.npix
 
 
-@pytest.mark.parametrize("prec", [cw.CMBWS_FP64, cw.CMBWS_FP32])
+PRECS = [cw.CMBWS_FP64, cw.CMBWS_FP32, cw.CMBWS_FP32X2]
+
+
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("kind,n,lmax", CASES)
 def test_synthesis_parity(kind, n, lmax, prec):
     g, _ = _grids(kind, n, lmax)
@@ -74,7 +80,7 @@ def test_synthesis_parity(kind, n, lmax, prec):
 
 
 @pytest.mark.parametrize("weighted", [0, 1])
-@pytest.mark.parametrize("prec", [cw.CMBWS_FP64, cw.CMBWS_FP32])
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("kind,n,lmax", CASES)
 def test_adjoint_parity(kind, n, lmax, prec, weighted):
     g, _ = _grids(kind, n, lmax)
@@ -108,6 +114,14 @@ def test_map_batches_of_any_size(nmaps):
 
 @pytest.mark.parametrize("lmax", [31, 255, 1023])
 def test_gl_round_trip_exact_on_gpu(lmax):
+    # the double-float path must match FP64 accuracy
+    g0 = cw.cmbws_plan_grid(cw.CMBWS_GRID_GL, lmax + 1, lmax)
+    a0 = np.random.default_rng(lmax + 1).standard_normal((lmax + 1) ** 2)
+    m0 = to_dev(np.zeros(g0.npix))
+    b0 = to_dev(np.zeros((lmax + 1) ** 2))
+    cw.cmbws_sht_synth(g0, cw.CMBWS_FP32X2, to_dev(a0), m0, 1)
+    cw.cmbws_sht_analysis(g0, cw.CMBWS_FP32X2, m0, b0, 1, 1)
+    assert rel_err(to_host(b0), a0) < tol(cw.CMBWS_FP32X2, lmax)
     # Sec. 2.1: Y^T W Y = I on the Gauss-Legendre grid
     g = cw.cmbws_plan_grid(cw.CMBWS_GRID_GL, lmax + 1, lmax)
     a = np.random.default_rng(lmax).standard_normal((lmax + 1) ** 2)
@@ -136,7 +150,8 @@ def test_adjointness_large_healpix():
     assert abs(lhs - rhs) <= 1e-10 * abs(lhs)
 
 
-def test_full_size_sampled_rings_nside1024():
+@pytest.mark.parametrize("prec", [cw.CMBWS_FP64, cw.CMBWS_FP32X2])
+def test_full_size_sampled_rings_nside1024(prec):
     # Nside 1024, L = 3071 (the largest band grid of the multi-resolution workload):
     # the synthesis of a few rings recomputed by the oracle on a sub-grid of those rings
     g = cw.cmbws_plan_grid(cw.CMBWS_GRID_HEALPIX, 1024, 3071)
@@ -147,7 +162,7 @@ def test_full_size_sampled_rings_nside1024():
                                                for m in range(1, L + 1)])
     a = rng.standard_normal((L + 1) ** 2) / (1.0 + ell)
     out = to_dev(np.zeros(g.npix))
-    cw.cmbws_sht_synth(g, cw.CMBWS_FP64, to_dev(a), out, 1)
+    cw.cmbws_sht_synth(g, prec, to_dev(a), out, 1)
     got = to_host(out)
     rings = np.array([0, 1, 5, 700, 1023, 1500, 2047, 2600, 4094])
     sub = og.RingGrid("healpix", 1024, o.theta[rings], o.phi0[rings], o.nphi[rings], o.weight[rings],

@@ -11,7 +11,8 @@ from tests._models import multires_small, oracle_model, tiny_workload
 
 pytestmark = pytest.mark.gpu
 
-TOL = {cw.CMBWS_FP64: 1e-10, cw.CMBWS_FP32: 1e-4}
+TOL = {cw.CMBWS_FP64: 1e-10, cw.CMBWS_FP32: 1e-4, cw.CMBWS_FP32X2: 1e-10}
+PRECS = [cw.CMBWS_FP64, cw.CMBWS_FP32, cw.CMBWS_FP32X2]
 
 
 def _setups():
@@ -34,7 +35,7 @@ def models():
     return cache
 
 
-@pytest.mark.parametrize("prec", [cw.CMBWS_FP64, cw.CMBWS_FP32])
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("name", list(SETUPS))
 def test_apply_A_parity(models, name, prec):
     work, m, inp = models[name]
@@ -45,7 +46,7 @@ def test_apply_A_parity(models, name, prec):
     assert rel_err(to_host(y), om.apply_A(m, x)) < TOL[prec]
 
 
-@pytest.mark.parametrize("prec", [cw.CMBWS_FP64, cw.CMBWS_FP32])
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("name", list(SETUPS))
 def test_apply_precond_parity(models, name, prec):
     work, m, inp = models[name]
@@ -64,10 +65,12 @@ def test_model_counts_shts_like_the_paper(models):
     assert g.nvec == m.nvec()
 
 
+@pytest.mark.parametrize("prec", [cw.CMBWS_FP64, cw.CMBWS_FP32])
 @pytest.mark.parametrize("name", ["tiny15", "multires64"])
-def test_rhs_parity(models, name):
+def test_rhs_parity(models, name, prec):
+    # the RHS is FP64-accurate for every model (double-float transforms for FP32 models)
     work, m, inp = models[name]
-    g, grids = gpu_model(work, inp)
+    g, grids = gpu_model(work, inp, prec)
     d = [mp + n for mp, n in zip(om.project(m, inp["x_true"]), inp["noise"])]
     rng = np.random.default_rng(3)
     w1 = [rng.standard_normal(x.size) for x in d]
@@ -113,11 +116,16 @@ def test_wiener_solve_fp64_and_fp32_refined(models, name):
     b = om.rhs(m, d)
     xo, _ = pcg(lambda v: om.apply_A(m, v), b, lambda v: opc.apply_precond(m, v), tol=1e-12,
                 maxiter=2000)
-    for prec in (cw.CMBWS_FP64, cw.CMBWS_FP32):
+    for prec, cert in ((cw.CMBWS_FP64, cw.CMBWS_FP64), (cw.CMBWS_FP32, cw.CMBWS_FP64),
+                       (cw.CMBWS_FP32, cw.CMBWS_FP32X2), (cw.CMBWS_FP32X2, cw.CMBWS_FP32X2)):
         g, _ = gpu_model(work, inp, prec)
         x = to_dev(np.zeros(m.nvec()))
-        rep = cw.cmbws_cg_solve(g, to_dev(b), x, tol=1e-6, maxiter=2000, inner_tol=1e-3)
+        rep = cw.cmbws_cg_solve(g, to_dev(b), x, tol=1e-6, maxiter=2000, inner_tol=1e-3,
+                                cert_prec=cert)
         assert rep["rel_res"] <= 1e-6
+        # the certified residual is the true one: recompute it with the oracle
+        r = b - om.apply_A(m, to_host(x))
+        assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.01e-6
         # relative error vs the FP64 oracle solution, bounded by cond * tol
         assert rel_err(to_host(x), xo) < 1e-4, (prec, rep)
 
