@@ -156,6 +156,15 @@ typedef struct {
   const double* const* ninv;     /* [nobs] device maps tau_nu = diag(N_nu^-1), npix_nu, > 0 */
   const double* mix_scalar;      /* [nobs * ncomp] q_{nu,k}, row nu (spatially constant
                                     mixing, Q~ = q I) */
+  /* Spatially variable mixing (Eq. Q), optional: both NULL for scalar mixing everywhere.
+   * Entry nu * ncomp + k of each array describes pair (nu, k); a NULL mix_map entry keeps
+   * that pair scalar.  For a variable pair, Q~_{nu,k} = Y^T W Q Y on mix_grid[...] (its
+   * lmax must be >= max(L_k, L_nu); input zero-padded from L_k, output truncated at L_nu,
+   * Sec. 2.2), and mix_map[...] is a device map of q_{nu,k}(n) on that grid, a mask
+   * included as zeros.  Pairs sharing a grid handle are transformed together.  The
+   * preconditioner uses the scalar of Eq. optimal-q of each variable map. */
+  const cmbws_grid* mix_grid;    /* [nobs * ncomp] or NULL */
+  const double* const* mix_map;  /* [nobs * ncomp] device pointers or NULL */
 } cmbws_model_desc;
 
 /*
@@ -173,7 +182,8 @@ int cmbws_model_create(const cmbws_model_desc* desc, cmbws_prec prec, void* stre
 int cmbws_model_destroy(cmbws_model m);
 
 /* Length of a stacked component vector, sum_k (L_k+1)^2; SHTs per apply of A and of
- * M_PI as the paper counts them (Sec. 3.3: 2(2 Nmix + Nobs) and 2 Nobs). */
+ * M_PI as the paper counts them (Sec. 3.3: 2(2 Nmix + Nobs) and 2 Nobs, Nmix = number of
+ * variable mixing pairs). */
 int cmbws_model_info(cmbws_model m, int64_t* nvec, int* nsht_A, int* nsht_M);
 
 /* y = A x = S^-1 x + P^T N^-1 P x (Eq. A).  x, y: device stacked vectors, distinct. */

@@ -40,7 +40,9 @@ class ModelDesc(ctypes.Structure):
                 ("beam", ctypes.POINTER(ctypes.POINTER(ctypes.c_double))),
                 ("cl", ctypes.POINTER(ctypes.POINTER(ctypes.c_double))),
                 ("ninv", ctypes.POINTER(ctypes.c_void_p)),
-                ("mix_scalar", ctypes.POINTER(ctypes.c_double))]
+                ("mix_scalar", ctypes.POINTER(ctypes.c_double)),
+                ("mix_grid", ctypes.POINTER(ctypes.c_void_p)),
+                ("mix_map", ctypes.POINTER(ctypes.c_void_p))]
 
 
 class CgOpts(ctypes.Structure):
@@ -218,9 +220,11 @@ def cmbws_sht_analysis_noalloc(grid, prec, map_in, alm, nmaps=1, weighted=1, str
 class Model:
     """A model handle (owns it); keeps its grids alive."""
 
-    def __init__(self, handle, grids, lmax_comp):
+    def __init__(self, handle, grids, lmax_comp, nobs=None):
         self.handle = handle
-        self.grids = grids
+        self.nobs = len(grids) if nobs is None else nobs
+        self.all_grids = grids
+        self.grids = grids[:self.nobs]
         self.lmax_comp = list(lmax_comp)
         nvec = ctypes.c_int64()
         na = ctypes.c_int()
@@ -241,15 +245,19 @@ class Model:
             pass
 
 
+def _handle(g):
+    return g.handle.value if isinstance(g.handle, ctypes.c_void_p) else g.handle
+
+
 def cmbws_model_create(lmax_comp, band_grids, beams, cls, ninv, mix_scalar, prec=CMBWS_FP64,
-                       stream=None):
+                       stream=None, mix_grids=None, mix_maps=None):
     """lmax_comp: [ncomp] ints; band_grids: [nobs] Grid; beams: [nobs] arrays b_l (l <= L_nu);
-    cls: [ncomp] arrays C_l or None; ninv: [nobs] CUDA float64 maps; mix_scalar: [nobs, ncomp]."""
+    cls: [ncomp] arrays C_l or None; ninv: [nobs] CUDA float64 maps; mix_scalar: [nobs, ncomp];
+    mix_grids / mix_maps: optional [nobs][ncomp] Grid / CUDA float64 map (None = scalar pair)."""
     ncomp, nobs = len(lmax_comp), len(band_grids)
     q = np.ascontiguousarray(np.asarray(mix_scalar, dtype=np.float64).reshape(nobs, ncomp))
     lk = (ctypes.c_int * ncomp)(*[int(v) for v in lmax_comp])
-    gh = (ctypes.c_void_p * nobs)(*[g.handle.value if isinstance(g.handle, ctypes.c_void_p) else g.handle
-                                    for g in band_grids])
+    gh = (ctypes.c_void_p * nobs)(*[_handle(g) for g in band_grids])
     keep = []
     bp = (ctypes.POINTER(ctypes.c_double) * nobs)()
     for nu in range(nobs):
@@ -270,11 +278,27 @@ def cmbws_model_create(lmax_comp, band_grids, beams, cls, ninv, mix_scalar, prec
             cp[k] = c.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     nv = (ctypes.c_void_p * nobs)(*[_dptr(ninv[nu], band_grids[nu].npix, f"ninv[{nu}]").value
                                     for nu in range(nobs)])
-    desc = ModelDesc(ncomp, nobs, lk, gh, bp, cp, nv, q.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    mg = ctypes.POINTER(ctypes.c_void_p)()
+    mm = ctypes.POINTER(ctypes.c_void_p)()
+    extra_grids = []
+    if mix_maps is not None:
+        mg = (ctypes.c_void_p * (nobs * ncomp))()
+        mm = (ctypes.c_void_p * (nobs * ncomp))()
+        for nu in range(nobs):
+            for k in range(ncomp):
+                t = mix_maps[nu][k]
+                if t is None:
+                    continue
+                g = mix_grids[nu][k]
+                extra_grids.append(g)
+                mg[nu * ncomp + k] = _handle(g)
+                mm[nu * ncomp + k] = _dptr(t, g.npix, f"mix_map[{nu}][{k}]").value
+    desc = ModelDesc(ncomp, nobs, lk, gh, bp, cp, nv, q.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                     mg, mm)
     h = ctypes.c_void_p()
     _check(load_library().cmbws_model_create(ctypes.byref(desc), int(prec), _stream(stream),
                                              ctypes.byref(h)))
-    return Model(h, list(band_grids), lmax_comp)
+    return Model(h, list(band_grids) + extra_grids, lmax_comp, nobs=nobs)
 
 
 def cmbws_model_destroy(model):

@@ -15,11 +15,11 @@
 // * synthesis: the coefficients of the current l-chunk are staged in shared
 //   memory and read as broadcasts; every map of the grid group shares one
 //   recurrence (NM maps per launch);
-// * adjoint: for a chunk of CH values of l each thread forms per-l products
-//   summed over its R pairs, a warp reduce-scatter sums them over 32 lanes,
-//   and the warps of the CTA are summed in shared memory; each CTA writes its
-//   partial sums, which a second kernel adds in a fixed order (deterministic)
-//   and scales by c_lm.
+// * adjoint: for a chunk of CH values of l the recurrence values of the CTA's
+//   pairs go to a shared-memory tile and the contraction over pairs runs as a
+//   small GEMM from shared memory (register-blocked row pairs x pair slices),
+//   the slices added in shared memory; each CTA writes its partial sums, which
+//   a second kernel adds in a fixed order (deterministic) and scales by c_lm.
 #include <climits>
 #include <type_traits>
 
@@ -156,56 +156,50 @@ k_leg_synth(const typename V2<T>::t* __restrict__ alm, int64_t alm_stride,
   }
 }
 
-// Sum NV values over the 32 lanes of a warp; afterwards lane q holds the
-// sums of flat indices [q * NV/32, (q+1) * NV/32) in v[0 .. NV/32).
-template <typename T, int NV>
-__device__ __forceinline__ void warp_reduce_scatter(T (&v)[NV], int lane) {
-  static_assert(NV % 32 == 0, "NV must be a multiple of 32");
-#pragma unroll
-  for (int s = 0; s < 5; ++s) {
-    const int o = 16 >> s;
-    const int h = (NV >> s) / 2;
-    const bool up = (lane & o) != 0;
-#pragma unroll
-    for (int i = 0; i < h; ++i) {
-      const T send = up ? v[i] : v[i + h];
-      const T keep = up ? v[i + h] : v[i];
-      v[i] = keep + __shfl_xor_sync(kFull, send, o);
-    }
-  }
-}
-
+// Adjoint as a per-chunk GEMM in shared memory.  For a chunk of CH values of l:
+//   phase 1: thread i runs the recurrence of its R pairs and stores mu[pair][l] (tile muT);
+//   phase 2: D[l][part] = sum_pairs mu[pair][l] * EO[pair][parity(l)][part], each thread
+//            owning two rows (an even/odd l pair) and a slice of KS pairs, 2P accumulators;
+//   phase 3: the NSLICE slice partials are added in shared memory and written out.
+// Shared memory: muT [NR][CH+2], EO [NR][2P], red [NSLICE][CH/2][2P].
 template <typename T, int NM, int R, int NT, int CH>
 __global__ void __launch_bounds__(NT)
-k_leg_adj(const typename V2<T>::t* __restrict__ F, int64_t F_stride, const T* __restrict__ Acoef,
-          const int* __restrict__ ls_tab, const typename V2<T>::t* __restrict__ st,
-          const T* __restrict__ yr, const int2* __restrict__ pring, T* __restrict__ part,
-          int64_t nlm, int L, int npair, int nring) {
+k_leg_adj2(const typename V2<T>::t* __restrict__ F, int64_t F_stride, const T* __restrict__ Acoef,
+           const int* __restrict__ ls_tab, const typename V2<T>::t* __restrict__ st,
+           const T* __restrict__ yr, const int2* __restrict__ pring, T* __restrict__ part,
+           int64_t nlm, int L, int npair) {
   using T2 = typename V2<T>::t;
   constexpr int P = 2 * NM;
-  constexpr int NV0 = CH * P;
-  constexpr int NV = (NV0 + 31) / 32 * 32;
-  constexpr int NW = NT / 32;
-  constexpr int PER = NV / 32;
-  __shared__ T red[NW][NV];
+  constexpr int NR = NT * R;
+  constexpr int CHP = CH + 2;
+  constexpr int NJ = CH / 2;
+  constexpr int NSLICE = NT / NJ;
+  constexpr int KS = NR / NSLICE;
+  static_assert(NT % NJ == 0 && NR % NSLICE == 0, "tile shape");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* muT = reinterpret_cast<T*>(smem_raw);
+  T* eo = muT + NR * CHP;
+  T* red = eo + NR * 2 * P;
   __shared__ int s_lo;
 
   const int m = blockIdx.y;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int tid = threadIdx.x;
   const int64_t lmo = lm_off(L, m) - m;
   const T* Am = Acoef + lmo;
-  T* pout = part + (int64_t)blockIdx.x * P * nlm + lmo;  // pout[pp * nlm + l]
-  const int pbase = blockIdx.x * NT * R + threadIdx.x;
+  T* pout = part + (int64_t)blockIdx.x * P * nlm + lmo;
+  const int p0 = blockIdx.x * NR;
 
+  // per-pair recurrence state (pairs tid + i NT of this block)
   int ls[R];
   T y[R], mu1[R], mu2[R];
   T2 inj[R];
-  T eR[R][NM], eI[R][NM], oR[R][NM], oI[R][NM];
   int mylo = INT_MAX;
 #pragma unroll
   for (int i = 0; i < R; ++i) {
-    const int p = pbase + i * NT;
+    const int lp = tid + i * NT;
+    const int p = p0 + lp;
     mu1[i] = mu2[i] = 0;
+    T* e = eo + lp * 2 * P;
     if (p < npair) {
       ls[i] = ls_tab[(int64_t)m * npair + p];
       y[i] = yr[p];
@@ -215,46 +209,39 @@ k_leg_adj(const typename V2<T>::t* __restrict__ F, int64_t F_stride, const T* __
       for (int k = 0; k < NM; ++k) {
         const T2 gn = F[k * F_stride + (int64_t)rr.x * (L + 1) + m];
         T2 gs;
-        if (rr.y >= 0) {
-          gs = F[k * F_stride + (int64_t)rr.y * (L + 1) + m];
-        } else {
-          gs.x = gs.y = 0;
-        }
-        eR[i][k] = gn.x + gs.x;
-        eI[i][k] = gn.y + gs.y;
-        oR[i][k] = rr.y >= 0 ? gn.x - gs.x : gn.x;
-        oI[i][k] = rr.y >= 0 ? gn.y - gs.y : gn.y;
+        gs.x = gs.y = 0;
+        if (rr.y >= 0) gs = F[k * F_stride + (int64_t)rr.y * (L + 1) + m];
+        e[2 * k] = gn.x + gs.x;
+        e[2 * k + 1] = gn.y + gs.y;
+        e[P + 2 * k] = rr.y >= 0 ? gn.x - gs.x : gn.x;
+        e[P + 2 * k + 1] = rr.y >= 0 ? gn.y - gs.y : gn.y;
       }
     } else {
       ls[i] = INT_MAX;
       y[i] = 0;
       inj[i].x = inj[i].y = 0;
 #pragma unroll
-      for (int k = 0; k < NM; ++k) eR[i][k] = eI[i][k] = oR[i][k] = oI[i][k] = 0;
+      for (int q = 0; q < 2 * P; ++q) e[q] = 0;
     }
     mylo = min(mylo, ls[i]);
   }
-  if (threadIdx.x == 0) s_lo = INT_MAX;
+  if (tid == 0) s_lo = INT_MAX;
   __syncthreads();
   atomicMin(&s_lo, mylo);
   __syncthreads();
   const int lo = s_lo;
   int nxt = mylo;
-
-  // coefficients below the first significant l of every pair in this block are zero
   {
     const int lend = min(lo, L + 1);
-    for (int l = m + threadIdx.x; l < lend; l += NT) {
+    for (int l = m + tid; l < lend; l += NT)
 #pragma unroll
       for (int pp = 0; pp < P; ++pp) pout[pp * nlm + l] = T(0);
-    }
   }
+  const int jrow = tid % NJ, slice = tid / NJ;
 
   for (int c0 = lo; c0 <= L; c0 += CH) {
-    T v[NV];
-#pragma unroll
-    for (int q = 0; q < NV; ++q) v[q] = 0;
-#pragma unroll
+    // phase 1: recurrence into the tile
+#pragma unroll 4
     for (int j = 0; j < CH; j += 2) {
       const int l = c0 + j;
       const T A0 = (l <= L) ? Am[l] : T(0);
@@ -281,25 +268,40 @@ k_leg_adj(const typename V2<T>::t* __restrict__ F, int64_t F_stride, const T* __
       for (int i = 0; i < R; ++i) {
         mu2[i] = ma[i];
         mu1[i] = mb[i];
-#pragma unroll
-        for (int k = 0; k < NM; ++k) {
-          v[j * P + 2 * k] += ma[i] * eR[i][k];
-          v[j * P + 2 * k + 1] += ma[i] * eI[i][k];
-          v[(j + 1) * P + 2 * k] += mb[i] * oR[i][k];
-          v[(j + 1) * P + 2 * k + 1] += mb[i] * oI[i][k];
-        }
+        T2 v;
+        v.x = ma[i];
+        v.y = mb[i];
+        *reinterpret_cast<T2*>(muT + (tid + i * NT) * CHP + j) = v;
       }
     }
-    warp_reduce_scatter<T, NV>(v, lane);
-#pragma unroll
-    for (int q = 0; q < PER; ++q) red[warp][lane * PER + q] = v[q];
     __syncthreads();
-    for (int f = threadIdx.x; f < NV0; f += NT) {
-      T sum = 0;
+    // phase 2: rows (2 jrow, 2 jrow + 1) over the pairs of this slice
+    T acc[2 * P];
 #pragma unroll
-      for (int w = 0; w < NW; ++w) sum += red[w][f];
-      const int l = c0 + f / P;
-      if (l <= L) pout[(f % P) * nlm + l] = sum;
+    for (int q = 0; q < 2 * P; ++q) acc[q] = 0;
+    const int pb = slice * KS;
+#pragma unroll 4
+    for (int pp = 0; pp < KS; ++pp) {
+      const T2 mv = *reinterpret_cast<const T2*>(muT + (pb + pp) * CHP + 2 * jrow);
+      const T* e = eo + (pb + pp) * 2 * P;
+#pragma unroll
+      for (int q = 0; q < P; ++q) {
+        acc[q] += mv.x * e[q];
+        acc[P + q] += mv.y * e[P + q];
+      }
+    }
+    T* rs = red + (slice * NJ + jrow) * 2 * P;
+#pragma unroll
+    for (int q = 0; q < 2 * P; ++q) rs[q] = acc[q];
+    __syncthreads();
+    // phase 3: add the slices; output index f = row-pair j, q (q < P: even row, else odd)
+    for (int f = tid; f < NJ * 2 * P; f += NT) {
+      const int j = f / (2 * P), q = f % (2 * P);
+      T sum = 0;
+#pragma unroll 8
+      for (int sl = 0; sl < NSLICE; ++sl) sum += red[(sl * NJ + j) * 2 * P + q];
+      const int l = c0 + 2 * j + (q >= P ? 1 : 0);
+      if (l <= L) pout[(q % P) * nlm + l] = sum;
     }
     __syncthreads();
   }
@@ -325,14 +327,19 @@ __global__ void k_adj_reduce(const T* __restrict__ part, int nblk, int64_t nlm, 
 template <typename T> struct Cfg;
 template <> struct Cfg<float> {
   static constexpr int SR = 2, SNT = 128, SCH = 256;  // synthesis
-  static constexpr int AR = 2, ANT = 256;             // adjoint
-  template <int NM> static constexpr int ACH() { return NM >= 4 ? 8 : 16; }
+  static constexpr int AR = 2, ANT = 256, ACH = 32;   // adjoint (shared-memory GEMM form)
 };
 template <> struct Cfg<double> {
   static constexpr int SR = 2, SNT = 128, SCH = 256;
-  static constexpr int AR = 2, ANT = 256;
-  template <int NM> static constexpr int ACH() { return NM == 1 ? 16 : 8; }
+  static constexpr int AR = 1, ANT = 256, ACH = 16;
 };
+
+template <typename T, int NM>
+constexpr size_t adj2_smem() {
+  using C = Cfg<T>;
+  constexpr int P = 2 * NM, NR = C::ANT * C::AR, NJ = C::ACH / 2, NSLICE = C::ANT / NJ;
+  return sizeof(T) * ((size_t)NR * (C::ACH + 2) + (size_t)NR * 2 * P + (size_t)NSLICE * NJ * 2 * P);
+}
 
 template <typename T, int NM>
 int launch_synth(const Grid& g, const void* alm, int64_t alm_stride, void* F, int64_t F_stride,
@@ -370,10 +377,12 @@ int launch_adj(const Grid& g, const void* F, int64_t F_stride, T* part, double* 
   const T2* st = std::is_same<T, double>::value ? (const T2*)g.st64.p : (const T2*)g.st32.p;
   const T* yr = std::is_same<T, double>::value ? (const T*)g.y64.p : (const T*)g.y32.p;
   {
+    constexpr size_t sm = adj2_smem<T, NM>();
+    auto kern = k_leg_adj2<T, NM, C::AR, C::ANT, C::ACH>;
+    CMBWS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     ProfScope ps(PROF_LEG_ADJ, s, sizeof(T) == 8, 4.0 * g.npair * (double)nlm * (NM + 1));
-    k_leg_adj<T, NM, C::AR, C::ANT, C::template ACH<NM>()><<<grd, C::ANT, 0, s>>>(
-        (const T2*)F, F_stride, A, g.ls.as<int>(), st, yr, g.pair_ring.as<int2>(), part, nlm, L,
-        g.npair, g.nring);
+    kern<<<grd, C::ANT, sm, s>>>((const T2*)F, F_stride, A, g.ls.as<int>(), st, yr,
+                                 g.pair_ring.as<int2>(), part, nlm, L, g.npair);
     CMBWS_LAUNCH_CHECK();
   }
   dim3 rg((unsigned)((nlm + 255) / 256), NM);

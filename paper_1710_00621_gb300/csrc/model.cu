@@ -54,6 +54,14 @@ __global__ void k_mix_forward(HarmDev h, GroupDev gd, const double* __restrict__
     const int nu = gd.bands[j];
     double ar = 0.0, ai = 0.0;
     for (int k = 0; k < h.ncomp; ++k) {
+      const PairDev& pd = h.pairs[nu * h.ncomp + k];
+      if (pd.var) {
+        // Q~ x_k from the mixing chain (its output band-limit covers l <= L_nu)
+        const double2 t = pd.out[lm_off(pd.L, m) + (l - m)];
+        ar += t.x;
+        ai += t.y;
+        continue;
+      }
       const double q = h.q[nu * h.ncomp + k];
       ar += q * xr[k];
       ai += q * xi[k];
@@ -75,6 +83,14 @@ __global__ void k_mix_adjoint(HarmDev h, BandDev bd, int k, const double* __rest
   if (l > Lk) return;
   double yr = 0.0, yi = 0.0;
   for (int nu = 0; nu < h.nobs; ++nu) {
+    const PairDev& pd = h.pairs[nu * h.ncomp + k];
+    if (pd.var) {
+      // Q~^T B u_nu from the transposed mixing chain (covers l <= L_k)
+      const double2 t = pd.out[lm_off(pd.L, m) + (l - m)];
+      yr += t.x;
+      yi += t.y;
+      continue;
+    }
     const int Ln = bd.L[nu];
     if (l > Ln) continue;
     const double2 u = bd.out[nu][lm_off(Ln, m) + (l - m)];
@@ -83,12 +99,93 @@ __global__ void k_mix_adjoint(HarmDev h, BandDev bd, int k, const double* __rest
     yi += w * u.y;
   }
   const int64_t base = h.compOff[k] + packed_off(Lk, m);
-  const double ci = h.cinv[h.clOff[k] + l];
-  y[base + (l - m)] = yr + ci * x[base + (l - m)];
+  const double ci = x ? h.cinv[h.clOff[k] + l] : 0.0;
+  y[base + (l - m)] = yr + (x ? ci * x[base + (l - m)] : 0.0);
   if (m > 0) {
     const int64_t is = base + (Lk - m + 1) + (l - m);
-    y[is] = yi + ci * x[is];
+    y[is] = yi + (x ? ci * x[is] : 0.0);
   }
+}
+
+// ---- inputs of the variable-mixing chains (Eq. Q) ----
+// forward: slot j of mixing group mg <- c_lm x_{k_j}(l, m), zero-padded above L_k
+template <typename T2>
+__global__ void k_mixvar_fwd_in(HarmDev h, MixGroupDev mg, const double* __restrict__ x) {
+  const int m = blockIdx.y;
+  const int l = m + blockIdx.x * blockDim.x + threadIdx.x;
+  const int L = mg.L;
+  if (l > L) return;
+  const int64_t i = lm_off(L, m) + (l - m);
+  const double cc = mg.c[i];
+  for (int j = 0; j < mg.npairs; ++j) {
+    const int k = mg.k[j];
+    const int Lk = h.compL[k];
+    double vr = 0.0, vi = 0.0;
+    if (l <= Lk) {
+      const double* xk = x + h.compOff[k] + packed_off(Lk, m);
+      vr = xk[l - m];
+      vi = m > 0 ? xk[(Lk - m + 1) + (l - m)] : 0.0;
+    }
+    T2 v;
+    v.x = (decltype(v.x))(cc * vr);
+    v.y = (decltype(v.y))(cc * vi);
+    reinterpret_cast<T2*>(mg.alm)[(int64_t)j * mg.nlm + i] = v;
+  }
+}
+
+// transposed: slot j <- c_lm b_{nu_j, l} u_{nu_j}(l, m), zero-padded above L_nu
+template <typename T2>
+__global__ void k_mixvar_adj_in(HarmDev h, BandDev bd, MixGroupDev mg) {
+  const int m = blockIdx.y;
+  const int l = m + blockIdx.x * blockDim.x + threadIdx.x;
+  const int L = mg.L;
+  if (l > L) return;
+  const int64_t i = lm_off(L, m) + (l - m);
+  const double cc = mg.c[i];
+  for (int j = 0; j < mg.npairs; ++j) {
+    const int nu = mg.nu[j];
+    const int Ln = bd.L[nu];
+    double vr = 0.0, vi = 0.0;
+    if (l <= Ln) {
+      const double2 u = bd.out[nu][lm_off(Ln, m) + (l - m)];
+      const double b = h.beam[h.beamOff[nu] + l];
+      vr = b * u.x;
+      vi = b * u.y;
+    }
+    T2 v;
+    v.x = (decltype(v.x))(cc * vr);
+    v.y = (decltype(v.y))(cc * vi);
+    reinterpret_cast<T2*>(mg.alm)[(int64_t)j * mg.nlm + i] = v;
+  }
+}
+
+// per-ring sums of q and q^2 (unweighted, Eq. optimal-q) and the pixel factor q w
+__global__ void k_mixq(const double* __restrict__ q, const int64_t* __restrict__ roff,
+                       const double* __restrict__ rw, double* __restrict__ f64, float* __restrict__ f32,
+                       double2* __restrict__ sums) {
+  const int r = blockIdx.x;
+  const int64_t b = roff[r], e = roff[r + 1];
+  const double w = rw[r];
+  double s1 = 0.0, s2 = 0.0;
+  for (int64_t i = b + threadIdx.x; i < e; i += blockDim.x) {
+    const double v = q[i];
+    s1 += v;
+    s2 += v * v;
+    f64[i] = v * w;
+    f32[i] = (float)(v * w);
+  }
+  __shared__ double a1[256], a2[256];
+  a1[threadIdx.x] = s1;
+  a2[threadIdx.x] = s2;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      a1[threadIdx.x] += a1[threadIdx.x + o];
+      a2[threadIdx.x] += a2[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) sums[r] = make_double2(a1[0], a2[0]);
 }
 
 // ---- t = (U^+)^T r: band rows into the group inputs (times c_lm), prior rows into tp ----
@@ -347,6 +444,7 @@ HarmDev Model::harm() const {
   h.clOff = d_clOff.as<int64_t>();
   h.Up = d_Up.as<double>();
   h.Lup = Lup;
+  h.pairs = d_pairs.as<PairDev>();
   return h;
 }
 
@@ -362,6 +460,65 @@ BandDev Model::bands_dev(int prec) const {
     b.alm[nu] = (char*)G.alm.p + (size_t)j * nlm * 2 * prec_size(prec);
   }
   return b;
+}
+
+int Model::mix_chain(Group& G, int prec, cudaStream_t s) {
+  const Grid& g = *G.grid;
+  const void* pix[kMaxMaps];
+  for (int j = 0; j < G.nmaps; ++j) pix[j] = !is_f32(prec) ? pixQ64[G.bands[j]].p : pixQ32[G.bands[j]].p;
+  CMBWS_TRY(legendre_synth(g, prec, G.nmaps, G.alm.p, G.F.p, s));
+  CMBWS_TRY(ringfft_fused(g, prec, G.nmaps, G.F.p, pix, s));
+  CMBWS_TRY(legendre_adjoint(g, prec, G.nmaps, G.F.p, part.p, part.bytes, G.out.as<double>(), s));
+  return CMBWS_OK;
+}
+
+static MixGroupDev mix_dev(const Group& G, int ncomp) {
+  MixGroupDev mg{};
+  mg.L = G.grid->lmax;
+  mg.npairs = G.nmaps;
+  for (int j = 0; j < G.nmaps; ++j) {
+    mg.nu[j] = G.bands[j] / ncomp;
+    mg.k[j] = G.bands[j] % ncomp;
+  }
+  mg.c = G.grid->c64.as<double>();
+  mg.alm = G.alm.p;
+  mg.nlm = nlm_of(mg.L);
+  return mg;
+}
+
+// t_{nu,k} = Q~_{nu,k} x_k for every variable pair
+int Model::mixvar_forward(int prec, const double* x, cudaStream_t s) {
+  const HarmDev h = harm();
+  for (Group& G : mgroups) {
+    const MixGroupDev mg = mix_dev(G, ncomp);
+    dim3 grd((mg.L + 1 + 127) / 128, mg.L + 1);
+    {
+      ProfScope ps(PROF_HARM, s, is_f32(prec) ? 0 : 1);
+      if (!is_f32(prec)) k_mixvar_fwd_in<double2><<<grd, 128, 0, s>>>(h, mg, x);
+      else k_mixvar_fwd_in<float2><<<grd, 128, 0, s>>>(h, mg, x);
+      CMBWS_LAUNCH_CHECK();
+    }
+    CMBWS_TRY(mix_chain(G, prec, s));
+  }
+  return CMBWS_OK;
+}
+
+// s_{nu,k} = Q~_{nu,k}^T B_nu u_nu for every variable pair (u_nu in the band outputs)
+int Model::mixvar_adjoint(int prec, cudaStream_t s) {
+  const HarmDev h = harm();
+  const BandDev bd = bands_dev(prec);
+  for (Group& G : mgroups) {
+    const MixGroupDev mg = mix_dev(G, ncomp);
+    dim3 grd((mg.L + 1 + 127) / 128, mg.L + 1);
+    {
+      ProfScope ps(PROF_HARM, s, is_f32(prec) ? 0 : 1);
+      if (!is_f32(prec)) k_mixvar_adj_in<double2><<<grd, 128, 0, s>>>(h, bd, mg);
+      else k_mixvar_adj_in<float2><<<grd, 128, 0, s>>>(h, bd, mg);
+      CMBWS_LAUNCH_CHECK();
+    }
+    CMBWS_TRY(mix_chain(G, prec, s));
+  }
+  return CMBWS_OK;
 }
 
 int Model::mix_forward(Group& G, int prec, const double* x, cudaStream_t s) {
@@ -382,6 +539,7 @@ int Model::mix_forward(Group& G, int prec, const double* x, cudaStream_t s) {
 }
 
 int Model::project(const double* x, double* const* d, int prec, cudaStream_t s) {
+  if (nmix) CMBWS_TRY(mixvar_forward(prec, x, s));
   for (Group& G : groups) {
     const Grid& g = *G.grid;
     CMBWS_TRY(pixtmp.ensure((size_t)G.nmaps * g.npix * 8));
@@ -392,16 +550,18 @@ int Model::project(const double* x, double* const* d, int prec, cudaStream_t s) 
       CMBWS_CUDA(cudaMemcpyAsync(d[G.bands[j]], pixtmp.as<double>() + (size_t)j * g.npix,
                                  (size_t)g.npix * 8, cudaMemcpyDeviceToDevice, s));
   }
-  n_sht += nobs;
+  n_sht += nobs + 2 * nmix;
   return CMBWS_OK;
 }
 
 int Model::apply_A(const double* x, double* y, int prec, cudaStream_t s) {
   const HarmDev h = harm();
+  if (nmix) CMBWS_TRY(mixvar_forward(prec, x, s));
   for (Group& G : groups) {
     CMBWS_TRY(mix_forward(G, prec, x, s));
     CMBWS_TRY(group_chain(G, prec, 0, s));
   }
+  if (nmix) CMBWS_TRY(mixvar_adjoint(prec, s));
   const BandDev bd = bands_dev(prec);
   for (int k = 0; k < ncomp; ++k) {
     dim3 grd((Lk[k] + 1 + 127) / 128, Lk[k] + 1);
@@ -445,7 +605,7 @@ int Model::rhs(const double* const* d, const double* const* w1, const double* w2
     for (int j = 0; j < G.nmaps; ++j) {
       const int nu = G.bands[j];
       const int64_t n = g.npix;
-      ProfScope ps(PROF_HARM, s);
+      ProfScope ps(PROF_HARM, s, 1);
       k_rhs_pixels<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
           d[nu], w1 ? w1[nu] : nullptr, pixA64[nu].as<double>(), tausq[nu].as<double>(),
           pixtmp.as<double>() + j * n, n);
@@ -454,20 +614,21 @@ int Model::rhs(const double* const* d, const double* const* w1, const double* w2
     CMBWS_TRY(ringfft_analysis(g, ap, G.nmaps, pixtmp.as<double>(), 0, G.F.p, s));
     CMBWS_TRY(legendre_adjoint(g, ap, G.nmaps, G.F.p, part.p, part.bytes, G.out.as<double>(), s));
   }
+  // transposed variable mixing of B u_nu, then the epilogue without a prior term (x = NULL)
+  if (nmix) CMBWS_TRY(mixvar_adjoint(ap, s));
   const BandDev bd = bands_dev(ap);
-  CMBWS_CUDA(cudaMemsetAsync(zero.p, 0, (size_t)nvec * 8, s));
   for (int k = 0; k < ncomp; ++k) {
     dim3 grd((Lk[k] + 1 + 127) / 128, Lk[k] + 1);
-    // x = 0 here, so the prior term of the epilogue vanishes
-    ProfScope ps(PROF_HARM, s);
-    k_mix_adjoint<<<grd, 128, 0, s>>>(h, bd, k, zero.as<double>(), b);
+    ProfScope ps(PROF_HARM, s, 1);
+    k_mix_adjoint<<<grd, 128, 0, s>>>(h, bd, k, nullptr, b);
     CMBWS_LAUNCH_CHECK();
     if (w2) {
+      ProfScope ps2(PROF_HARM, s, 1);
       k_add_scaled_prior<<<grd, 128, 0, s>>>(h, w2, b, k);
       CMBWS_LAUNCH_CHECK();
     }
   }
-  n_sht += nobs;
+  n_sht += nobs + 2 * nmix;
   return CMBWS_OK;
 }
 
@@ -603,6 +764,79 @@ int model_create(const cmbws_model_desc* desc, int prec, cudaStream_t s, Model**
     CMBWS_LAUNCH_CHECK();
   }
 
+  // ---- spatially variable mixing (Eq. Q) ----
+  std::vector<double> qpre(q);  // scalars of the preconditioner (Eq. optimal-q for variable pairs)
+  std::vector<PairDev> pairs((size_t)no * nc);
+  for (auto& pd : pairs) pd = PairDev{nullptr, nullptr, nullptr, nullptr, 0, 0};
+  M->pixQ64.resize((size_t)no * nc);
+  M->pixQ32.resize((size_t)no * nc);
+  if (desc->mix_grid && desc->mix_map) {
+    for (int nu = 0; nu < no; ++nu)
+      for (int k = 0; k < nc; ++k) {
+        const int id = nu * nc + k;
+        if (!desc->mix_map[id]) continue;
+        Grid* g = reinterpret_cast<Grid*>(desc->mix_grid[id]);
+        if (!g || g->device != dev) {
+          set_error("cmbws_model_create: mixing pair (%d, %d) has no grid on this device", nu, k);
+          return CMBWS_ERR_ARG;
+        }
+        if (g->lmax < std::max(M->Lk[k], M->Lnu[nu]) || !ringfft_smem_ok(*g, CMBWS_FP64)) {
+          set_error("cmbws_model_create: mixing grid of pair (%d, %d) needs lmax >= %d", nu, k,
+                    std::max(M->Lk[k], M->Lnu[nu]));
+          return CMBWS_ERR_ARG;
+        }
+        int gi = -1;
+        for (size_t i = 0; i < M->mgroups.size(); ++i)
+          if (M->mgroups[i].grid == g && M->mgroups[i].nmaps < kMaxMaps) gi = (int)i;
+        if (gi < 0) {
+          M->mgroups.emplace_back();
+          M->mgroups.back().grid = g;
+          gi = (int)M->mgroups.size() - 1;
+        }
+        Group& G = M->mgroups[gi];
+        G.bands[G.nmaps++] = id;
+        CMBWS_TRY(M->pixQ64[id].alloc(g->npix * 8));
+        CMBWS_TRY(M->pixQ32[id].alloc(g->npix * 4));
+        DevMem sums;
+        CMBWS_TRY(sums.alloc((size_t)g->nring * 16));
+        k_mixq<<<g->nring, 256, 0, s>>>(desc->mix_map[id], g->ring_off.as<int64_t>(),
+                                         g->ring_w64.as<double>(), M->pixQ64[id].as<double>(),
+                                         M->pixQ32[id].as<float>(), sums.as<double2>());
+        CMBWS_LAUNCH_CHECK();
+        std::vector<double> hs(2 * g->nring);
+        CMBWS_CUDA(cudaMemcpyAsync(hs.data(), sums.p, hs.size() * 8, cudaMemcpyDeviceToHost, s));
+        CMBWS_CUDA(cudaStreamSynchronize(s));
+        double s1 = 0.0, s2 = 0.0;
+        for (int r = 0; r < g->nring; ++r) {
+          s1 += hs[2 * r];
+          s2 += hs[2 * r + 1];
+        }
+        if (!(s1 != 0.0) || !std::isfinite(s2)) {
+          set_error("cmbws_model_create: mixing map of pair (%d, %d) sums to zero", nu, k);
+          return CMBWS_ERR_ARG;
+        }
+        qpre[id] = s2 / s1;  // Eq. optimal-q
+        M->nmix += 1;
+      }
+  }
+  for (Group& G : M->mgroups) {
+    const Grid& g = *G.grid;
+    const int64_t nlm = nlm_of(g.lmax);
+    CMBWS_TRY(G.alm.alloc((size_t)G.nmaps * nlm * 16));
+    CMBWS_TRY(G.F.alloc((size_t)G.nmaps * g.nring * (g.lmax + 1) * 16));
+    CMBWS_TRY(G.out.alloc((size_t)G.nmaps * nlm * 16));
+    for (int j = 0; j < G.nmaps; ++j) {
+      PairDev& pd = pairs[G.bands[j]];
+      pd.out = G.out.as<double2>() + j * nlm;
+      pd.alm64 = (char*)G.alm.p + (size_t)j * nlm * 16;
+      pd.alm32 = (char*)G.alm.p + (size_t)j * nlm * 8;
+      pd.c = g.c64.as<double>();
+      pd.L = g.lmax;
+      pd.var = 1;
+    }
+  }
+  CMBWS_TRY(M->d_pairs.upload(pairs.data(), pairs.size() * sizeof(PairDev)));
+
   // ---- U blocks (Eqs. U-data, U-prior) and U^+ (Sec. 3.1) ----
   M->Lup = M->Lcomp;
   const int nr = no + nc;
@@ -617,7 +851,7 @@ int model_create(const cmbws_model_desc* desc, int prec, cudaStream_t s, Model**
       const int k = act[a];
       for (int nu = 0; nu < no; ++nu)
         if (l <= M->Lnu[nu])
-          U[(size_t)nu * na + a] = M->alpha[nu] * desc->beam[nu][l] * q[nu * nc + k];
+          U[(size_t)nu * na + a] = M->alpha[nu] * desc->beam[nu][l] * qpre[nu * nc + k];
       U[(size_t)(no + k) * na + a] = cinv_k[k][l];
     }
     if (!pinv_jacobi(U, nr, na, 1e-12, P)) {
@@ -650,10 +884,11 @@ int model_create(const cmbws_model_desc* desc, int prec, cudaStream_t s, Model**
     CMBWS_TRY(G.out.alloc((size_t)G.nmaps * nlm * 16));
     part_bytes = std::max(part_bytes, legendre_adjoint_part_bytes(g, CMBWS_FP64, G.nmaps));
   }
+  for (Group& G : M->mgroups)
+    part_bytes = std::max(part_bytes, legendre_adjoint_part_bytes(*G.grid, CMBWS_FP64, G.nmaps));
   CMBWS_TRY(M->part.alloc(part_bytes));
   CMBWS_TRY(M->tprior.alloc((size_t)M->nvec * 8));
-  CMBWS_TRY(M->zero.alloc((size_t)M->nvec * 8));
-  M->nsht_A = 2 * no;  // 2 (2 Nmix + Nobs) with Nmix = 0 (scalar mixing)
+  M->nsht_A = 2 * (2 * M->nmix + no);  // Sec. 3.3: 2 (2 Nmix + Nobs)
   M->nsht_M = 2 * no;
   CMBWS_CUDA(cudaStreamSynchronize(s));
   *out = guard.release();

@@ -12,6 +12,16 @@ constexpr int kMaxComp = 8;    // components
 constexpr int kMaxBands = 16;  // observations
 constexpr int kMaxMaps = 8;    // bands transformed together on one grid
 
+// Variable mixing pair (nu, k), device view (array of nobs * ncomp in device memory).
+struct PairDev {
+  const double2* out;  // chain output of the pair (internal layout of its mixing grid, FP64)
+  void* alm64;         // chain input slot, FP64 / FP32X2 layout
+  void* alm32;         // chain input slot, FP32 layout
+  const double* c;     // c_lm of the mixing grid
+  int L;               // mixing-grid band-limit
+  int var;             // 1 if the pair is variable
+};
+
 // Device view of the harmonic-space model tables (kernel argument by value).
 struct HarmDev {
   int ncomp, nobs, Lup;
@@ -24,6 +34,7 @@ struct HarmDev {
   const double* cisq;      // C_{k,l}^-1/2
   const int64_t* clOff;
   const double* Up;        // U^+ [Lup+1][ncomp][nobs+ncomp]
+  const PairDev* pairs;    // [nobs * ncomp] variable-mixing pairs (var = 0: scalar q)
 };
 
 struct GroupDev {
@@ -39,6 +50,14 @@ struct BandDev {
   const double2* out[kMaxBands];  // adjoint-chain result of band nu (internal layout, FP64)
   const double* c[kMaxBands];     // c_lm of band nu's grid
   void* alm[kMaxBands];           // chain input slot of band nu (T2)
+};
+
+struct MixGroupDev {
+  int L, npairs;
+  int nu[kMaxMaps], k[kMaxMaps];
+  const double* c;
+  void* alm;
+  int64_t nlm;
 };
 
 struct Group {
@@ -62,16 +81,25 @@ struct Model {
   std::vector<double> alpha;
   std::vector<DevMem> pixA64, pixA32, pixM64, pixM32, tausq;
   DevMem d_compL, d_compOff, d_q, d_beam, d_beamOff, d_cinv, d_cisq, d_clOff, d_Up;
-  DevMem part, tprior, zero, pixtmp;
+  DevMem part, tprior, pixtmp;
   int nsht_A = 0, nsht_M = 0;
   long long n_sht = 0;  // SHTs executed since creation (paper's counting)
 
   // CG workspace (cg.cu)
   DevMem cg_r, cg_z, cg_p, cg_q, cg_d, cg_x, cg_red;
 
+  // spatially variable mixing (Eq. Q)
+  int nmix = 0;
+  std::vector<Group> mgroups;             // pairs sharing a mixing grid; bands[] holds pair ids
+  std::vector<DevMem> pixQ64, pixQ32;     // q_{nu,k}(n) w(n) per pair id (empty if scalar)
+  DevMem d_pairs;                         // PairDev [nobs * ncomp]
+
   HarmDev harm() const;
   BandDev bands_dev(int prec) const;
   int group_chain(Group& G, int prec, int which, cudaStream_t s);
+  int mix_chain(Group& G, int prec, cudaStream_t s);
+  int mixvar_forward(int prec, const double* x, cudaStream_t s);
+  int mixvar_adjoint(int prec, cudaStream_t s);
   int mix_forward(Group& G, int prec, const double* x, cudaStream_t s);
   int project(const double* x, double* const* d, int prec, cudaStream_t s);
   int apply_A(const double* x, double* y, int prec, cudaStream_t s);

@@ -35,12 +35,28 @@ class GridCache:
         return self.grids[key]
 
 
-def gpu_model(work, inp, prec=cw.CMBWS_FP64, cache=None):
+def gpu_model(work, inp, prec=cw.CMBWS_FP64, cache=None, mix=None):
+    """mix: optional (mix_grid_lmax[nu][k] or None, mix_map[nu][k] numpy or None) for variable
+    mixing on Gauss-Legendre grids."""
     cache = cache or GridCache()
     grids = [cache.get(b) for b in work.bands]
     ninv = [to_dev(t) for t in inp["tau"]]
+    mg = mm = None
+    if mix is not None:
+        lm, maps = mix
+        gl = {}
+        mg = [[None] * len(work.comps) for _ in work.bands]
+        mm = [[None] * len(work.comps) for _ in work.bands]
+        for nu in range(len(work.bands)):
+            for k in range(len(work.comps)):
+                if maps[nu][k] is None:
+                    continue
+                if lm[nu][k] not in gl:
+                    gl[lm[nu][k]] = cw.cmbws_plan_grid(cw.CMBWS_GRID_GL, lm[nu][k] + 1, lm[nu][k])
+                mg[nu][k] = gl[lm[nu][k]]
+                mm[nu][k] = to_dev(maps[nu][k])
     m = cw.cmbws_model_create([c.lmax for c in work.comps], grids, inp["beams"], inp["cl"], ninv,
-                              inp["q"], prec)
+                              inp["q"], prec, mix_grids=mg, mix_maps=mm)
     return m, grids
 
 
