@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--no-fp64-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--inner-tol", type=float, default=1e-3,
+                    help="relative residual reduction per refinement pass (FP32 solves)")
     ap.add_argument("--cert", default="fp32x2", choices=["fp32x2", "fp64"],
                     help="arithmetic of the FP64-accurate residual applies of the mixed solve")
     return ap.parse_args()
@@ -163,13 +165,16 @@ def build_problem(work, prec, seed_offset=0):
     return dict(grids=band_grids, inp=inp, m64=m64, model=m_run, d=d, x_true=x_true)
 
 
+INNER_TOL = [1e-3]
+
+
 def solve_step(P, model, tol, x, b, cert="fp32x2"):
     import paper_1710_00621_gb300 as cw
     cw.cmbws_rhs(model, P["d"], b)
     x.zero_()
     cp = cw.CMBWS_FP32X2 if cert == "fp32x2" else cw.CMBWS_FP64
-    return cw.cmbws_cg_solve(model, b, x, tol=tol, maxiter=3000, precond=1, inner_tol=1e-3,
-                             max_outer=30, cert_prec=cp)
+    return cw.cmbws_cg_solve(model, b, x, tol=tol, maxiter=3000, precond=1,
+                             inner_tol=INNER_TOL[0], max_outer=30, cert_prec=cp)
 
 
 def roofline(prof):
@@ -249,6 +254,7 @@ def main():
         return run_reference(args)
     import torch
     import paper_1710_00621_gb300 as cw
+    INNER_TOL[0] = args.inner_tol
     rank, world, local = dist_init(args.gpus)
     work = workload(args.scale)
     P = build_problem(work, args.prec, seed_offset=rank)
@@ -344,7 +350,7 @@ def main():
             "data": "synthetic",
             "config": {"workload": work.name, "ncomp": len(work.comps), "nobs": len(work.bands),
                        "band_nside": [b.n for b in work.bands], "lmax_comp": [c.lmax for c in work.comps],
-                       "tol": args.tol, "precond": "M_PI",
+                       "tol": args.tol, "inner_tol": args.inner_tol, "precond": "M_PI",
                        "arithmetic": ("FP32 transforms, FP64 vectors/scalars, iterative refinement "
                                       f"certified by FP64-accurate ({cert}) applies"
                                       if args.prec == "fp32" else "FP64"),
