@@ -257,6 +257,20 @@ typedef struct {
 int cmbws_cg_solve(cmbws_model m, const double* b, double* x, const cmbws_cg_opts* opts,
                    cmbws_cg_report* report, void* stream);
 
+/*
+ * Solve nprob independent systems A_i x_i = b_i (each as cmbws_cg_solve) concurrently.
+ *   models: [nprob] distinct models (each owns its workspace); b, x: host arrays [nprob] of
+ *   device stacked vectors.  reports: [nprob] or NULL.
+ * The problems are distributed over nworkers host threads (<= 0: 8), each driving its own
+ * CUDA stream, so the kernels of different problems overlap on the GPU.  Work already
+ * queued on `stream` completes before the solves start; the call returns after all solves
+ * have finished.  Returns CMBWS_OK if every problem succeeded, else the first failing
+ * problem's code (all reports are filled either way).
+ */
+int cmbws_cg_solve_batched(const cmbws_model* models, int nprob, const double* const* b,
+                           double* const* x, const cmbws_cg_opts* opts, cmbws_cg_report* reports,
+                           int nworkers, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -23,6 +23,7 @@ from .binding import (  # noqa: F401
     cmbws_apply_A,
     cmbws_apply_precond,
     cmbws_cg_solve,
+    cmbws_cg_solve_batched,
     cmbws_grid_destroy,
     cmbws_grid_info,
     cmbws_grid_rings,

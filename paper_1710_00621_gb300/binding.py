@@ -97,6 +97,8 @@ def load_library(path=None):
     lib.cmbws_profile_read.argtypes = [ctypes.POINTER(d), ctypes.POINTER(ctypes.c_int64),
                                        ctypes.POINTER(d), i]
     lib.cmbws_cg_solve.argtypes = [vp, vp, vp, ctypes.POINTER(CgOpts), ctypes.POINTER(CgReport), vp]
+    lib.cmbws_cg_solve_batched.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                           ctypes.POINTER(CgOpts), ctypes.POINTER(CgReport), i, vp]
     _lib = lib
     return lib
 
@@ -376,4 +378,25 @@ def cmbws_cg_solve(model, b, x, tol=1e-6, maxiter=1000, precond=1, inner_tol=1e-
         _check(code)
     out = rep.as_dict()
     out["code"] = code
+    return out
+
+
+def cmbws_cg_solve_batched(models, b, x, tol=1e-6, maxiter=1000, precond=1, inner_tol=1e-3,
+                           max_outer=20, timeout_s=0.0, cert_prec=CMBWS_FP64, nworkers=8,
+                           stream=None, check=True):
+    """Solve the independent systems models[i] x[i] = b[i] concurrently; returns the reports."""
+    n = len(models)
+    opts = CgOpts(float(tol), int(maxiter), int(precond), float(inner_tol), int(max_outer),
+                  float(timeout_s), int(cert_prec))
+    reps = (CgReport * n)()
+    mh = (ctypes.c_void_p * n)(*[_handle(m) for m in models])
+    bp = (ctypes.c_void_p * n)(*[_dptr(b[i], models[i].nvec, f"b[{i}]").value for i in range(n)])
+    xp = (ctypes.c_void_p * n)(*[_dptr(x[i], models[i].nvec, f"x[{i}]").value for i in range(n)])
+    code = load_library().cmbws_cg_solve_batched(mh, n, bp, xp, ctypes.byref(opts), reps,
+                                                 int(nworkers), _stream(stream))
+    if check:
+        _check(code)
+    out = [r.as_dict() for r in reps]
+    for r in out:
+        r["code"] = r["status"]
     return out

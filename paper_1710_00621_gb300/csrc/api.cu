@@ -94,6 +94,31 @@ ProfScope::~ProfScope() {
   g_prof.push_back({slot, flops, a, b});
 }
 
+int ensure_dyn_smem(const void* func, size_t bytes) {
+  // fixed table (no host allocation): one slot per (kernel, device)
+  struct Slot {
+    const void* func;
+    int dev;
+    size_t bytes;
+  };
+  static std::mutex mu;
+  static Slot lim[512];
+  static int nlim = 0;
+  int dev = 0;
+  CMBWS_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  for (int i = 0; i < nlim; ++i)
+    if (lim[i].func == func && lim[i].dev == dev) {
+      if (lim[i].bytes >= bytes) return CMBWS_OK;
+      CMBWS_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+      lim[i].bytes = bytes;
+      return CMBWS_OK;
+    }
+  CMBWS_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  if (nlim < 512) lim[nlim++] = Slot{func, dev, bytes};
+  return CMBWS_OK;
+}
+
 static int check_device(const Grid& g) {
   int dev = -1;
   CMBWS_CUDA(cudaGetDevice(&dev));

@@ -11,8 +11,12 @@
 // residual falls by inner_tol, then x += d and r = b - A x with an
 // FP64-accurate chain (native FP64 or double-float, opts.cert_prec); the loop
 // ends when that residual certifies tol.
+#include <atomic>
 #include <chrono>
 #include <cmath>
+#include <string>
+#include <thread>
+#include <vector>
 
 #include "model.h"
 
@@ -329,4 +333,71 @@ extern "C" int cmbws_cg_solve(cmbws_model mh, const double* b, double* x, const 
   rep.status = st;
   if (report) *report = rep;
   return st;
+}
+
+extern "C" int cmbws_cg_solve_batched(const cmbws_model* models, int nprob, const double* const* b,
+                                      double* const* x, const cmbws_cg_opts* opts,
+                                      cmbws_cg_report* reports, int nworkers, void* stream) {
+  clear_error();
+  if (!models || nprob < 1 || !b || !x || !opts || !(opts->tol > 0.0) || opts->maxiter < 1) {
+    set_error("cmbws_cg_solve_batched: invalid arguments");
+    return CMBWS_ERR_ARG;
+  }
+  for (int i = 0; i < nprob; ++i) {
+    if (!models[i] || !b[i] || !x[i] || b[i] == x[i]) {
+      set_error("cmbws_cg_solve_batched: invalid arguments for problem %d", i);
+      return CMBWS_ERR_ARG;
+    }
+    for (int j = 0; j < i; ++j)
+      if (models[j] == models[i]) {
+        set_error("cmbws_cg_solve_batched: problems %d and %d share a model (workspace)", j, i);
+        return CMBWS_ERR_ARG;
+      }
+  }
+  cmbws_cg_opts o = *opts;
+  if (!(o.inner_tol > 0.0 && o.inner_tol < 1.0)) o.inner_tol = 1e-3;
+  if (o.max_outer < 1) o.max_outer = 20;
+  int dev = 0;
+  CMBWS_CUDA(cudaGetDevice(&dev));
+  // work queued on the caller's stream (the inputs) completes before the solves start
+  CMBWS_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  const int nw = std::max(1, std::min(nworkers > 0 ? nworkers : 8, nprob));
+  std::vector<cudaStream_t> ws(nw, nullptr);
+  for (int w = 0; w < nw; ++w)
+    if (cudaStreamCreateWithFlags(&ws[w], cudaStreamNonBlocking) != cudaSuccess) {
+      for (int v = 0; v < w; ++v) cudaStreamDestroy(ws[v]);
+      set_error("cmbws_cg_solve_batched: stream creation failed");
+      return CMBWS_ERR_CUDA;
+    }
+  std::vector<cmbws_cg_report> rep(nprob);
+  std::vector<std::string> msg(nprob);
+  std::atomic<int> next(0);
+  auto worker = [&](int w) {
+    cudaSetDevice(dev);
+    for (int i = next.fetch_add(1); i < nprob; i = next.fetch_add(1)) {
+      Model* M = reinterpret_cast<Model*>(models[i]);
+      cmbws_cg_report r{};
+      const auto t0 = std::chrono::steady_clock::now();
+      clear_error();
+      const int st = cg_solve_impl(*M, b[i], x[i], o, r, ws[w]);
+      r.ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      r.status = st;
+      if (st != CMBWS_OK) msg[i] = cmbws_last_error();
+      rep[i] = r;
+    }
+  };
+  std::vector<std::thread> th;
+  for (int w = 1; w < nw; ++w) th.emplace_back(worker, w);
+  worker(0);
+  for (auto& t : th) t.join();
+  for (int w = 0; w < nw; ++w) cudaStreamDestroy(ws[w]);
+  int status = CMBWS_OK;
+  for (int i = 0; i < nprob; ++i) {
+    if (reports) reports[i] = rep[i];
+    if (status == CMBWS_OK && rep[i].status != CMBWS_OK) {
+      status = rep[i].status;
+      set_error("cmbws_cg_solve_batched: problem %d: %s", i, msg[i].c_str());
+    }
+  }
+  return status;
 }

@@ -180,6 +180,11 @@ int legendre_synth_df(const Grid& g, int nmaps, const void* alm, void* F, cudaSt
 int legendre_adj_df_chunk(const Grid& g, int nm, const void* F, double* part, cudaStream_t s);
 int legendre_df_adj_nblk(const Grid& g);
 
+// Raise a kernel's dynamic shared-memory limit to at least `bytes` on the current device.
+// The limit only ever grows, so concurrent launches with different sizes (several host
+// threads, cmbws_cg_solve_batched) never see it lowered under them.
+int ensure_dyn_smem(const void* func, size_t bytes);
+
 // ---- kernel timing (api.cu): CUDA events around launches while enabled ----
 // Stages; a record's slot is stage + PROF_N * arith, arith 0 = FP32, 1 = FP64,
 // 2 = double-float (FP32X2).  `flops` is the algorithmic count of the launch (full (l, m)

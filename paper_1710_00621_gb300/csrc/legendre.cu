@@ -379,7 +379,7 @@ int launch_adj(const Grid& g, const void* F, int64_t F_stride, T* part, double* 
   {
     constexpr size_t sm = adj2_smem<T, NM>();
     auto kern = k_leg_adj2<T, NM, C::AR, C::ANT, C::ACH>;
-    CMBWS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    CMBWS_TRY(ensure_dyn_smem((const void*)kern, sm));
     ProfScope ps(PROF_LEG_ADJ, s, sizeof(T) == 8, 4.0 * g.npair * (double)nlm * (NM + 1));
     kern<<<grd, C::ANT, sm, s>>>((const T2*)F, F_stride, A, g.ls.as<int>(), st, yr,
                                  g.pair_ring.as<int2>(), part, nlm, L, g.npair);

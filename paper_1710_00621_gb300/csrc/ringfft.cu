@@ -271,7 +271,7 @@ int launch(const Grid& g, int nmaps, void* F, double* map_out, const double* map
     return CMBWS_ERR_ARG;
   }
   auto kern = k_ringfft<T, MODE>;
-  CMBWS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  CMBWS_TRY(ensure_dyn_smem((const void*)kern, sm));
   const int64_t fs = (int64_t)g.nring * (g.lmax + 1);
   const bool dbl = sizeof(T) == 8;
   const T* rw = nullptr;

@@ -214,3 +214,26 @@ def make_inputs(work, pixel_coords, pixel_weights, with_noise=True):
         noise = [sigmas[nu] * rng_n.standard_normal(sigmas[nu].size) for nu in range(len(work.bands))]
     return dict(tau=taus, sigma=sigmas, cl=cls, q=work.q(), beams=work.beams(),
                 x_true=np.concatenate(x_parts), noise=noise)
+
+
+def batched_uneven(nprob=64, lmin=128, lmax=1024, fmax=0.3, seed_offset=0):
+    """Independent problems (Ncomp = 2: CMB + dust beta 1.6; Nobs = 3: 30/100/353 GHz) with
+    band-limits L_p ~ U{lmin..lmax} on Gauss-Legendre grids and a galactic-band mask
+    |b| < b0, sin b0 = f_p ~ U[0, fmax] (sky fraction f_p), applied through the mixing maps.
+    Returns [(workload, f_p)]."""
+    rng = np.random.default_rng([SEED_BASE + 3, seed_offset])
+    out = []
+    for p in range(nprob):
+        L = int(rng.integers(lmin, lmax + 1))
+        f = float(rng.uniform(0.0, fmax))
+        bands = [Band(fr, "gl", L, L, fw, 10.0) for fr, fw in ((30.0, 60.0), (100.0, 40.0), (353.0, 30.0))]
+        comps = [Comp("cmb", L, "cmb", None, 1.0, 0.40), Comp("dust", L, "dust", 1.6, 353.0, 0.75)]
+        w = Workload(f"batched_p{p}_gl{L}_f{f:.3f}", SEED_BASE + 3 + 1000 * (p + 1) + seed_offset,
+                     bands, comps)
+        out.append((w, f))
+    return out
+
+
+def galactic_mask(z, f):
+    """1 outside the band |b| < b0 with sin b0 = f (b = 90 deg - theta, so sin b = z), 0 inside."""
+    return (np.abs(z) >= f).astype(np.float64)

@@ -209,3 +209,43 @@ def test_variable_mixing_rhs_and_solve():
     assert rep["rel_res"] <= 1e-8
     r = bref - om.apply_A(m, to_host(x))
     assert np.linalg.norm(r) / np.linalg.norm(bref) <= 1.01e-8
+
+
+def test_batched_solve_equals_sequential_solves():
+    # independent uneven problems (GL L 12..40, galactic-band masks through the mixing maps),
+    # solved concurrently and one by one: identical results (all reductions are deterministic)
+    import skygen
+    from oracle import grids as og
+    probs = skygen.batched_uneven(nprob=6, lmin=12, lmax=40)
+    models, bs, ms_o = [], [], []
+    for work, f in probs:
+        m, inp = oracle_model(work)
+        L = work.bands[0].lmax
+        g = og.gauss_legendre(L)
+        z = np.cos(g.pixel_angles()[0])
+        mask = skygen.galactic_mask(z, f)
+        maps = [[m.q[nu, k] * mask for k in range(m.ncomp)] for nu in range(m.nobs)]
+        lm = [[L] * m.ncomp for _ in range(m.nobs)]
+        gm, _ = gpu_model(work, inp, cw.CMBWS_FP32, mix=(lm, maps))
+        b = om.rhs(m, [mp + n for mp, n in zip(om.project(m, inp["x_true"]), inp["noise"])])
+        models.append(gm)
+        bs.append(to_dev(b))
+        ms_o.append((m, b))
+    xs = [to_dev(np.zeros(g.nvec)) for g in models]
+    reps = cw.cmbws_cg_solve_batched(models, bs, xs, tol=1e-6, maxiter=3000,
+                                     cert_prec=cw.CMBWS_FP32X2, nworkers=4)
+    assert all(r["status"] == 0 and r["rel_res"] <= 1e-6 for r in reps)
+    for i, g in enumerate(models):
+        xi = to_dev(np.zeros(g.nvec))
+        r1 = cw.cmbws_cg_solve(g, bs[i], xi, tol=1e-6, maxiter=3000, cert_prec=cw.CMBWS_FP32X2)
+        np.testing.assert_array_equal(to_host(xi), to_host(xs[i]))
+        assert r1["iters"] == reps[i]["iters"]
+    # the first problem's certified residual, recomputed by the oracle
+    m, b = ms_o[0]
+    mg = [[og.gauss_legendre(m.lmax_band[0])] * m.ncomp for _ in range(m.nobs)]
+    z = np.cos(mg[0][0].pixel_angles()[0])
+    mask = skygen.galactic_mask(z, probs[0][1])
+    mo, _ = oracle_model(probs[0][0], mix_maps=[[m.q[nu, k] * mask for k in range(m.ncomp)]
+                                                 for nu in range(m.nobs)], mix_grids=mg)
+    r = b - om.apply_A(mo, to_host(xs[0]))
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.01e-6
