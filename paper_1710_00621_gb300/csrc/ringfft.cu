@@ -43,8 +43,19 @@ __device__ __forceinline__ T2 cconj(T2 a) {
 __device__ __forceinline__ void sincospi_t(double x, double* s, double* c) { sincospi(x, s, c); }
 __device__ __forceinline__ void sincospi_t(float x, float* s, float* c) { sincospif(x, s, c); }
 
-// In-place radix-2 transform of size N (power of two >= 1) in shared memory.
+// In-place power-of-two transform of size N (>= 1) in shared memory, decimation in
+// time after a bit-reversal permutation; two radix-2 stages per pass (each thread owns
+// a closed group of 4 elements i, i+h, i+2h, i+3h), so one barrier per two stages.
 // tw[k] = exp(-2 pi i k / NMAX), k < NMAX/2.  inverse: exp(+2 pi i ...), unnormalised.
+template <typename T2>
+__device__ __forceinline__ void bfly(T2& a, T2& b, T2 w) {
+  const T2 v = cmul(b, w);
+  b.x = a.x - v.x;
+  b.y = a.y - v.y;
+  a.x += v.x;
+  a.y += v.y;
+}
+
 template <typename T2>
 __device__ void smem_fft(T2* buf, int N, const T2* __restrict__ tw, int nmax, bool inverse) {
   if (N < 2) return;
@@ -58,21 +69,43 @@ __device__ void smem_fft(T2* buf, int N, const T2* __restrict__ tw, int nmax, bo
     }
   }
   __syncthreads();
-  for (int lg = 1; lg <= logN; ++lg) {
+  int lg = 1;
+  for (; lg + 1 <= logN; lg += 2) {
+    const int h = 1 << (lg - 1);  // stage lg pairs (i, i+h); stage lg+1 pairs (i, i+2h)
+    const int s1 = nmax >> lg, s2 = nmax >> (lg + 1);
+    for (int b = threadIdx.x; b < N / 4; b += blockDim.x) {
+      const int pos = b & (h - 1);
+      const int i = ((b >> (lg - 1)) << (lg + 1)) + pos;
+      T2 w1 = tw[pos * s1], w2a = tw[pos * s2], w2b = tw[(pos + h) * s2];
+      if (inverse) {
+        w1.y = -w1.y;
+        w2a.y = -w2a.y;
+        w2b.y = -w2b.y;
+      }
+      T2 x0 = buf[i], x1 = buf[i + h], x2 = buf[i + 2 * h], x3 = buf[i + 3 * h];
+      bfly(x0, x1, w1);
+      bfly(x2, x3, w1);
+      bfly(x0, x2, w2a);
+      bfly(x1, x3, w2b);
+      buf[i] = x0;
+      buf[i + h] = x1;
+      buf[i + 2 * h] = x2;
+      buf[i + 3 * h] = x3;
+    }
+    __syncthreads();
+  }
+  if (lg == logN) {  // odd number of stages: one radix-2 stage left
     const int half = 1 << (lg - 1);
     const int tstride = nmax >> lg;
     for (int b = threadIdx.x; b < N / 2; b += blockDim.x) {
       const int pos = b & (half - 1);
       const int i = ((b >> (lg - 1)) << lg) + pos;
-      const int j = i + half;
       T2 w = tw[pos * tstride];
       if (inverse) w.y = -w.y;
-      const T2 u = buf[i];
-      const T2 v = cmul(buf[j], w);
-      buf[i].x = u.x + v.x;
-      buf[i].y = u.y + v.y;
-      buf[j].x = u.x - v.x;
-      buf[j].y = u.y - v.y;
+      T2 x0 = buf[i], x1 = buf[i + half];
+      bfly(x0, x1, w);
+      buf[i] = x0;
+      buf[i + half] = x1;
     }
     __syncthreads();
   }
@@ -136,6 +169,7 @@ k_ringfft(typename V2<T>::t* __restrict__ F, int64_t F_stride, double* __restric
   using T2 = typename V2<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T2* buf = reinterpret_cast<T2*>(smem_raw);
+  T2* ptab = buf + nmax;  // exp(i pi k / n), k < n (shifted rings only)
 
   const int p = blockIdx.x;
   const int k = blockIdx.y;
@@ -150,41 +184,69 @@ k_ringfft(typename V2<T>::t* __restrict__ F, int64_t F_stride, double* __restric
   const int64_t offS = has_s ? roff[rr.y] : 0;
   const T rs2 = T(0.70710678118654752440);  // 1/sqrt(2)
   const T sq2 = T(1.41421356237309504880);
+  // Shifted rings (phi0 = pi / n): exp(i m phi0) = (-1)^(m div n) exp(i pi (m mod n) / n),
+  // so one table of n phases serves every alias of every frequency.
+  if (ph) {
+    for (int kk = threadIdx.x; kk < n; kk += blockDim.x) {
+      T s, c;
+      sincospi_t(T(kk) / T(n), &s, &c);
+      T2 e;
+      e.x = c;
+      e.y = s;
+      ptab[kk] = e;
+    }
+    __syncthreads();
+  }
 
   if (MODE == MODE_SYNTH || MODE == MODE_FUSED) {
-    // fold the two-sided spectrum modulo n
+    // fold the two-sided spectrum modulo n:
+    //   H_k = [k = 0] Fc_0 + P_k / sqrt(2) (sum_{m = k + jn} s_j (Fc - i Fs)_m
+    //                                      + sum_{m = jn - k} s_j (Fc + i Fs)_m),
+    // P_k = exp(i pi k / n), s_j = (-1)^j on shifted rings (P_k = s_j = 1 otherwise)
     for (int kk = threadIdx.x; kk < n; kk += blockDim.x) {
-      T hnx = 0, hny = 0, hsx = 0, hsy = 0;
+      T anx = 0, any = 0, asx = 0, asy = 0;
+      // +m frequencies, m = kk + j n >= 1: sum of s_j (Fc, -Fs)
+      {
+        int j = kk == 0 ? 1 : 0;
+        for (int m = kk + j * n; m <= L; m += n, ++j) {
+          const T sg = (ph && (j & 1)) ? T(-1) : T(1);
+          const T2 a = FN[m];
+          anx += sg * a.x;
+          any -= sg * a.y;
+          if (has_s) {
+            const T2 b = FS[m];
+            asx += sg * b.x;
+            asy -= sg * b.y;
+          }
+        }
+      }
+      // -m frequencies, m = j n - kk >= 1: sum of s_j (Fc, +Fs)
+      {
+        int j = 1;
+        for (int m = n - kk; m <= L; m += n, ++j) {
+          const T sg = (ph && (j & 1)) ? T(-1) : T(1);
+          const T2 a = FN[m];
+          anx += sg * a.x;
+          any += sg * a.y;
+          if (has_s) {
+            const T2 b = FS[m];
+            asx += sg * b.x;
+            asy += sg * b.y;
+          }
+        }
+      }
+      T cp = 1, sp = 0;
+      if (ph) {
+        const T2 e = ptab[kk];
+        cp = e.x;
+        sp = e.y;
+      }
+      // H = P (a) / sqrt(2) (+ Fc_0 at k = 0)
+      T hnx = rs2 * (cp * anx - sp * any), hny = rs2 * (cp * any + sp * anx);
+      T hsx = rs2 * (cp * asx - sp * asy), hsy = rs2 * (cp * asy + sp * asx);
       if (kk == 0) {
-        hnx = FN[0].x;
-        if (has_s) hsx = FS[0].x;
-      }
-      // +m frequencies, m = kk (mod n), m >= 1
-      for (int m = (kk == 0 ? n : kk); m <= L; m += n) {
-        T c = 1, s = 0;
-        if (ph) sincospi_t(T(m % (2 * n)) / T(n), &s, &c);
-        const T2 a = FN[m];
-        // q = (Fc - i Fs) e^{i m phi0} / sqrt(2)
-        hnx += rs2 * (a.x * c + a.y * s);
-        hny += rs2 * (a.x * s - a.y * c);
-        if (has_s) {
-          const T2 b = FS[m];
-          hsx += rs2 * (b.x * c + b.y * s);
-          hsy += rs2 * (b.x * s - b.y * c);
-        }
-      }
-      // -m frequencies: m = -kk (mod n), m >= 1, conj(q)
-      for (int m = (kk == 0 ? n : n - kk); m <= L; m += n) {
-        T c = 1, s = 0;
-        if (ph) sincospi_t(T(m % (2 * n)) / T(n), &s, &c);
-        const T2 a = FN[m];
-        hnx += rs2 * (a.x * c + a.y * s);
-        hny -= rs2 * (a.x * s - a.y * c);
-        if (has_s) {
-          const T2 b = FS[m];
-          hsx += rs2 * (b.x * c + b.y * s);
-          hsy -= rs2 * (b.x * s - b.y * c);
-        }
+        hnx += FN[0].x;
+        if (has_s) hsx += FS[0].x;
       }
       T2 z;
       z.x = hnx - hsy;
@@ -236,7 +298,12 @@ k_ringfft(typename V2<T>::t* __restrict__ F, int64_t F_stride, double* __restric
     T xnx = T(0.5) * (zk.x + zc.x), xny = T(0.5) * (zk.y + zc.y);
     T xsx = T(0.5) * (zk.y - zc.y), xsy = T(-0.5) * (zk.x - zc.x);
     T c = 1, s = 0;
-    if (ph) sincospi_t(T(m % (2 * n)) / T(n), &s, &c);
+    if (ph) {
+      const T2 e = ptab[kk];
+      const T sg = ((m / n) & 1) ? T(-1) : T(1);
+      c = sg * e.x;
+      s = sg * e.y;
+    }
     const T cm = m == 0 ? T(1) : sq2;
     // G = (c - i s) X
     T gx = c * xnx + s * xny, gy = c * xny - s * xnx;
@@ -257,7 +324,8 @@ k_ringfft(typename V2<T>::t* __restrict__ F, int64_t F_stride, double* __restric
 
 template <typename T>
 size_t smem_bytes(const Grid& g) {
-  return (size_t)g.nmax2 * sizeof(typename V2<T>::t);
+  // transform buffer (nmax2) + phase table (max ring length)
+  return (size_t)(g.nmax2 + g.max_n) * sizeof(typename V2<T>::t);
 }
 
 template <typename T, int MODE>
