@@ -123,6 +123,7 @@ struct Grid {
 
   // Legendre recurrence tables (device), index lm(m, l)
   DevMem A64, A32;        // A_lm of the rescaled recurrence mu_l = A_l x mu_{l-1} - mu_{l-2}
+  DevMem A2f;             // A_lm as a double-float pair (float2 hi, lo) for the FP32X2 kernels
   DevMem c64;             // lambda_lm = c_lm mu_lm
   DevMem ls;              // int [L+1][npair] first l (same parity as m) that is injected
   DevMem st64, st32;      // {mu_ls, mu_ls+1} [L+1][npair]

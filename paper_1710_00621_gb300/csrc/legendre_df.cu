@@ -227,7 +227,7 @@ __device__ __forceinline__ void warp_reduce_scatter_df(df (&v)[NV], int lane) {
 // warps of the CTA are added in FP64 in shared memory.
 template <int NM, int R, int NT, int CH>
 __global__ void __launch_bounds__(NT)
-k_leg_adj_df(const double2* __restrict__ F, int64_t F_stride, const double* __restrict__ Acoef,
+k_leg_adj_df(const double2* __restrict__ F, int64_t F_stride, const float2* __restrict__ Acoef,
              const int* __restrict__ ls_tab, const double2* __restrict__ st,
              const double* __restrict__ yr, const int2* __restrict__ pring, double* __restrict__ part,
              int64_t nlm, int L, int npair) {
@@ -241,7 +241,7 @@ k_leg_adj_df(const double2* __restrict__ F, int64_t F_stride, const double* __re
   const int m = blockIdx.y;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t lmo = lm_off(L, m) - m;
-  const double* Am = Acoef + lmo;
+  const float2* Am = Acoef + lmo;
   double* pout = part + (int64_t)blockIdx.x * P * nlm + lmo;
   const int pbase = blockIdx.x * NT * R + threadIdx.x;
 
@@ -298,8 +298,9 @@ k_leg_adj_df(const double2* __restrict__ F, int64_t F_stride, const double* __re
 #pragma unroll
     for (int j = 0; j < CH; j += 2) {
       const int l = c0 + j;
-      const df A0 = df_from((l <= L) ? Am[l] : 0.0);
-      const df A1 = df_from((l + 1 <= L) ? Am[l + 1] : 0.0);
+      const float2 a0 = (l <= L) ? Am[l] : make_float2(0.f, 0.f);
+      const float2 a1 = (l + 1 <= L) ? Am[l + 1] : make_float2(0.f, 0.f);
+      const df A0 = {a0.x, a0.y}, A1 = {a1.x, a1.y};
       df ma[R], mb[R];
 #pragma unroll
       for (int i = 0; i < R; ++i) {
@@ -366,7 +367,7 @@ int launch_adj_df(const Grid& g, const void* F, int64_t fs, double* part, cudaSt
   dim3 grd((g.npair + kANT * kAR - 1) / (kANT * kAR), L + 1);
   ProfScope ps(PROF_LEG_ADJ, s, 2, 4.0 * g.npair * (double)nlm * (NM + 1));
   k_leg_adj_df<NM, kAR, kANT, kACH><<<grd, kANT, 0, s>>>(
-      (const double2*)F, fs, g.A64.as<double>(), g.ls.as<int>(), g.st64.as<double2>(),
+      (const double2*)F, fs, g.A2f.as<float2>(), g.ls.as<int>(), g.st64.as<double2>(),
       g.y64.as<double>(), g.pair_ring.as<int2>(), part, nlm, L, g.npair);
   CMBWS_LAUNCH_CHECK();
   return CMBWS_OK;

@@ -279,6 +279,15 @@ int grid_build_tables(Grid& g) {
   }
   CMBWS_TRY(g.A64.upload(A.data(), nlm * 8));
   CMBWS_TRY(g.A32.upload(Af.data(), nlm * 4));
+  {
+    std::vector<float> A2(2 * nlm);
+    for (int64_t i = 0; i < nlm; ++i) {
+      const float h = (float)A[i];
+      A2[2 * i] = h;
+      A2[2 * i + 1] = (float)(A[i] - (double)h);
+    }
+    CMBWS_TRY(g.A2f.upload(A2.data(), nlm * 8));
+  }
   CMBWS_TRY(g.c64.upload(c.data(), nlm * 8));
 
   // ---- start values ----
