@@ -86,6 +86,8 @@ struct DevMem {
   template <typename T> T* as() const { return static_cast<T*>(p); }
 };
 
+constexpr int kChunk = 8;  // l-chunk of the checkpointed FP32 adjoint (even)
+
 inline __host__ __device__ int64_t lm_off(int L, int m) {
   return (int64_t)m * (L + 1) - (int64_t)m * (m - 1) / 2;
 }
@@ -127,6 +129,8 @@ struct Grid {
   DevMem c64;             // lambda_lm = c_lm mu_lm
   DevMem ls;              // int [L+1][npair] first l (same parity as m) that is injected
   DevMem st64, st32;      // {mu_ls, mu_ls+1} [L+1][npair]
+  DevMem ck32;            // FP32 {mu_l0, mu_l0+1} at every chunk start l0 = m + kChunk c
+  DevMem ck_base;         // int64 [L+1]: offset of m's block [pair][chunk] in ck32
 
   // ring FFT tables (device)
   std::vector<FftPlan> plans;

@@ -307,6 +307,176 @@ k_leg_adj2(const typename V2<T>::t* __restrict__ F, int64_t F_stride, const T* _
   }
 }
 
+
+// FP32 adjoint from chunk checkpoints: one thread per chunk of kChunk values of l
+// (a CTA covers NT consecutive chunks of one m) loops over every ring pair of the
+// grid.  Each pair's recurrence restarts at the chunk from the stored FP64-computed
+// values (setup.cu), so no thread needs another thread's sums: each output (l, m) is
+// owned by one thread and summed over the pairs in a fixed order.
+// Tiles of PT pairs are staged in shared memory with cp.async, double-buffered: the
+// per-pair even/odd parts E, O (prepared by k_adj_eo), y, the start index and values,
+// and each thread's own column of checkpoints, so the HBM reads of the next tile
+// overlap the arithmetic of the current one.
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+// E/O parts of every (pair, m): eo[(m * npair + p) * 2P + q], q < P even-l parts (north +
+// south), q >= P odd-l parts (north - south), parts = (re, im) per map.
+template <int NM>
+__global__ void k_adj_eo(const float2* __restrict__ F, int64_t F_stride, const int2* __restrict__ pring,
+                         float* __restrict__ eo, int L, int npair) {
+  constexpr int P = 2 * NM;
+  const int m = blockIdx.y;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= npair) return;
+  const int2 rr = pring[p];
+  float* e = eo + ((int64_t)m * npair + p) * 2 * P;
+#pragma unroll
+  for (int k = 0; k < NM; ++k) {
+    const float2 gn = F[k * F_stride + (int64_t)rr.x * (L + 1) + m];
+    float2 gs = make_float2(0.f, 0.f);
+    if (rr.y >= 0) gs = F[k * F_stride + (int64_t)rr.y * (L + 1) + m];
+    e[2 * k] = gn.x + gs.x;
+    e[2 * k + 1] = gn.y + gs.y;
+    e[P + 2 * k] = rr.y >= 0 ? gn.x - gs.x : gn.x;
+    e[P + 2 * k + 1] = rr.y >= 0 ? gn.y - gs.y : gn.y;
+  }
+}
+
+template <int NM, int PT>
+struct AdjCkWarp {  // one warp's double-buffered tile
+  float eo[2][PT][4 * NM];
+  float y[2][PT];
+  int ls[2][PT];
+  float2 st[2][PT];
+  float2 ck[2][PT][32];
+};
+
+template <int NM, int NT, int PT>
+__global__ void __launch_bounds__(NT)
+k_leg_adj_ck(const float* __restrict__ eo, const float* __restrict__ Acoef,
+             const int* __restrict__ ls_tab, const float2* __restrict__ st,
+             const float* __restrict__ yr, const float2* __restrict__ ck,
+             const int64_t* __restrict__ ck_base, const double* __restrict__ c64,
+             double2* __restrict__ out, int64_t nlm, int L, int npair) {
+  constexpr int P = 2 * NM;
+  constexpr int K = kChunk;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  AdjCkWarp<NM, PT>& S = reinterpret_cast<AdjCkWarp<NM, PT>*>(smem_raw)[warp];
+  const int m = blockIdx.y;
+  const int nck = (L - m + K) / K;
+  const int cw = blockIdx.x * NT + warp * 32;  // first chunk of this warp
+  if (cw >= nck) return;                       // warp-uniform: no block barrier below
+  const int c = cw + lane;
+  const bool valid = c < nck;
+  const int l0 = m + K * c;
+  const int64_t lmo = lm_off(L, m) - m;
+  float Al[K];
+#pragma unroll
+  for (int j = 0; j < K; ++j) Al[j] = (valid && l0 + j <= L) ? Acoef[lmo + l0 + j] : 0.f;
+  float acc[K][P];
+#pragma unroll
+  for (int j = 0; j < K; ++j)
+#pragma unroll
+    for (int q = 0; q < P; ++q) acc[j][q] = 0.f;
+  const float2* ckc = ck + ck_base[m] + c;  // + p * nck
+  const float* eom = eo + (int64_t)m * npair * 2 * P;
+  const int ntile = (npair + PT - 1) / PT;
+  // the first pair that has started by the warp's last chunk bounds nothing (pairs are
+  // not sorted by start), so every tile is visited; pairs not yet started are skipped
+
+  auto stage = [&](int t) {
+    const int bf = t & 1, p0 = t * PT;
+    const int np = min(PT, npair - p0);
+    const float* src = eom + (int64_t)p0 * 2 * P;
+    for (int i = lane; i < np * NM; i += 32) cp_async16(&S.eo[bf][0][0] + 4 * i, src + 4 * i);
+    for (int i = lane; i < np; i += 32) {
+      cp_async4(&S.y[bf][i], yr + p0 + i);
+      cp_async4(&S.ls[bf][i], ls_tab + (int64_t)m * npair + p0 + i);
+      cp_async8(&S.st[bf][i], st + (int64_t)m * npair + p0 + i);
+    }
+    if (valid)
+      for (int i = 0; i < np; ++i) cp_async8(&S.ck[bf][i][lane], ckc + (int64_t)(p0 + i) * nck);
+    cp_async_commit();
+  };
+
+  stage(0);
+  for (int t = 0; t < ntile; ++t) {
+    if (t + 1 < ntile) {
+      stage(t + 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncwarp();
+    if (valid) {
+      const int bf = t & 1;
+      const int np = min(PT, npair - t * PT);
+      for (int i = 0; i < np; ++i) {
+        const int lsp = S.ls[bf][i];
+        if (lsp > l0 + K - 1) continue;  // the pair starts after this chunk
+        const float2 cv = S.ck[bf][i][lane];
+        float ma = cv.x, mb = cv.y;
+        if (lsp == l0) {
+          ma = S.st[bf][i].x;
+          mb = S.st[bf][i].y;
+        }
+        const float yv = S.y[bf][i];
+        const float* e = S.eo[bf][i];
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+          acc[0][q] += ma * e[q];
+          acc[1][q] += mb * e[P + q];
+        }
+#pragma unroll
+        for (int j = 2; j < K; j += 2) {
+          float na = fmaf(-Al[j], yv, Al[j]) * mb - ma;
+          float nb = fmaf(-Al[j + 1], yv, Al[j + 1]) * na - mb;
+          if (l0 + j == lsp) {
+            na = S.st[bf][i].x;
+            nb = S.st[bf][i].y;
+          }
+          ma = na;
+          mb = nb;
+#pragma unroll
+          for (int q = 0; q < P; ++q) {
+            acc[j][q] += ma * e[q];
+            acc[j + 1][q] += mb * e[P + q];
+          }
+        }
+      }
+    }
+    __syncwarp();  // buffer t & 1 is restaged two iterations later
+  }
+  if (!valid) return;
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    const int l = l0 + j;
+    if (l > L) break;
+    const int64_t i = lmo + l;
+    const double cc = c64[i];
+#pragma unroll
+    for (int k = 0; k < NM; ++k)
+      out[k * nlm + i] = make_double2(cc * (double)acc[j][2 * k], cc * (double)acc[j][2 * k + 1]);
+  }
+}
+
 template <typename T>
 __global__ void k_adj_reduce(const T* __restrict__ part, int nblk, int64_t nlm, int nm,
                              const double* __restrict__ c, double2* __restrict__ out) {
@@ -365,8 +535,36 @@ int adj_nblk(const Grid& g) {
   return (g.npair + C::ANT * C::AR - 1) / (C::ANT * C::AR);
 }
 
+template <int NM>
+int launch_adj_ck(const Grid& g, const void* F, int64_t F_stride, void* part, double* out,
+                  cudaStream_t s) {
+  constexpr int NT = 128, PT = 16;
+  const int L = g.lmax;
+  const int64_t nlm = nlm_of(L);
+  float* eo = (float*)part;  // [L+1][npair][2P] floats, sized by legendre_adjoint_part_bytes
+  {
+    dim3 grd((g.npair + 127) / 128, L + 1);
+    ProfScope ps(PROF_LEG_RED, s, 0);
+    k_adj_eo<NM><<<grd, 128, 0, s>>>((const float2*)F, F_stride, g.pair_ring.as<int2>(), eo, L,
+                                     g.npair);
+    CMBWS_LAUNCH_CHECK();
+  }
+  const int maxck = (L + kChunk) / kChunk;
+  dim3 grd((maxck + NT - 1) / NT, L + 1);
+  constexpr size_t sm = sizeof(AdjCkWarp<NM, PT>) * (NT / 32);
+  auto kern = k_leg_adj_ck<NM, NT, PT>;
+  CMBWS_TRY(ensure_dyn_smem((const void*)kern, sm));
+  ProfScope ps(PROF_LEG_ADJ, s, 0, 4.0 * g.npair * (double)nlm * (NM + 1));
+  kern<<<grd, NT, sm, s>>>(eo, g.A32.as<float>(), g.ls.as<int>(), g.st32.as<float2>(),
+                           g.y32.as<float>(), g.ck32.as<float2>(), g.ck_base.as<int64_t>(),
+                           g.c64.as<double>(), (double2*)out, nlm, L, g.npair);
+  CMBWS_LAUNCH_CHECK();
+  return CMBWS_OK;
+}
+
 template <typename T, int NM>
 int launch_adj(const Grid& g, const void* F, int64_t F_stride, T* part, double* out, cudaStream_t s) {
+  if (std::is_same<T, float>::value) return launch_adj_ck<NM>(g, F, F_stride, part, out, s);
   using C = Cfg<T>;
   using T2 = typename V2<T>::t;
   const int L = g.lmax;
@@ -442,6 +640,8 @@ int legendre_synth(const Grid& g, int prec, int nmaps, const void* alm, void* F,
 
 size_t legendre_adjoint_part_bytes(const Grid& g, int prec, int nmaps) {
   const int nm = nmaps < 4 ? nmaps : 4;
+  if (prec == CMBWS_FP32)  // E/O parts of the checkpointed adjoint
+    return (size_t)(g.lmax + 1) * g.npair * 4 * nm * sizeof(float);
   const int nblk = prec == CMBWS_FP32X2 ? legendre_df_adj_nblk(g)
                    : prec == CMBWS_FP64 ? adj_nblk<double>(g) : adj_nblk<float>(g);
   return (size_t)nblk * 2 * nm * nlm_of(g.lmax) * prec_size(prec);

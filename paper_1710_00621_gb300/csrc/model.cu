@@ -882,10 +882,12 @@ int model_create(const cmbws_model_desc* desc, int prec, cudaStream_t s, Model**
     CMBWS_TRY(G.alm.alloc((size_t)G.nmaps * nlm * 16));
     CMBWS_TRY(G.F.alloc((size_t)G.nmaps * g.nring * (g.lmax + 1) * 16));
     CMBWS_TRY(G.out.alloc((size_t)G.nmaps * nlm * 16));
-    part_bytes = std::max(part_bytes, legendre_adjoint_part_bytes(g, CMBWS_FP64, G.nmaps));
+    for (int pr : {CMBWS_FP64, CMBWS_FP32, CMBWS_FP32X2})
+      part_bytes = std::max(part_bytes, legendre_adjoint_part_bytes(g, pr, G.nmaps));
   }
   for (Group& G : M->mgroups)
-    part_bytes = std::max(part_bytes, legendre_adjoint_part_bytes(*G.grid, CMBWS_FP64, G.nmaps));
+    for (int pr : {CMBWS_FP64, CMBWS_FP32, CMBWS_FP32X2})
+      part_bytes = std::max(part_bytes, legendre_adjoint_part_bytes(*G.grid, pr, G.nmaps));
   CMBWS_TRY(M->part.alloc(part_bytes));
   CMBWS_TRY(M->tprior.alloc((size_t)M->nvec * 8));
   M->nsht_A = 2 * (2 * M->nmix + no);  // Sec. 3.3: 2 (2 Nmix + Nobs)

@@ -20,6 +20,10 @@
 // v * 2^(-600 k)): for every (m, ring pair) the first l (same parity as m)
 // at which |mu_l| or |mu_{l+1}| exceeds 1e-30 with k = 0, and the two values
 // there.  Every skipped term is below 1e-30 in magnitude.
+// The same FP64 pass stores, for the FP32 adjoint, the two recurrence values at the
+// start of every chunk of kChunk = 8 values of l ([m][pair][chunk], FP32; about
+// npair (L+1)^2 / 16 x 8 bytes: 9.7 GB at Nside 1024, L = 3071), so that the adjoint can
+// restart the recurrence of any pair at any chunk without a serial walk along l.
 #include <cmath>
 #include <complex>
 #include <cstring>
@@ -135,7 +139,8 @@ __global__ void k_seeds(const double* __restrict__ sinth, const double* __restri
 
 __global__ void k_start(const double* __restrict__ y, const double* __restrict__ A, int L, int npair,
                         const double* __restrict__ sv, const int* __restrict__ sk,
-                        int* __restrict__ ls, double2* __restrict__ st64, float2* __restrict__ st32) {
+                        int* __restrict__ ls, double2* __restrict__ st64, float2* __restrict__ st32,
+                        const int64_t* __restrict__ ck_base, float2* __restrict__ ck) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   const int m = blockIdx.y;
   if (p >= npair) return;
@@ -148,12 +153,20 @@ __global__ void k_start(const double* __restrict__ y, const double* __restrict__
   int l = m;
   int found = L + 1;
   double o0 = 0.0, o1 = 0.0;
+  const int nck = (L - m + kChunk) / kChunk;
+  float2* ckp = ck ? ck + ck_base[m] + (int64_t)p * nck : nullptr;
   while (l <= L) {
-    if (k == 0 && (fabs(v0) > kStartThreshold || fabs(v1) > kStartThreshold)) {
+    if (found > L && k == 0 && (fabs(v0) > kStartThreshold || fabs(v1) > kStartThreshold)) {
       found = l;
       o0 = v0;
       o1 = (l + 1 <= L) ? v1 : 0.0;
-      break;
+      if (!ckp) break;
+    }
+    if (ckp && (l - m) % kChunk == 0) {
+      // chunk checkpoint: the recurrence pair at the chunk's first l once the pair has
+      // started there, zero before (a pair starting inside the chunk is injected at ls)
+      ckp[(l - m) / kChunk] = found <= l ? make_float2((float)v0, (float)((l + 1 <= L) ? v1 : 0.0))
+                                        : make_float2(0.f, 0.f);
     }
     if (l + 2 > L) break;
     const double n0 = fma(-Am[l + 2], yy, Am[l + 2]) * v1 - v0;
@@ -307,8 +320,18 @@ int grid_build_tables(Grid& g) {
                                             d_sv.as<double>(), d_sk.as<int>());
     CMBWS_LAUNCH_CHECK();
     dim3 grd((g.npair + 127) / 128, L + 1);
+    // FP32 chunk checkpoints of the adjoint (legendre.cu): [m][pair][chunk]
+    std::vector<int64_t> cb(L + 1, 0);
+    int64_t tot = 0;
+    for (int m = 0; m <= L; ++m) {
+      cb[m] = tot;
+      tot += (int64_t)g.npair * ((L - m + kChunk) / kChunk);
+    }
+    CMBWS_TRY(g.ck_base.upload(cb.data(), (L + 1) * 8));
+    CMBWS_TRY(g.ck32.alloc((size_t)tot * 8));
     k_start<<<grd, 128>>>(g.y64.as<double>(), g.A64.as<double>(), L, g.npair, d_sv.as<double>(),
-                          d_sk.as<int>(), g.ls.as<int>(), g.st64.as<double2>(), g.st32.as<float2>());
+                          d_sk.as<int>(), g.ls.as<int>(), g.st64.as<double2>(), g.st32.as<float2>(),
+                          g.ck_base.as<int64_t>(), g.ck32.as<float2>());
     CMBWS_LAUNCH_CHECK();
     CMBWS_CUDA(cudaDeviceSynchronize());
   }
