@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -131,6 +132,10 @@ struct Grid {
   DevMem st64, st32;      // {mu_ls, mu_ls+1} [L+1][npair]
   DevMem ck32;            // FP32 {mu_l0, mu_l0+1} at every chunk start l0 = m + kChunk c
   DevMem ck_base;         // int64 [L+1]: offset of m's block [pair][chunk] in ck32
+  mutable DevMem ck64;    // double-float {mu_l0, mu_l0+1} (float4), same layout; built on first use
+  mutable DevMem y2f;     // y as a double-float pair (float2), built with ck64
+  mutable std::mutex ck64_mu;
+  std::vector<double> fmm_h;  // sqrt((2m+1)/(2m)) (host, for rebuilding seeds)
 
   // ring FFT tables (device)
   std::vector<FftPlan> plans;
@@ -165,6 +170,8 @@ int ringfft_smem_ok(const Grid& g, int prec);
 
 // ---- grid setup (setup.cu) ----
 int grid_build_tables(Grid& g);
+// build the double-float chunk checkpoints of the FP32X2 adjoint if not yet built
+int grid_ensure_ck64(const Grid& g);
 
 // ---- pack / unpack (setup.cu) ----
 // packed CMBWS_ALM FP64 [nmaps][(L+1)^2] -> internal lm complex (prec), multiplied by c_lm
@@ -182,8 +189,9 @@ inline bool valid_prec(int prec) {
 
 // ---- double-float Legendre stage (legendre_df.cu) ----
 int legendre_synth_df(const Grid& g, int nmaps, const void* alm, void* F, cudaStream_t s);
-int legendre_adj_df_chunk(const Grid& g, int nm, const void* F, double* part, cudaStream_t s);
-int legendre_df_adj_nblk(const Grid& g);
+// double-float adjoint from chunk checkpoints: F (FP64 ring spectra of nm maps) ->
+// out (FP64 coefficients); eo is a scratch of legendre_adjoint_part_bytes bytes
+int legendre_adj_df_ck(const Grid& g, int nm, const void* F, void* eo, double* out, cudaStream_t s);
 
 // Raise a kernel's dynamic shared-memory limit to at least `bytes` on the current device.
 // The limit only ever grows, so concurrent launches with different sizes (several host
@@ -211,5 +219,25 @@ struct ProfScope {
   ProfScope(int stage, cudaStream_t s_, int arith = 1, double flops_ = 0.0);
   ~ProfScope();
 };
+
+// cp.async staging (global -> shared, asynchronous; 4/8-byte copies through L1,
+// 16-byte copies bypassing it)
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
 
 }  // namespace cmbws

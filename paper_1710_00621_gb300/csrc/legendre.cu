@@ -317,24 +317,6 @@ k_leg_adj2(const typename V2<T>::t* __restrict__ F, int64_t F_stride, const T* _
 // per-pair even/odd parts E, O (prepared by k_adj_eo), y, the start index and values,
 // and each thread's own column of checkpoints, so the HBM reads of the next tile
 // overlap the arithmetic of the current one.
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
-}
-
 // E/O parts of every (pair, m): eo[(m * npair + p) * 2P + q], q < P even-l parts (north +
 // south), q >= P odd-l parts (north - south), parts = (re, im) per map.
 template <int NM>
@@ -642,9 +624,9 @@ size_t legendre_adjoint_part_bytes(const Grid& g, int prec, int nmaps) {
   const int nm = nmaps < 4 ? nmaps : 4;
   if (prec == CMBWS_FP32)  // E/O parts of the checkpointed adjoint
     return (size_t)(g.lmax + 1) * g.npair * 4 * nm * sizeof(float);
-  const int nblk = prec == CMBWS_FP32X2 ? legendre_df_adj_nblk(g)
-                   : prec == CMBWS_FP64 ? adj_nblk<double>(g) : adj_nblk<float>(g);
-  return (size_t)nblk * 2 * nm * nlm_of(g.lmax) * prec_size(prec);
+  if (prec == CMBWS_FP32X2)  // double-float E/O parts
+    return (size_t)(g.lmax + 1) * g.npair * 4 * nm * 2 * sizeof(float);
+  return (size_t)adj_nblk<double>(g) * 2 * nm * nlm_of(g.lmax) * sizeof(double);
 }
 
 int legendre_adjoint(const Grid& g, int prec, int nmaps, const void* F, void* part,
@@ -655,15 +637,10 @@ int legendre_adjoint(const Grid& g, int prec, int nmaps, const void* F, void* pa
   }
   if (prec == CMBWS_FP32X2) {
     const int64_t nlm = nlm_of(g.lmax), fs = (int64_t)g.nring * (g.lmax + 1);
-    const int nblk = legendre_df_adj_nblk(g);
-    for (int k0 = 0; k0 < nmaps; k0 += 4) {
-      const int nm = nmaps - k0 < 4 ? nmaps - k0 : 4;
-      CMBWS_TRY(legendre_adj_df_chunk(g, nm, (const double2*)F + k0 * fs, (double*)part, s));
-      dim3 rg((unsigned)((nlm + 255) / 256), nm);
-      ProfScope ps(PROF_LEG_RED, s, 2);
-      k_adj_reduce<double><<<rg, 256, 0, s>>>((const double*)part, nblk, nlm, nm, g.c64.as<double>(),
-                                              (double2*)(out + 2 * k0 * nlm));
-      CMBWS_LAUNCH_CHECK();
+    // at most 3 maps per launch: 4 maps' double-float accumulators exceed the register file
+    for (int k0 = 0; k0 < nmaps; k0 += 3) {
+      const int nm = nmaps - k0 < 3 ? nmaps - k0 : 3;
+      CMBWS_TRY(legendre_adj_df_ck(g, nm, (const double2*)F + k0 * fs, part, out + 2 * k0 * nlm, s));
     }
     return CMBWS_OK;
   }

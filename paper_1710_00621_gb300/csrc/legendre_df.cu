@@ -195,158 +195,160 @@ k_leg_synth_df(const double2* __restrict__ alm, int64_t alm_stride, const double
   }
 }
 
-__device__ __forceinline__ df df_add(df a, df b) {
-  const df s = two_sum(a.h, b.h);
-  return quick_two_sum(s.h, s.l + (a.l + b.l));
-}
-
-// Sum NV double-float values over the 32 lanes of a warp (reduce-scatter):
-// afterwards lane q holds the sums of flat indices [q NV/32, (q+1) NV/32).
-template <int NV>
-__device__ __forceinline__ void warp_reduce_scatter_df(df (&v)[NV], int lane) {
-  static_assert(NV % 32 == 0, "NV must be a multiple of 32");
-#pragma unroll
-  for (int s = 0; s < 5; ++s) {
-    const int o = 16 >> s;
-    const int h = (NV >> s) / 2;
-    const bool up = (lane & o) != 0;
-#pragma unroll
-    for (int i = 0; i < h; ++i) {
-      const df send = up ? v[i] : v[i + h];
-      const df keep = up ? v[i + h] : v[i];
-      df recv;
-      recv.h = __shfl_xor_sync(0xffffffffu, send.h, o);
-      recv.l = __shfl_xor_sync(0xffffffffu, send.l, o);
-      v[i] = df_add(keep, recv);
-    }
-  }
-}
-
-// Adjoint: per l-chunk each thread sums its R pairs' products in double-float
-// (compensated), a double-float warp reduce-scatter adds the 32 lanes, and the
-// warps of the CTA are added in FP64 in shared memory.
-template <int NM, int R, int NT, int CH>
-__global__ void __launch_bounds__(NT)
-k_leg_adj_df(const double2* __restrict__ F, int64_t F_stride, const float2* __restrict__ Acoef,
-             const int* __restrict__ ls_tab, const double2* __restrict__ st,
-             const double* __restrict__ yr, const int2* __restrict__ pring, double* __restrict__ part,
-             int64_t nlm, int L, int npair) {
+// E/O parts of every (pair, m) as double-float pairs: eo[(m * npair + p) * 2P + q],
+// q < P even-l parts (north + south), q >= P odd-l parts (north - south).
+template <int NM>
+__global__ void k_adj_eo_df(const double2* __restrict__ F, int64_t F_stride,
+                            const int2* __restrict__ pring, float2* __restrict__ eo, int L, int npair) {
   constexpr int P = 2 * NM;
-  constexpr int NV0 = CH * P;
-  constexpr int NV = (NV0 + 31) / 32 * 32;
-  constexpr int PER = NV / 32;
-  constexpr int NW = NT / 32;
-  __shared__ double red[NW][NV];
-  __shared__ int s_lo;
   const int m = blockIdx.y;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t lmo = lm_off(L, m) - m;
-  const float2* Am = Acoef + lmo;
-  double* pout = part + (int64_t)blockIdx.x * P * nlm + lmo;
-  const int pbase = blockIdx.x * NT * R + threadIdx.x;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= npair) return;
+  const int2 rr = pring[p];
+  float2* e = eo + ((int64_t)m * npair + p) * 2 * P;
+#pragma unroll
+  for (int k = 0; k < NM; ++k) {
+    const double2 gn = F[k * F_stride + (int64_t)rr.x * (L + 1) + m];
+    double2 gs = make_double2(0.0, 0.0);
+    if (rr.y >= 0) gs = F[k * F_stride + (int64_t)rr.y * (L + 1) + m];
+    const df er = df_from(gn.x + gs.x), ei = df_from(gn.y + gs.y);
+    const df orr = df_from(rr.y >= 0 ? gn.x - gs.x : gn.x);
+    const df oi = df_from(rr.y >= 0 ? gn.y - gs.y : gn.y);
+    e[2 * k] = make_float2(er.h, er.l);
+    e[2 * k + 1] = make_float2(ei.h, ei.l);
+    e[P + 2 * k] = make_float2(orr.h, orr.l);
+    e[P + 2 * k + 1] = make_float2(oi.h, oi.l);
+  }
+}
 
-  int ls[R];
-  df y[R], mu1[R], mu2[R], i0[R], i1[R];
-  df ev[R][P], ov[R][P];
-  int mylo = INT_MAX;
+template <int NM, int PT>
+struct AdjCkDfWarp {  // one warp's double-buffered tile
+  float2 eo[2][PT][4 * NM];
+  float2 y[2][PT];
+  int ls[2][PT];
+  double2 st[2][PT];
+  float4 ck[2][PT][32];
+};
+
+// Adjoint in double-float from chunk checkpoints (the FP32 kernel's scheme in
+// legendre.cu with every value a hi + lo pair): one thread per chunk of kChunk values
+// of l loops over all ring pairs, restarting the recurrence at its chunk from the
+// double-float checkpoints, and accumulates each output (l, m, part) with the
+// compensated dot product.  Each output has one owner and a fixed summation order, so
+// no cross-thread reduction or partial-sum buffer is needed.
+template <int NM, int NT, int PT>
+__global__ void __launch_bounds__(NT)
+k_leg_adj_ck_df(const float2* __restrict__ eo, const float2* __restrict__ Acoef,
+                const int* __restrict__ ls_tab, const double2* __restrict__ st,
+                const float2* __restrict__ yr, const float4* __restrict__ ck,
+                const int64_t* __restrict__ ck_base, const double* __restrict__ c64,
+                double2* __restrict__ out, int64_t nlm, int L, int npair) {
+  constexpr int P = 2 * NM;
+  constexpr int K = kChunk;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  AdjCkDfWarp<NM, PT>& S = reinterpret_cast<AdjCkDfWarp<NM, PT>*>(smem_raw)[warp];
+  const int m = blockIdx.y;
+  const int nck = (L - m + K) / K;
+  const int cw = blockIdx.x * NT + warp * 32;  // first chunk of this warp
+  if (cw >= nck) return;                       // warp-uniform: no block barrier below
+  const int c = cw + lane;
+  const bool valid = c < nck;
+  const int l0 = m + K * c;
+  const int64_t lmo = lm_off(L, m) - m;
+  df Al[K];
 #pragma unroll
-  for (int i = 0; i < R; ++i) {
-    const int p = pbase + i * NT;
-    mu1[i] = mu2[i] = {0.f, 0.f};
-    if (p < npair) {
-      ls[i] = ls_tab[(int64_t)m * npair + p];
-      y[i] = df_from(yr[p]);
-      const double2 s2 = st[(int64_t)m * npair + p];
-      i0[i] = df_from(s2.x);
-      i1[i] = df_from(s2.y);
-      const int2 rr = pring[p];
+  for (int j = 0; j < K; ++j) {
+    const float2 a = (valid && l0 + j <= L) ? Acoef[lmo + l0 + j] : make_float2(0.f, 0.f);
+    Al[j] = {a.x, a.y};
+  }
+  float ah[K][P], al[K][P];
 #pragma unroll
-      for (int k = 0; k < NM; ++k) {
-        const double2 gn = F[k * F_stride + (int64_t)rr.x * (L + 1) + m];
-        const double2 gs = rr.y >= 0 ? F[k * F_stride + (int64_t)rr.y * (L + 1) + m]
-                                     : make_double2(0.0, 0.0);
-        ev[i][2 * k] = df_from(gn.x + gs.x);
-        ev[i][2 * k + 1] = df_from(gn.y + gs.y);
-        ov[i][2 * k] = df_from(rr.y >= 0 ? gn.x - gs.x : gn.x);
-        ov[i][2 * k + 1] = df_from(rr.y >= 0 ? gn.y - gs.y : gn.y);
-      }
+  for (int j = 0; j < K; ++j)
+#pragma unroll
+    for (int q = 0; q < P; ++q) ah[j][q] = al[j][q] = 0.f;
+  const float4* ckc = ck + ck_base[m] + c;  // + p * nck
+  const float2* eom = eo + (int64_t)m * npair * 2 * P;
+  const int ntile = (npair + PT - 1) / PT;
+
+  auto stage = [&](int t) {
+    const int bf = t & 1, p0 = t * PT;
+    const int np = min(PT, npair - p0);
+    const float2* src = eom + (int64_t)p0 * 2 * P;
+    for (int i = lane; i < np * P; i += 32) cp_async16(&S.eo[bf][0][0] + 2 * i, src + 2 * i);
+    for (int i = lane; i < np; i += 32) {
+      cp_async8(&S.y[bf][i], yr + p0 + i);
+      cp_async4(&S.ls[bf][i], ls_tab + (int64_t)m * npair + p0 + i);
+      cp_async16(&S.st[bf][i], st + (int64_t)m * npair + p0 + i);
+    }
+    if (valid)
+      for (int i = 0; i < np; ++i) cp_async16(&S.ck[bf][i][lane], ckc + (int64_t)(p0 + i) * nck);
+    cp_async_commit();
+  };
+
+  stage(0);
+  for (int t = 0; t < ntile; ++t) {
+    if (t + 1 < ntile) {
+      stage(t + 1);
+      cp_async_wait<1>();
     } else {
-      ls[i] = INT_MAX;
-      y[i] = {0.f, 0.f};
-      i0[i] = i1[i] = {0.f, 0.f};
-#pragma unroll
-      for (int c = 0; c < P; ++c) ev[i][c] = ov[i][c] = {0.f, 0.f};
+      cp_async_wait<0>();
     }
-    mylo = min(mylo, ls[i]);
-  }
-  if (threadIdx.x == 0) s_lo = INT_MAX;
-  __syncthreads();
-  atomicMin(&s_lo, mylo);
-  __syncthreads();
-  const int lo = s_lo;
-  int nxt = mylo;
-  {
-    const int lend = min(lo, L + 1);
-    for (int l = m + threadIdx.x; l < lend; l += NT)
+    __syncwarp();
+    if (valid) {
+      const int bf = t & 1;
+      const int np = min(PT, npair - t * PT);
+      for (int i = 0; i < np; ++i) {
+        const int lsp = S.ls[bf][i];
+        if (lsp > l0 + K - 1) continue;  // the pair starts after this chunk
+        const float4 cv = S.ck[bf][i][lane];
+        df ma = {cv.x, cv.y}, mb = {cv.z, cv.w};
+        const float2 yy = S.y[bf][i];
+        const df yv = {yy.x, yy.y};
+        const float2* e = S.eo[bf][i];
 #pragma unroll
-      for (int pp = 0; pp < P; ++pp) pout[pp * nlm + l] = 0.0;
-  }
-  for (int c0 = lo; c0 <= L; c0 += CH) {
-    df v[NV];
+        for (int q = 0; q < P; ++q) {
+          const float2 ev = e[q], ov = e[P + q];
+          dot2_acc(ah[0][q], al[0][q], ma, df{ev.x, ev.y});
+          dot2_acc(ah[1][q], al[1][q], mb, df{ov.x, ov.y});
+        }
 #pragma unroll
-    for (int q = 0; q < NV; ++q) v[q] = {0.f, 0.f};
-#pragma unroll
-    for (int j = 0; j < CH; j += 2) {
-      const int l = c0 + j;
-      const float2 a0 = (l <= L) ? Am[l] : make_float2(0.f, 0.f);
-      const float2 a1 = (l + 1 <= L) ? Am[l + 1] : make_float2(0.f, 0.f);
-      const df A0 = {a0.x, a0.y}, A1 = {a1.x, a1.y};
-      df ma[R], mb[R];
-#pragma unroll
-      for (int i = 0; i < R; ++i) {
-        ma[i] = df_recur(A0, y[i], mu1[i], mu2[i]);
-        mb[i] = df_recur(A1, y[i], ma[i], mu1[i]);
-      }
-      if (l == nxt) {
-        int nn = INT_MAX;
-#pragma unroll
-        for (int i = 0; i < R; ++i) {
-          if (ls[i] == l) {
-            ma[i] = i0[i];
-            mb[i] = i1[i];
+        for (int j = 2; j < K; j += 2) {
+          df na = df_recur(Al[j], yv, mb, ma);
+          df nb = df_recur(Al[j + 1], yv, na, mb);
+          if (l0 + j == lsp) {
+            const double2 sv = S.st[bf][i];
+            na = df_from(sv.x);
+            nb = df_from(sv.y);
           }
-          if (ls[i] > l) nn = min(nn, ls[i]);
-        }
-        nxt = nn;
-      }
+          ma = na;
+          mb = nb;
 #pragma unroll
-      for (int i = 0; i < R; ++i) {
-        mu2[i] = ma[i];
-        mu1[i] = mb[i];
-#pragma unroll
-        for (int c = 0; c < P; ++c) {
-          dot2_acc(v[j * P + c].h, v[j * P + c].l, ma[i], ev[i][c]);
-          dot2_acc(v[(j + 1) * P + c].h, v[(j + 1) * P + c].l, mb[i], ov[i][c]);
+          for (int q = 0; q < P; ++q) {
+            const float2 ev = e[q], ov = e[P + q];
+            dot2_acc(ah[j][q], al[j][q], ma, df{ev.x, ev.y});
+            dot2_acc(ah[j + 1][q], al[j + 1][q], mb, df{ov.x, ov.y});
+          }
         }
       }
     }
-    warp_reduce_scatter_df<NV>(v, lane);
+    __syncwarp();  // buffer t & 1 is restaged two iterations later
+  }
+  if (!valid) return;
 #pragma unroll
-    for (int q = 0; q < PER; ++q) red[warp][lane * PER + q] = (double)v[q].h + (double)v[q].l;
-    __syncthreads();
-    for (int f = threadIdx.x; f < NV0; f += NT) {
-      double sum = 0.0;
+  for (int j = 0; j < K; ++j) {
+    const int l = l0 + j;
+    if (l > L) break;
+    const int64_t i = lmo + l;
+    const double cc = c64[i];
 #pragma unroll
-      for (int w = 0; w < NW; ++w) sum += red[w][f];
-      const int l = c0 + f / P;
-      if (l <= L) pout[(f % P) * nlm + l] = sum;
-    }
-    __syncthreads();
+    for (int k = 0; k < NM; ++k)
+      out[k * nlm + i] = make_double2(cc * ((double)ah[j][2 * k] + (double)al[j][2 * k]),
+                                      cc * ((double)ah[j][2 * k + 1] + (double)al[j][2 * k + 1]));
   }
 }
 
 constexpr int kSR = 1, kSNT = 128, kSCH = 128;
-constexpr int kAR = 2, kANT = 256, kACH = 4;
 
 template <int NM>
 int launch_synth_df(const Grid& g, const void* alm, int64_t as, void* F, int64_t fs, cudaStream_t s) {
@@ -360,22 +362,34 @@ int launch_synth_df(const Grid& g, const void* alm, int64_t as, void* F, int64_t
   return CMBWS_OK;
 }
 
+constexpr int kANT = 128, kAPT = 8;
+
 template <int NM>
-int launch_adj_df(const Grid& g, const void* F, int64_t fs, double* part, cudaStream_t s) {
+int launch_adj_ck_df(const Grid& g, const void* F, int64_t fs, void* eo_buf, double* out, cudaStream_t s) {
   const int L = g.lmax;
   const int64_t nlm = nlm_of(L);
-  dim3 grd((g.npair + kANT * kAR - 1) / (kANT * kAR), L + 1);
+  float2* eo = (float2*)eo_buf;  // [L+1][npair][2P] double-float pairs
+  {
+    dim3 grd((g.npair + 127) / 128, L + 1);
+    ProfScope ps(PROF_LEG_RED, s, 2);
+    k_adj_eo_df<NM><<<grd, 128, 0, s>>>((const double2*)F, fs, g.pair_ring.as<int2>(), eo, L, g.npair);
+    CMBWS_LAUNCH_CHECK();
+  }
+  const int maxck = (L + kChunk) / kChunk;
+  dim3 grd((maxck + kANT - 1) / kANT, L + 1);
+  constexpr size_t sm = sizeof(AdjCkDfWarp<NM, kAPT>) * (kANT / 32);
+  auto kern = k_leg_adj_ck_df<NM, kANT, kAPT>;
+  CMBWS_TRY(ensure_dyn_smem((const void*)kern, sm));
   ProfScope ps(PROF_LEG_ADJ, s, 2, 4.0 * g.npair * (double)nlm * (NM + 1));
-  k_leg_adj_df<NM, kAR, kANT, kACH><<<grd, kANT, 0, s>>>(
-      (const double2*)F, fs, g.A2f.as<float2>(), g.ls.as<int>(), g.st64.as<double2>(),
-      g.y64.as<double>(), g.pair_ring.as<int2>(), part, nlm, L, g.npair);
+  kern<<<grd, kANT, sm, s>>>(eo, g.A2f.as<float2>(), g.ls.as<int>(), g.st64.as<double2>(),
+                             g.y2f.as<float2>(), g.ck64.as<float4>(), g.ck_base.as<int64_t>(),
+                             g.c64.as<double>(), (double2*)out, nlm, L, g.npair);
   CMBWS_LAUNCH_CHECK();
   return CMBWS_OK;
 }
 
 }  // namespace
 
-int legendre_df_adj_nblk(const Grid& g) { return (g.npair + kANT * kAR - 1) / (kANT * kAR); }
 
 int legendre_synth_df(const Grid& g, int nmaps, const void* alm, void* F, cudaStream_t s) {
   const int64_t as = nlm_of(g.lmax), fs = (int64_t)g.nring * (g.lmax + 1);
@@ -395,16 +409,14 @@ int legendre_synth_df(const Grid& g, int nmaps, const void* alm, void* F, cudaSt
   return CMBWS_OK;
 }
 
-// F -> partial sums (FP64, [nblk][2 nm][nlm]) for maps k0 .. k0 + nm - 1
-int legendre_adj_df_chunk(const Grid& g, int nm, const void* F, double* part, cudaStream_t s) {
+int legendre_adj_df_ck(const Grid& g, int nm, const void* F, void* eo, double* out, cudaStream_t s) {
+  CMBWS_TRY(grid_ensure_ck64(g));
   const int64_t fs = (int64_t)g.nring * (g.lmax + 1);
   switch (nm) {
-    case 1: return launch_adj_df<1>(g, F, fs, part, s);
-    case 2: return launch_adj_df<2>(g, F, fs, part, s);
-    case 3: return launch_adj_df<3>(g, F, fs, part, s);
-    default: return launch_adj_df<4>(g, F, fs, part, s);
+    case 1: return launch_adj_ck_df<1>(g, F, fs, eo, out, s);
+    case 2: return launch_adj_ck_df<2>(g, F, fs, eo, out, s);
+    default: return launch_adj_ck_df<3>(g, F, fs, eo, out, s);
   }
-  (void)fs;
 }
 
 }  // namespace cmbws

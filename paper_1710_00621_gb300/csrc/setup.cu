@@ -140,7 +140,8 @@ __global__ void k_seeds(const double* __restrict__ sinth, const double* __restri
 __global__ void k_start(const double* __restrict__ y, const double* __restrict__ A, int L, int npair,
                         const double* __restrict__ sv, const int* __restrict__ sk,
                         int* __restrict__ ls, double2* __restrict__ st64, float2* __restrict__ st32,
-                        const int64_t* __restrict__ ck_base, float2* __restrict__ ck) {
+                        const int64_t* __restrict__ ck_base, float2* __restrict__ ck,
+                        float4* __restrict__ ck64) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   const int m = blockIdx.y;
   if (p >= npair) return;
@@ -155,18 +156,24 @@ __global__ void k_start(const double* __restrict__ y, const double* __restrict__
   double o0 = 0.0, o1 = 0.0;
   const int nck = (L - m + kChunk) / kChunk;
   float2* ckp = ck ? ck + ck_base[m] + (int64_t)p * nck : nullptr;
+  float4* ckd = ck64 ? ck64 + ck_base[m] + (int64_t)p * nck : nullptr;
   while (l <= L) {
     if (found > L && k == 0 && (fabs(v0) > kStartThreshold || fabs(v1) > kStartThreshold)) {
       found = l;
       o0 = v0;
       o1 = (l + 1 <= L) ? v1 : 0.0;
-      if (!ckp) break;
+      if (!ckp && !ckd) break;
     }
-    if (ckp && (l - m) % kChunk == 0) {
+    if ((l - m) % kChunk == 0) {
       // chunk checkpoint: the recurrence pair at the chunk's first l once the pair has
       // started there, zero before (a pair starting inside the chunk is injected at ls)
-      ckp[(l - m) / kChunk] = found <= l ? make_float2((float)v0, (float)((l + 1 <= L) ? v1 : 0.0))
-                                        : make_float2(0.f, 0.f);
+      const double w0 = found <= l ? v0 : 0.0;
+      const double w1 = (found <= l && l + 1 <= L) ? v1 : 0.0;
+      if (ckp) ckp[(l - m) / kChunk] = make_float2((float)w0, (float)w1);
+      if (ckd) {
+        const float h0 = (float)w0, h1 = (float)w1;
+        ckd[(l - m) / kChunk] = make_float4(h0, (float)(w0 - (double)h0), h1, (float)(w1 - (double)h1));
+      }
     }
     if (l + 2 > L) break;
     const double n0 = fma(-Am[l + 2], yy, Am[l + 2]) * v1 - v0;
@@ -307,6 +314,7 @@ int grid_build_tables(Grid& g) {
   {
     std::vector<double> fmm(L + 1, 0.0);
     for (int m = 1; m <= L; ++m) fmm[m] = std::sqrt((2.0 * m + 1.0) / (2.0 * m));
+    g.fmm_h = fmm;
     DevMem d_fmm, d_sin, d_sv, d_sk;
     CMBWS_TRY(d_fmm.upload(fmm.data(), fmm.size() * 8));
     CMBWS_TRY(d_sin.upload(sh.data(), sh.size() * 8));
@@ -331,7 +339,7 @@ int grid_build_tables(Grid& g) {
     CMBWS_TRY(g.ck32.alloc((size_t)tot * 8));
     k_start<<<grd, 128>>>(g.y64.as<double>(), g.A64.as<double>(), L, g.npair, d_sv.as<double>(),
                           d_sk.as<int>(), g.ls.as<int>(), g.st64.as<double2>(), g.st32.as<float2>(),
-                          g.ck_base.as<int64_t>(), g.ck32.as<float2>());
+                          g.ck_base.as<int64_t>(), g.ck32.as<float2>(), nullptr);
     CMBWS_LAUNCH_CHECK();
     CMBWS_CUDA(cudaDeviceSynchronize());
   }
@@ -390,6 +398,50 @@ int grid_build_tables(Grid& g) {
     CMBWS_TRY(g.plans_d.upload(g.plans.data(), g.plans.size() * sizeof(FftPlan)));
     CMBWS_TRY(g.pair_plan.upload(pplan.data(), pplan.size() * 4));
   }
+  return CMBWS_OK;
+}
+
+__global__ void k_to_df(const double* __restrict__ v, float2* __restrict__ o, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float h = (float)v[i];
+  o[i] = make_float2(h, (float)(v[i] - (double)h));
+}
+
+int grid_ensure_ck64(const Grid& gc) {
+  std::lock_guard<std::mutex> lk(gc.ck64_mu);
+  if (gc.ck64.p) return CMBWS_OK;
+  Grid& g = const_cast<Grid&>(gc);  // tables only; the geometry is not touched
+  const int L = g.lmax;
+  int64_t tot = 0;
+  for (int m = 0; m <= L; ++m) tot += (int64_t)g.npair * ((L - m + kChunk) / kChunk);
+  DevMem d_fmm, d_sin, d_sv, d_sk, ls_t, st64_t, st32_t;
+  std::vector<double> sh(g.npair);
+  for (int p = 0; p < g.npair; ++p) sh[p] = std::sin(g.theta[p]);
+  CMBWS_TRY(d_fmm.upload(g.fmm_h.data(), g.fmm_h.size() * 8));
+  CMBWS_TRY(d_sin.upload(sh.data(), sh.size() * 8));
+  const int64_t nst = (int64_t)(L + 1) * g.npair;
+  CMBWS_TRY(d_sv.alloc(nst * 8));
+  CMBWS_TRY(d_sk.alloc(nst * 4));
+  CMBWS_TRY(ls_t.alloc(nst * 4));
+  CMBWS_TRY(st64_t.alloc(nst * 16));
+  CMBWS_TRY(st32_t.alloc(nst * 8));
+  DevMem ck, y2;
+  CMBWS_TRY(ck.alloc((size_t)tot * 16));
+  CMBWS_TRY(y2.alloc((size_t)g.npair * 8));
+  k_to_df<<<(g.npair + 127) / 128, 128>>>(g.y64.as<double>(), y2.as<float2>(), g.npair);
+  CMBWS_LAUNCH_CHECK();
+  k_seeds<<<(g.npair + 127) / 128, 128>>>(d_sin.as<double>(), d_fmm.as<double>(), L, g.npair,
+                                          d_sv.as<double>(), d_sk.as<int>());
+  CMBWS_LAUNCH_CHECK();
+  dim3 grd((g.npair + 127) / 128, L + 1);
+  k_start<<<grd, 128>>>(g.y64.as<double>(), g.A64.as<double>(), L, g.npair, d_sv.as<double>(),
+                        d_sk.as<int>(), ls_t.as<int>(), st64_t.as<double2>(), st32_t.as<float2>(),
+                        g.ck_base.as<int64_t>(), nullptr, ck.as<float4>());
+  CMBWS_LAUNCH_CHECK();
+  CMBWS_CUDA(cudaDeviceSynchronize());
+  g.y2f = std::move(y2);
+  g.ck64 = std::move(ck);
   return CMBWS_OK;
 }
 
