@@ -159,6 +159,24 @@ def multires_fullsky(scale=1):
     return Workload(f"multires_fullsky_nside{256 // scale}-{1024 // scale}", SEED_BASE + 1, bands, comps)
 
 
+def differentiable(lmax=511):
+    """Ncomp = 3 (CMB, synch beta -3.0, dust beta 1.6), Nobs = 5 (30/70/143/353/857 GHz), all
+    on Gauss-Legendre grids at L = lmax (lmax + 1 rings x 2 lmax + 1 px), FWHM 40/30/20/15/10
+    arcmin, sigma varying x3 over the sky, full sky, scalar mixing."""
+    bands = [Band(f, "gl", lmax, lmax, fw, 10.0, contrast=3.0)
+             for f, fw in ((30.0, 40.0), (70.0, 30.0), (143.0, 20.0), (353.0, 15.0), (857.0, 10.0))]
+    comps = [Comp("cmb", lmax, "cmb", None, 1.0, 0.40),
+             Comp("synch", lmax, "synch", -3.0, 30.0, 0.35),
+             Comp("dust", lmax, "dust", 1.6, 353.0, 0.75)]
+    return Workload(f"differentiable_gl{lmax}_3comp_5band", SEED_BASE + 5, bands, comps)
+
+
+def harmonic_weight(lmax_comp, seed=SEED_BASE + 5):
+    """Diagonal harmonic weight w_lm ~ U[0, 1] over a stacked component vector."""
+    n = sum((L + 1) ** 2 for L in lmax_comp)
+    return np.random.default_rng([seed, 7]).uniform(0.0, 1.0, n)
+
+
 def sigma_map(band, z, phi, rng):
     """Per-pixel noise rms: sigma_nu * contrast^s(n) with s a smooth field in [0, 1]."""
     if band.contrast == 1.0:
