@@ -203,6 +203,33 @@ int cmbws_rhs(cmbws_model m, const double* const* d, const double* const* omega1
               const double* omega2, double* b, void* stream);
 
 /*
+ * Terms of the gradient of a loss of the solution.  The paper solves A x = b
+ * (Eq. A) for fixed parameters; differentiating A x = b gives, for a loss L(x)
+ * and the adjoint solution lambda of A lambda = dL/dx (A is symmetric),
+ *   dL/dtheta = lambda^T (db/dtheta - (dA/dtheta) x).
+ * This call evaluates that form for the scalar mixing entries theta = q_{nu,k}
+ * (P_{nu,k} = Y_nu B_nu q_{nu,k}, Eq. P) and for a log-scale theta = t_k of each
+ * prior spectrum (C_{k,l} -> exp(t_k) C_{k,l}, at t_k = 0), with b the right-hand
+ * side of cmbws_rhs built from the same d, omega1, omega2:
+ *   out[nu * ncomp + k] = <B_nu lambda_k, Y^T (N^-1 d + N^-1/2 omega1 - N^-1 P x)>_nu
+ *                       - <B_nu x_k, Y^T N^-1 P lambda>_nu
+ *   out[nobs * ncomp + k] = lambda_k^T S_k^-1 x_k - 1/2 lambda_k^T S_k^-1/2 omega2_k
+ * (dot products over l <= min(L_nu, L_k)).  Spectral indices and amplitudes follow
+ * by the chain rule (dq/dbeta = q ln(nu / nu_0) for a power law).
+ *   x, lambda: device stacked vectors.  d, omega1: host arrays [nobs] of device maps
+ *   (omega1 may be NULL); omega2: device stacked vector or NULL.
+ *   out: device array of nobs * ncomp + ncomp doubles, written.
+ * The transforms run FP64-accurate (FP64 for FP64 models, CMBWS_FP32X2 otherwise);
+ * the sums are reduced in a fixed order.  Uses the model's workspaces: calls on one
+ * model must not overlap.
+ * Errors: CMBWS_ERR_ARG for models with spatially variable mixing (the gradient with
+ * respect to a mixing map is not provided) or NULL arguments.
+ */
+int cmbws_grad_terms(cmbws_model m, const double* x, const double* lambda,
+                     const double* const* d, const double* const* omega1, const double* omega2,
+                     double* out, void* stream);
+
+/*
  * Data-model projection d_nu = P_nu x = Y_nu B_nu sum_k Q~_{nu,k} x_k (Eq. P), e.g. to
  * simulate d = P s + n (Eq. block-data-model).
  *   x: device stacked vector.  d: host array [nobs] of device maps (npix_nu FP64), written.

@@ -5,7 +5,8 @@ CMB component separation with the pseudo-inverse preconditioner of Seljebotn et 
 The compute path is the C-ABI library ``libcmbws.so`` (hand-written CUDA kernels); this
 package is a thin ctypes binding with the same call names (``cmbws_plan_grid``,
 ``cmbws_sht_synth``, ``cmbws_sht_analysis``, ``cmbws_model_create``, ``cmbws_apply_A``,
-``cmbws_apply_precond``, ``cmbws_rhs``, ``cmbws_cg_solve``).  PyTorch only supplies
+``cmbws_apply_precond``, ``cmbws_rhs``, ``cmbws_cg_solve``, ``cmbws_grad_terms``; the
+autograd wrapper is in ``autodiff``).  PyTorch only supplies
 device memory and streams.  There is no CPU fallback: loading fails loudly when the
 library has not been built.
 """
@@ -24,6 +25,7 @@ from .binding import (  # noqa: F401
     cmbws_apply_precond,
     cmbws_cg_solve,
     cmbws_cg_solve_batched,
+    cmbws_grad_terms,
     cmbws_grid_destroy,
     cmbws_grid_info,
     cmbws_grid_rings,

@@ -93,6 +93,7 @@ def load_library(path=None):
     lib.cmbws_apply_precond.argtypes = [vp, vp, vp, vp]
     lib.cmbws_rhs.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp, vp, vp]
     lib.cmbws_project.argtypes = [vp, vp, ctypes.POINTER(vp), vp]
+    lib.cmbws_grad_terms.argtypes = [vp, vp, vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp, vp, vp]
     lib.cmbws_profile_enable.argtypes = [i]
     lib.cmbws_profile_read.argtypes = [ctypes.POINTER(d), ctypes.POINTER(ctypes.c_int64),
                                        ctypes.POINTER(d), i]
@@ -333,6 +334,23 @@ def cmbws_rhs(model, d, b, omega1=None, omega2=None, stream=None):
     w2 = _dptr(omega2, model.nvec, "omega2") if omega2 is not None else ctypes.c_void_p()
     _check(load_library().cmbws_rhs(model.handle, dp, w1, w2, _dptr(b, model.nvec, "b"),
                                     _stream(stream)))
+
+
+def cmbws_grad_terms(model, x, lam, d, out, omega1=None, omega2=None, stream=None):
+    """out[nu * ncomp + k] = dL/dq_{nu,k}, out[nobs * ncomp + k] = dL/dt_k given the solution x
+    and the adjoint solution lam (A lam = dL/dx); out: CUDA float64 of nobs * ncomp + ncomp."""
+    nobs, ncomp = model.nobs, len(model.lmax_comp)
+    dp = (ctypes.c_void_p * nobs)(*[_dptr(d[nu], model.grids[nu].npix, f"d[{nu}]").value
+                                    for nu in range(nobs)])
+    if omega1 is not None:
+        w1 = (ctypes.c_void_p * nobs)(*[_dptr(omega1[nu], model.grids[nu].npix, f"omega1[{nu}]").value
+                                        for nu in range(nobs)])
+    else:
+        w1 = ctypes.POINTER(ctypes.c_void_p)()
+    w2 = _dptr(omega2, model.nvec, "omega2") if omega2 is not None else ctypes.c_void_p()
+    _check(load_library().cmbws_grad_terms(model.handle, _dptr(x, model.nvec, "x"),
+                                           _dptr(lam, model.nvec, "lam"), dp, w1, w2,
+                                           _dptr(out, nobs * ncomp + ncomp, "out"), _stream(stream)))
 
 
 def cmbws_project(model, x, d, stream=None):

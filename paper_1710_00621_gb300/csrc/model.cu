@@ -869,6 +869,7 @@ int model_create(const cmbws_model_desc* desc, int prec, cudaStream_t s, Model**
   CMBWS_TRY(M->d_q.upload(q.data(), q.size() * 8));
   CMBWS_TRY(M->d_beam.upload(beam.data(), beam.size() * 8));
   CMBWS_TRY(M->d_beamOff.upload(beamOff.data(), no * 8));
+  M->beam_off_h = beamOff;
   CMBWS_TRY(M->d_cinv.upload(cinv.data(), cinv.size() * 8));
   CMBWS_TRY(M->d_cisq.upload(cisq.data(), cisq.size() * 8));
   CMBWS_TRY(M->d_clOff.upload(clOff.data(), nc * 8));

@@ -81,9 +81,13 @@ struct Model {
   std::vector<double> alpha;
   std::vector<DevMem> pixA64, pixA32, pixM64, pixM32, tausq;
   DevMem d_compL, d_compOff, d_q, d_beam, d_beamOff, d_cinv, d_cisq, d_clOff, d_Up;
+  std::vector<int64_t> beam_off_h;  // host copy of the beam offsets
   DevMem part, tprior, pixtmp;
   int nsht_A = 0, nsht_M = 0;
   long long n_sht = 0;  // SHTs executed since creation (paper's counting)
+
+  // gradient-term workspace (grad.cu): band maps and per-block partial sums
+  DevMem gradmaps, gradpart;
 
   // CG workspace (cg.cu)
   DevMem cg_r, cg_z, cg_p, cg_q, cg_d, cg_x, cg_red;

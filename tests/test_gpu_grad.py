@@ -1,0 +1,170 @@
+"""GPU parity of the solution gradient (cmbws_grad_terms and the autograd wrapper).
+
+* the gradient terms against the oracle's operator form on the same x, lambda, d;
+* the full gradient of ||W x||^2 against the oracle (dense Cholesky solves) at L = 31;
+* the gradient in spectral indices and amplitudes against central finite differences
+  of FP64 GPU solves (step 1e-4), at L = 127 and at the full L = 511 problem, where the
+  FP32 model (FP64 scalars, double-float certified residual) is compared as well.
+"""
+import numpy as np
+import pytest
+
+import skygen
+from oracle import grad as ograd
+from oracle import model as omodel
+from tests._gpu import GridCache, gpu_model, rel_err, to_dev, to_host
+from tests._models import oracle_model
+
+pytestmark = pytest.mark.gpu
+
+
+def _inputs(L, cr=False):
+    w = skygen.differentiable(lmax=L)
+    m, inp = oracle_model(w)
+    d = omodel.project(m, inp["x_true"])
+    d = [a + n for a, n in zip(d, inp["noise"])]
+    rng = np.random.default_rng([L, 3])
+    o1 = [rng.standard_normal(t.size) for t in m.tau] if cr else None
+    o2 = rng.standard_normal(m.nvec()) if cr else None
+    return w, m, inp, d, o1, o2
+
+
+@pytest.mark.parametrize("L,cr", [(31, False), (31, True), (100, True)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_grad_terms_parity(L, cr, prec):
+    import paper_1710_00621_gb300 as cw
+    import torch
+    w, m, inp, d, o1, o2 = _inputs(L, cr)
+    p = cw.CMBWS_FP64 if prec == "fp64" else cw.CMBWS_FP32
+    gm, _ = gpu_model(w, inp, p)
+    rng = np.random.default_rng(17)
+    x = rng.standard_normal(m.nvec())
+    lam = rng.standard_normal(m.nvec())
+    dq0, dt0 = ograd.grad_terms(m, x, lam, d, o1, o2)
+    out = torch.empty(m.nobs * m.ncomp + m.ncomp, dtype=torch.float64, device="cuda")
+    cw.cmbws_grad_terms(gm, to_dev(x), to_dev(lam), [to_dev(a) for a in d], out,
+                        [to_dev(a) for a in o1] if cr else None, to_dev(o2) if cr else None)
+    g = to_host(out)
+    # FP64-accurate transforms either way (FP32 models evaluate the terms in double-float)
+    tol = max(1e-11, 4e-16 * (L + 1) ** 2)
+    assert rel_err(g[:m.nobs * m.ncomp].reshape(m.nobs, m.ncomp), dq0) < tol
+    assert rel_err(g[m.nobs * m.ncomp:], dt0) < 1e-13
+
+
+def test_grad_terms_rejects_variable_mixing():
+    import paper_1710_00621_gb300 as cw
+    import torch
+    w = skygen.tiny_plain()
+    for b in w.bands:
+        b.n = b.lmax = 15
+    for c in w.comps:
+        c.lmax = 15
+    m, inp = oracle_model(w)
+    maps = [[None, np.ones(16 * 31)] for _ in w.bands]
+    lm = [[None, 15] for _ in w.bands]
+    gm, _ = gpu_model(w, inp, cw.CMBWS_FP64, mix=(lm, maps))
+    x = torch.zeros(m.nvec(), dtype=torch.float64, device="cuda")
+    out = torch.empty(m.nobs * m.ncomp + m.ncomp, dtype=torch.float64, device="cuda")
+    d = [torch.zeros(t.size, dtype=torch.float64, device="cuda") for t in m.tau]
+    with pytest.raises(cw.CmbwsError):
+        cw.cmbws_grad_terms(gm, x, x, d, out)
+
+
+def _problem(w, inp, d, prec, tol, cache):
+    import paper_1710_00621_gb300 as cw
+    from paper_1710_00621_gb300.autodiff import WienerProblem
+    grids = [cache.get(b) for b in w.bands]
+    return WienerProblem([c.lmax for c in w.comps], grids, inp["beams"], inp["cl"],
+                         [to_dev(t) for t in inp["tau"]], [to_dev(a) for a in d], prec=prec,
+                         tol=tol, maxiter=5000)
+
+
+def _params(w):
+    import torch
+    betas = torch.tensor([0.0 if c.beta is None else c.beta for c in w.comps], dtype=torch.float64,
+                         requires_grad=True)
+    logamp = torch.zeros(len(w.comps), dtype=torch.float64, requires_grad=True)
+    return betas, logamp
+
+
+def _loss(w, prob, betas, logamp, wgt):
+    from paper_1710_00621_gb300.autodiff import power_law_q, wiener_solution
+    q = power_law_q([b.freq for b in w.bands], [c.nu0 for c in w.comps], betas,
+                    [c.beta is None for c in w.comps])
+    x = wiener_solution(q, logamp, prob)
+    return ((wgt * x) ** 2).sum()
+
+
+def test_gradient_matches_oracle_dense_l31():
+    import paper_1710_00621_gb300 as cw
+    w, m, inp, d, _, _ = _inputs(31)
+    wgt_h = skygen.harmonic_weight(m.lmax_comp)
+    b = omodel.rhs(m, d)
+    x = ograd.solve_dense(m, b)
+    L0, g = ograd.weighted_loss(x, wgt_h)
+    lam = ograd.solve_dense(m, g)
+    dq, dt = ograd.grad_terms(m, x, lam, d)
+    freqs = np.array([bd.freq for bd in w.bands])
+    dbeta = np.array([0.0 if c.beta is None else np.sum(dq[:, k] * m.q[:, k] * np.log(freqs / c.nu0))
+                      for k, c in enumerate(w.comps)])
+    prob = _problem(w, inp, d, cw.CMBWS_FP64, 1e-12, GridCache())
+    betas, logamp = _params(w)
+    loss = _loss(w, prob, betas, logamp, to_dev(wgt_h))
+    loss.backward()
+    assert abs(loss.item() - L0) < 1e-9 * L0
+    gb = betas.grad.numpy()
+    ga = logamp.grad.numpy()
+    for k, c in enumerate(w.comps):
+        if c.beta is not None:
+            assert abs(gb[k] - dbeta[k]) < 1e-7 * abs(dbeta[k]), (k, gb[k], dbeta[k])
+    np.testing.assert_allclose(ga, dt, rtol=1e-7)
+
+
+def _fd_check(L, h=1e-4):
+    import paper_1710_00621_gb300 as cw
+    import torch
+    w, m, inp, d, _, _ = _inputs(L)
+    cache = GridCache()
+    wgt = to_dev(skygen.harmonic_weight(m.lmax_comp))
+    prob = _problem(w, inp, d, cw.CMBWS_FP64, 1e-12, cache)
+    betas, logamp = _params(w)
+    loss = _loss(w, prob, betas, logamp, wgt)
+    loss.backward()
+    grad = np.concatenate([betas.grad.numpy(), logamp.grad.numpy()])
+    fd = np.zeros_like(grad)
+    base = np.concatenate([betas.detach().numpy(), logamp.detach().numpy()])
+    nc = len(w.comps)
+    with torch.no_grad():
+        for i in range(2 * nc):
+            if i < nc and w.comps[i].beta is None:
+                continue
+            vals = []
+            for s in (+1, -1):
+                p = base.copy()
+                p[i] += s * h
+                vals.append(float(_loss(w, prob, torch.tensor(p[:nc]), torch.tensor(p[nc:]), wgt)))
+            fd[i] = (vals[0] - vals[1]) / (2 * h)
+    for i in range(2 * nc):
+        if i < nc and w.comps[i].beta is None:
+            continue
+        assert abs(fd[i] - grad[i]) <= 2e-6 * max(abs(fd[i]), 1e-6 * loss.item()), (i, fd[i], grad[i])
+    return w, inp, d, cache, wgt, grad
+
+
+def test_gradient_central_differences_l127():
+    _fd_check(127)
+
+
+def test_gradient_full_size_l511_fp64_fd_and_fp32():
+    import paper_1710_00621_gb300 as cw
+    w, inp, d, cache, wgt, g64 = _fd_check(511)
+    prob = _problem(w, inp, d, cw.CMBWS_FP32, 1e-10, cache)
+    betas, logamp = _params(w)
+    loss = _loss(w, prob, betas, logamp, wgt)
+    loss.backward()
+    g32 = np.concatenate([betas.grad.numpy(), logamp.grad.numpy()])
+    nc = len(w.comps)
+    for i in range(2 * nc):
+        if i < nc and w.comps[i].beta is None:
+            continue
+        assert abs(g32[i] - g64[i]) <= 1e-7 * abs(g64[i]), (i, g32[i], g64[i])
