@@ -64,8 +64,19 @@ typedef enum { CMBWS_GRID_GL = 0, CMBWS_GRID_HEALPIX = 1 } cmbws_grid_kind;
  *   CMBWS_FP32:   FP32 throughout (relative error ~1e-6 at L ~ 3000).
  *   CMBWS_FP32X2: FP64-accurate Legendre stage in double-float arithmetic (pairs of FP32
  *                 values, ~48-bit significand, on the FP32 pipe, which GB300 runs 61x
- *                 faster than FP64); ring FFTs and pixel stages in FP64. */
-typedef enum { CMBWS_FP64 = 0, CMBWS_FP32 = 1, CMBWS_FP32X2 = 2 } cmbws_prec;
+ *                 faster than FP64); ring FFTs and pixel stages in FP64.
+ *   CMBWS_TF32:   as CMBWS_FP32, with the Legendre synthesis on the tensor cores (tcgen05,
+ *                 TF32 recurrence values and coefficients, FP32 accumulation; relative error
+ *                 ~1e-4); the adjoint Legendre stage stays FP32 on the CUDA cores.
+ *   CMBWS_3XTF32: as CMBWS_TF32 with split-TF32 products (hi/lo parts, three MMAs per
+ *                 step), FP32-level accuracy. */
+typedef enum {
+  CMBWS_FP64 = 0,
+  CMBWS_FP32 = 1,
+  CMBWS_FP32X2 = 2,
+  CMBWS_TF32 = 3,
+  CMBWS_3XTF32 = 4
+} cmbws_prec;
 
 typedef struct cmbws_grid_s* cmbws_grid;    /* opaque, library-owned */
 typedef struct cmbws_model_s* cmbws_model;  /* opaque, library-owned */
@@ -242,8 +253,9 @@ int cmbws_project(cmbws_model m, const double* x, double* const* d, void* stream
  * CUDA events on the launching stream.  Records are kept per slot = stage + 6 * arith,
  * stages 0 Legendre synthesis, 1 Legendre adjoint, 2 adjoint partial-sum reduction,
  * 3 ring FFT, 4 harmonic-space kernels, 5 CG vector kernels; arith 0 = FP32, 1 = FP64,
- * 2 = double-float (CMBWS_FP32X2).  cmbws_profile_read synchronises the recorded events and
- * writes, per slot (host arrays of 18, any may be NULL), the summed milliseconds, the launch count
+ * 2 = double-float (CMBWS_FP32X2), 3 = TF32 tensor cores, 4 = split TF32 tensor cores.
+ * cmbws_profile_read synchronises the recorded events and writes, per slot (host arrays
+ * of 30, any may be NULL), the summed milliseconds, the launch count
  * and the summed algorithmic flops (Legendre stages: 4 flops per (l, m, ring pair) for
  * the recurrence plus 4 per map for the contraction, over the full (l, m) triangle;
  * 0 elsewhere) since the last reset; reset = 1 clears the record.

@@ -11,11 +11,13 @@ device memory and streams.  There is no CPU fallback: loading fails loudly when 
 library has not been built.
 """
 from .binding import (  # noqa: F401
+    CMBWS_3XTF32,
     CMBWS_FP32,
     CMBWS_FP32X2,
     CMBWS_FP64,
     CMBWS_GRID_GL,
     CMBWS_GRID_HEALPIX,
+    CMBWS_TF32,
     CmbwsError,
     CgOpts,
     CgReport,

@@ -19,6 +19,8 @@ CMBWS_GRID_HEALPIX = 1
 CMBWS_FP64 = 0
 CMBWS_FP32 = 1
 CMBWS_FP32X2 = 2
+CMBWS_TF32 = 3
+CMBWS_3XTF32 = 4
 
 _ERRORS = {-1: "CMBWS_ERR_ARG", -2: "CMBWS_ERR_CUDA", -3: "CMBWS_ERR_NOMEM",
            -4: "CMBWS_ERR_SINGULAR", -5: "CMBWS_ERR_BREAKDOWN", -6: "CMBWS_ERR_NOT_CONVERGED",
@@ -369,17 +371,20 @@ def cmbws_profile_enable(on=True):
     _check(load_library().cmbws_profile_enable(1 if on else 0))
 
 
+PROFILE_ARITH = ("fp32", "fp64", "fp32x2", "tf32", "3xtf32")
+
+
 def cmbws_profile_read(reset=True):
-    """{(stage, "fp32"|"fp64"|"fp32x2"): (milliseconds, launches, algorithmic flops)} since the
-    last reset."""
-    ns = len(PROFILE_STAGES)
-    ms = (ctypes.c_double * (3 * ns))()
-    n = (ctypes.c_int64 * (3 * ns))()
-    fl = (ctypes.c_double * (3 * ns))()
+    """{(stage, arith): (milliseconds, launches, algorithmic flops)} since the last reset;
+    arith in PROFILE_ARITH."""
+    ns, na = len(PROFILE_STAGES), len(PROFILE_ARITH)
+    ms = (ctypes.c_double * (na * ns))()
+    n = (ctypes.c_int64 * (na * ns))()
+    fl = (ctypes.c_double * (na * ns))()
     _check(load_library().cmbws_profile_read(ms, n, fl, 1 if reset else 0))
     out = {}
-    for i in range(3 * ns):
-        out[(PROFILE_STAGES[i % ns], ("fp32", "fp64", "fp32x2")[i // ns])] = (ms[i], n[i], fl[i])
+    for i in range(na * ns):
+        out[(PROFILE_STAGES[i % ns], PROFILE_ARITH[i // ns])] = (ms[i], n[i], fl[i])
     return out
 
 

@@ -147,8 +147,8 @@ extern "C" int cmbws_profile_enable(int on) {
 extern "C" int cmbws_profile_read(double* ms, int64_t* launches, double* flops, int reset) {
   clear_error();
   std::lock_guard<std::mutex> lk(g_prof_mu);
-  double t[3 * PROF_N] = {0}, f[3 * PROF_N] = {0};
-  int64_t c[3 * PROF_N] = {0};
+  double t[PROF_ARITH * PROF_N] = {0}, f[PROF_ARITH * PROF_N] = {0};
+  int64_t c[PROF_ARITH * PROF_N] = {0};
   for (const ProfRec& r : g_prof) {
     CMBWS_CUDA(cudaEventSynchronize(r.b));
     float dt = 0.f;
@@ -157,7 +157,7 @@ extern "C" int cmbws_profile_read(double* ms, int64_t* launches, double* flops, 
     f[r.slot] += r.flops;
     c[r.slot] += 1;
   }
-  for (int i = 0; i < 3 * PROF_N; ++i) {
+  for (int i = 0; i < PROF_ARITH * PROF_N; ++i) {
     if (ms) ms[i] = t[i];
     if (launches) launches[i] = c[i];
     if (flops) flops[i] = f[i];

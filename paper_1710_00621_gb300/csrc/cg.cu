@@ -280,7 +280,7 @@ static int cg_solve_impl(Model& M, const double* b, double* x, const cmbws_cg_op
     }
     // inner solve A d = r; FP64 models aim directly at the target (plus a small
     // margin for the gap between recursive and true residuals)
-    const double stop = M.prec != CMBWS_FP32 ? 0.5 * target
+    const double stop = !is_f32(M.prec) ? 0.5 * target
                                              : std::max(o.inner_tol * std::sqrt(rr), 0.5 * target);
     int it = 0;
     double rr_in;

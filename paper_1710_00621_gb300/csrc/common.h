@@ -180,15 +180,20 @@ int pack_alm(const Grid& g, int prec, int nmaps, const double* packed, void* alm
 int unpack_alm(const Grid& g, int nmaps, const double* lmc, double* packed, cudaStream_t s);
 
 // FP32 transforms use float buffers; FP64 and FP32X2 use the FP64 layouts.
-inline bool is_f32(int prec) { return prec == CMBWS_FP32; }
+// FP32 buffers and CUDA-core FP32 stages (the TF32 modes differ in the Legendre synthesis only)
+inline bool is_f32(int prec) {
+  return prec == CMBWS_FP32 || prec == CMBWS_TF32 || prec == CMBWS_3XTF32;
+}
+inline bool is_tc(int prec) { return prec == CMBWS_TF32 || prec == CMBWS_3XTF32; }
 inline size_t prec_size(int prec) { return is_f32(prec) ? 4 : 8; }
-inline int arith_of(int prec) { return prec == CMBWS_FP32 ? 0 : prec == CMBWS_FP64 ? 1 : 2; }
 inline bool valid_prec(int prec) {
-  return prec == CMBWS_FP64 || prec == CMBWS_FP32 || prec == CMBWS_FP32X2;
+  return prec == CMBWS_FP64 || prec == CMBWS_FP32 || prec == CMBWS_FP32X2 || is_tc(prec);
 }
 
 // ---- double-float Legendre stage (legendre_df.cu) ----
 int legendre_synth_df(const Grid& g, int nmaps, const void* alm, void* F, cudaStream_t s);
+// ---- tensor-core Legendre synthesis (legendre_tc.cu), prec CMBWS_TF32 / CMBWS_3XTF32 ----
+int legendre_synth_tc(const Grid& g, int prec, int nmaps, const void* alm, void* F, cudaStream_t s);
 // double-float adjoint from chunk checkpoints: F (FP64 ring spectra of nm maps) ->
 // out (FP64 coefficients); eo is a scratch of legendre_adjoint_part_bytes bytes
 int legendre_adj_df_ck(const Grid& g, int nm, const void* F, void* eo, double* out, cudaStream_t s);
@@ -200,8 +205,9 @@ int ensure_dyn_smem(const void* func, size_t bytes);
 
 // ---- kernel timing (api.cu): CUDA events around launches while enabled ----
 // Stages; a record's slot is stage + PROF_N * arith, arith 0 = FP32, 1 = FP64,
-// 2 = double-float (FP32X2).  `flops` is the algorithmic count of the launch (full (l, m)
-// triangle), 0 for stages without one.
+// 2 = double-float (FP32X2), 3 = TF32 tensor cores, 4 = split TF32 (PROF_ARITH kinds).
+// `flops` is the algorithmic count of the launch (full (l, m) triangle), 0 for stages
+// without one.
 enum {
   PROF_LEG_SYNTH = 0,
   PROF_LEG_ADJ = 1,
@@ -209,7 +215,8 @@ enum {
   PROF_FFT = 3,
   PROF_HARM = 4,
   PROF_CG = 5,
-  PROF_N = 6
+  PROF_N = 6,
+  PROF_ARITH = 5
 };
 struct ProfScope {
   int slot;

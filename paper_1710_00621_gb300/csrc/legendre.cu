@@ -616,13 +616,14 @@ int adj_dispatch(const Grid& g, int nmaps, const void* F, void* part, double* ou
 
 int legendre_synth(const Grid& g, int prec, int nmaps, const void* alm, void* F, cudaStream_t s) {
   if (prec == CMBWS_FP32X2) return legendre_synth_df(g, nmaps, alm, F, s);
+  if (is_tc(prec)) return legendre_synth_tc(g, prec, nmaps, alm, F, s);
   if (prec == CMBWS_FP64) return synth_dispatch<double>(g, nmaps, alm, F, s);
   return synth_dispatch<float>(g, nmaps, alm, F, s);
 }
 
 size_t legendre_adjoint_part_bytes(const Grid& g, int prec, int nmaps) {
   const int nm = nmaps < 4 ? nmaps : 4;
-  if (prec == CMBWS_FP32)  // E/O parts of the checkpointed adjoint
+  if (is_f32(prec))  // E/O parts of the checkpointed FP32 adjoint
     return (size_t)(g.lmax + 1) * g.npair * 4 * nm * sizeof(float);
   if (prec == CMBWS_FP32X2)  // double-float E/O parts
     return (size_t)(g.lmax + 1) * g.npair * 4 * nm * 2 * sizeof(float);

@@ -1,0 +1,359 @@
+// Legendre synthesis on the fifth-generation tensor cores (tcgen05, TF32 inputs,
+// FP32 accumulation in tensor memory).
+//
+// Per m and ring pair the synthesis F_m(theta) = sum_l lambda_lm(theta) a_lm (Sec. 2.1)
+// is, for a tile of 128 ring pairs, the product D[pair][col] = sum_l Lambda[pair][l] B[l][col]
+// with B[l][parity(l - m) * 8 + part] = a_lm part (real / imaginary of each map), so that
+// columns 0..7 accumulate the even sums E and 8..15 the odd sums O of every map, and
+// F_north = E + O, F_south = E - O.
+//
+// * Lambda is generated on the fly by the recurrence of legendre.cu (one thread per ring
+//   pair, start values injected at the pair's first significant l), rounded to TF32 and
+//   written by each thread into its own lane of tensor memory (tcgen05.st), so the A operand
+//   of the MMA never passes through shared memory;
+// * B (the block's coefficients, 16 x 32 TF32) is written to shared memory in the
+//   K-major core-matrix layout and described by a shared-memory descriptor;
+// * blocks of 32 values of l alternate between two tensor-memory / shared-memory stages;
+//   one thread issues the MMAs (M = 128, N = 16, K = 8) and commits them to the stage's
+//   mbarrier, which the threads wait on (bounded) before overwriting the stage;
+// * SPLIT = 1 keeps FP32-level accuracy with the split-TF32 product
+//   A_hi B_hi + A_hi B_lo + A_lo B_hi (x = hi + lo, hi = tf32(x), lo = tf32(x - hi)).
+#include <climits>
+
+#include "common.h"
+
+namespace cmbws {
+
+namespace {
+
+constexpr int kTcNT = 128;  // threads = ring pairs per CTA = MMA M
+constexpr int kTcKB = 32;   // values of l per stage (4 MMAs of K = 8)
+
+// Round to TF32 (10 explicit significand bits), nearest with ties away from zero: adding
+// half a unit of the 11th bit to the bit pattern carries into the kept bits exactly when the
+// dropped 13 bits are at least half a unit (sign-magnitude format, finite inputs).  The MMA
+// reads only the upper 19 bits of a TF32 operand, so tf32_bits() leaves the low bits for it
+// to drop; tf32_rna() clears them (needed where the rounded value is reused).
+__device__ __forceinline__ uint32_t tf32_bits(float x) { return __float_as_uint(x) + 0x1000u; }
+__device__ __forceinline__ uint32_t tf32_rna(float x) { return tf32_bits(x) & 0xFFFFE000u; }
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// K-major, no-swizzle shared-memory matrix descriptor: core matrices of 8 rows x 16 bytes,
+// LBO = byte step between core matrices along K, SBO = along N; descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor: D FP32, A and B TF32, both K-major, N = 16, M = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint32_t a, uint64_t bdesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(d),
+      "r"(a), "l"(bdesc), "r"(kIdesc), "r"(acc));
+}
+
+// Wait for the completion of phase `parity` of an mbarrier; false after the limit.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_addr(bar);
+  const long long t0 = clock64();
+  for (int it = 0; it < (1 << 26); ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > (1ll << 32)) break;  // about two seconds
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};\n" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]),
+      "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]),
+      "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]),
+      "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31]));
+}
+
+template <int SPLIT>
+struct TcLayout {
+  static constexpr int kBStage = 4 * 512;                         // one 16 x 32 TF32 tile
+  static constexpr int kStage = (SPLIT ? 2 : 1) * kBStage;        // hi (+ lo) per stage
+  static constexpr int kOffA = 2 * kStage;                        // float sAc[2][32]
+  static constexpr int kOffBar = kOffA + 2 * kTcKB * 4;           // uint64_t mbar[2]
+  static constexpr int kOffT = kOffBar + 16;                      // uint32_t tmem base, bad flag
+  static constexpr int kUsed = kOffT + 16;
+  // Shared memory requested per CTA: caps residency so that the CTAs of an SM never ask
+  // for more than its 512 tensor-memory columns (4 x 128 or 2 x 256).
+  static constexpr int kSmem = SPLIT ? 80 * 1024 : 48 * 1024;
+  static constexpr uint32_t kCols = SPLIT ? 256 : 128;
+  static constexpr uint32_t kColA = 0, kColAlo = 64, kColD = SPLIT ? 128 : 64;
+};
+
+// Byte offset of B[n][k] (n < 16 output column, k < 32 within the block) in a stage tile.
+__device__ __forceinline__ int b_off(int n, int k) {
+  return (k >> 3) * 512 + (n >> 3) * 256 + ((k >> 2) & 1) * 128 + (n & 7) * 16 + (k & 3) * 4;
+}
+
+template <int NM, int SPLIT>
+__global__ void __launch_bounds__(kTcNT)
+k_leg_synth_tc(const float2* __restrict__ alm, int64_t alm_stride, const float* __restrict__ Acoef,
+               const int* __restrict__ ls_tab, const float2* __restrict__ st,
+               const float* __restrict__ yr, const int2* __restrict__ pring, float2* __restrict__ F,
+               int64_t F_stride, int L, int npair) {
+  using LY = TcLayout<SPLIT>;
+  static_assert(NM >= 1 && NM <= 4, "at most 4 maps (16 output columns)");
+  extern __shared__ __align__(1024) unsigned char sm[];
+  float* sAc = reinterpret_cast<float*>(sm + LY::kOffA);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + LY::kOffBar);
+  uint32_t* s_tb = reinterpret_cast<uint32_t*>(sm + LY::kOffT);
+  int* s_lo = reinterpret_cast<int*>(sm + LY::kOffT + 4);
+  int* s_bad = reinterpret_cast<int*>(sm + LY::kOffT + 8);
+
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int m = blockIdx.y;
+  const int64_t lmo = lm_off(L, m) - m;
+  const int p = blockIdx.x * kTcNT + tid;
+  const bool valid = p < npair;
+  const int ls = valid ? ls_tab[(int64_t)m * npair + p] : INT_MAX;
+  const float y = valid ? yr[p] : 0.f;
+  const float2 inj = valid ? st[(int64_t)m * npair + p] : make_float2(0.f, 0.f);
+
+  if (tid == 0) {
+    *s_lo = INT_MAX;
+    *s_bad = 0;
+  }
+  __syncthreads();
+  atomicMin(s_lo, ls);
+  __syncthreads();
+  const int lo = *s_lo;
+  if (lo > L) {  // no pair of the tile has a significant value at this m
+    if (valid) {
+      const int2 rr = pring[p];
+#pragma unroll
+      for (int k = 0; k < NM; ++k) {
+        F[k * F_stride + (int64_t)rr.x * (L + 1) + m] = make_float2(0.f, 0.f);
+        if (rr.y >= 0) F[k * F_stride + (int64_t)rr.y * (L + 1) + m] = make_float2(0.f, 0.f);
+      }
+    }
+    return;
+  }
+  const int nb = (L - lo + kTcKB) / kTcKB;
+
+  // zero the B tiles (positions of the other parity and of absent maps stay zero)
+  for (int i = tid; i < 2 * LY::kStage / 16; i += kTcNT)
+    reinterpret_cast<float4*>(sm)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_addr(s_tb)),
+                 "r"(LY::kCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&mbar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&mbar[1])));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+  const uint32_t tb = *s_tb;
+  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+
+  // B element of this thread: block position k, map j (real and imaginary columns)
+  const int kk = tid & 31, jj = tid >> 5;
+  const int n_re = (kk & 1) * 8 + 2 * jj;
+  auto load_coef = [&](int b) {
+    const int l = lo + b * kTcKB + kk;
+    float2 v = make_float2(0.f, 0.f);
+    if (jj < NM && l <= L) v = alm[jj * alm_stride + lmo + l];
+    return v;
+  };
+  auto load_A = [&](int b) {
+    const int l = lo + b * kTcKB + tid;
+    return (tid < kTcKB && l <= L) ? Acoef[lmo + l] : 0.f;
+  };
+  float2 cnext = load_coef(0);
+  float anext = load_A(0);
+
+  float mu1 = 0.f, mu2 = 0.f;
+  bool bad = false;
+  for (int b = 0; b < nb; ++b) {
+    const int s = b & 1;
+    // once a wait has failed no more MMAs are issued, so later waits are skipped
+    if (b >= 2 && !*s_bad && !mbar_wait(&mbar[s], ((b - 2) >> 1) & 1)) bad = true;
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+    // stage the block's coefficients (B) and recurrence coefficients A_l
+    {
+      unsigned char* bs = sm + s * LY::kStage;
+      if (jj < NM) {
+        const uint32_t hr = tf32_rna(cnext.x), hi = tf32_rna(cnext.y);
+        *reinterpret_cast<uint32_t*>(bs + b_off(n_re, kk)) = hr;
+        *reinterpret_cast<uint32_t*>(bs + b_off(n_re + 1, kk)) = hi;
+        if constexpr (SPLIT) {
+          *reinterpret_cast<uint32_t*>(bs + LY::kBStage + b_off(n_re, kk)) =
+              tf32_bits(cnext.x - __uint_as_float(hr));
+          *reinterpret_cast<uint32_t*>(bs + LY::kBStage + b_off(n_re + 1, kk)) =
+              tf32_bits(cnext.y - __uint_as_float(hi));
+        }
+      }
+      if (tid < kTcKB) sAc[s * kTcKB + tid] = anext;
+    }
+    if (b + 1 < nb) {  // prefetch the next block (consumed next iteration)
+      cnext = load_coef(b + 1);
+      anext = load_A(b + 1);
+    }
+    __syncthreads();
+    // recurrence over the block: lambda values (rescaled) of this thread's pair
+    uint32_t vh[kTcKB];
+    uint32_t vl[kTcKB];
+    const int jinj = ls - (lo + b * kTcKB);  // start of this thread's pair within the block
+    // one step pair (l, l + 1) of the recurrence, TF32 parts written to vh / vl
+    auto step = [&](int j, float2 a2) {
+      const float ma = fmaf(fmaf(-a2.x, y, a2.x), mu1, -mu2);
+      const float mb = fmaf(fmaf(-a2.y, y, a2.y), ma, -mu1);
+      mu2 = ma;
+      mu1 = mb;
+    };
+    auto emit = [&](int j) {
+      if constexpr (SPLIT) {
+        vh[j] = tf32_rna(mu2);
+        vh[j + 1] = tf32_rna(mu1);
+        vl[j] = tf32_bits(mu2 - __uint_as_float(vh[j]));
+        vl[j + 1] = tf32_bits(mu1 - __uint_as_float(vh[j + 1]));
+      } else {
+        vh[j] = tf32_bits(mu2);
+        vh[j + 1] = tf32_bits(mu1);
+      }
+    };
+    const float* sa = &sAc[s * kTcKB];
+    if (__any_sync(0xffffffffu, jinj >= 0 && jinj < kTcKB)) {
+      // a pair of this warp starts in the block: inject its start values at jinj
+#pragma unroll
+      for (int j = 0; j < kTcKB; j += 2) {
+        step(j, *reinterpret_cast<const float2*>(sa + j));
+        if (j == jinj) {
+          mu2 = inj.x;
+          mu1 = inj.y;
+        }
+        emit(j);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < kTcKB; j += 4) {
+        const float4 a4 = *reinterpret_cast<const float4*>(sa + j);
+        step(j, make_float2(a4.x, a4.y));
+        emit(j);
+        step(j + 2, make_float2(a4.z, a4.w));
+        emit(j + 2);
+      }
+    }
+    tmem_st32(tb + lane_base + LY::kColA + 32 * s, vh);
+    if constexpr (SPLIT) tmem_st32(tb + lane_base + LY::kColAlo + 32 * s, vl);
+    asm volatile("tcgen05.wait::st.sync.aligned;\n" ::);
+    asm volatile("fence.proxy.async.shared::cta;\n" ::);
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+    if (bad) atomicOr(s_bad, 1);
+    __syncthreads();
+    if (tid == 0 && !*s_bad) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+      const uint32_t bh = smem_addr(sm + s * LY::kStage);
+#pragma unroll
+      for (int i = 0; i < kTcKB / 8; ++i) {
+        const uint32_t a_hi = tb + LY::kColA + 32 * s + 8 * i;
+        const uint64_t dh = smem_desc(bh + 512 * i, 128, 256);
+        mma_tf32(tb + LY::kColD, a_hi, dh, (b > 0 || i > 0) ? 1u : 0u);
+        if constexpr (SPLIT) {
+          const uint64_t dl = smem_desc(bh + LY::kBStage + 512 * i, 128, 256);
+          mma_tf32(tb + LY::kColD, a_hi, dl, 1u);
+          mma_tf32(tb + LY::kColD, tb + LY::kColAlo + 32 * s + 8 * i, dh, 1u);
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+          smem_addr(&mbar[s])));
+    }
+  }
+  // accumulators of the last block
+  if (!*s_bad && !mbar_wait(&mbar[(nb - 1) & 1], ((nb - 1) >> 1) & 1)) bad = true;
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+  uint32_t d[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(d[0]), "=r"(d[1]), "=r"(d[2]), "=r"(d[3]), "=r"(d[4]), "=r"(d[5]), "=r"(d[6]), "=r"(d[7]),
+        "=r"(d[8]), "=r"(d[9]), "=r"(d[10]), "=r"(d[11]), "=r"(d[12]), "=r"(d[13]), "=r"(d[14]), "=r"(d[15])
+      : "r"(tb + lane_base + LY::kColD));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
+  if (bad) atomicOr(s_bad, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+  __syncthreads();
+  const bool failed = *s_bad != 0;
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tb), "r"(LY::kCols));
+  if (!valid) return;
+  const int2 rr = pring[p];
+  const float nan = __int_as_float(0x7fc00000);
+#pragma unroll
+  for (int k = 0; k < NM; ++k) {
+    const float er = __uint_as_float(d[2 * k]), ei = __uint_as_float(d[2 * k + 1]);
+    const float orr = __uint_as_float(d[8 + 2 * k]), oi = __uint_as_float(d[8 + 2 * k + 1]);
+    // a timed-out wait leaves NaN in the output, which the solver reports as a breakdown
+    const float2 fn = failed ? make_float2(nan, nan) : make_float2(er + orr, ei + oi);
+    const float2 fs = failed ? make_float2(nan, nan) : make_float2(er - orr, ei - oi);
+    F[k * F_stride + (int64_t)rr.x * (L + 1) + m] = fn;
+    if (rr.y >= 0) F[k * F_stride + (int64_t)rr.y * (L + 1) + m] = fs;
+  }
+}
+
+template <int NM, int SPLIT>
+int launch_synth_tc(const Grid& g, const void* alm, int64_t as, void* F, int64_t fs, cudaStream_t s) {
+  using LY = TcLayout<SPLIT>;
+  const int L = g.lmax;
+  dim3 grd((g.npair + kTcNT - 1) / kTcNT, L + 1);
+  auto kern = k_leg_synth_tc<NM, SPLIT>;
+  CMBWS_TRY(ensure_dyn_smem((const void*)kern, LY::kSmem));
+  ProfScope ps(PROF_LEG_SYNTH, s, SPLIT ? 4 : 3, 4.0 * g.npair * (double)nlm_of(L) * (NM + 1));
+  kern<<<grd, kTcNT, LY::kSmem, s>>>((const float2*)alm, as, g.A32.as<float>(), g.ls.as<int>(),
+                                     g.st32.as<float2>(), g.y32.as<float>(), g.pair_ring.as<int2>(),
+                                     (float2*)F, fs, L, g.npair);
+  CMBWS_LAUNCH_CHECK();
+  return CMBWS_OK;
+}
+
+static_assert(TcLayout<0>::kUsed <= TcLayout<0>::kSmem && TcLayout<1>::kUsed <= TcLayout<1>::kSmem,
+              "shared-memory layout exceeds the request");
+
+}  // namespace
+
+int legendre_synth_tc(const Grid& g, int prec, int nmaps, const void* alm, void* F, cudaStream_t s) {
+  const int64_t as = nlm_of(g.lmax), fs = (int64_t)g.nring * (g.lmax + 1);
+  const bool split = prec == CMBWS_3XTF32;
+  for (int k0 = 0; k0 < nmaps; k0 += 4) {
+    const int nm = nmaps - k0 < 4 ? nmaps - k0 : 4;
+    const void* a = (const float2*)alm + k0 * as;
+    void* f = (float2*)F + k0 * fs;
+    int st;
+    switch (nm * 2 + (split ? 1 : 0)) {
+      case 2: st = launch_synth_tc<1, 0>(g, a, as, f, fs, s); break;
+      case 3: st = launch_synth_tc<1, 1>(g, a, as, f, fs, s); break;
+      case 4: st = launch_synth_tc<2, 0>(g, a, as, f, fs, s); break;
+      case 5: st = launch_synth_tc<2, 1>(g, a, as, f, fs, s); break;
+      case 6: st = launch_synth_tc<3, 0>(g, a, as, f, fs, s); break;
+      case 7: st = launch_synth_tc<3, 1>(g, a, as, f, fs, s); break;
+      case 8: st = launch_synth_tc<4, 0>(g, a, as, f, fs, s); break;
+      default: st = launch_synth_tc<4, 1>(g, a, as, f, fs, s); break;
+    }
+    if (st != CMBWS_OK) return st;
+  }
+  return CMBWS_OK;
+}
+
+}  // namespace cmbws

@@ -21,6 +21,13 @@ def tol(prec, lmax):
         return max(1e-12, 1e-16 * (lmax + 1) ** 2)
     if prec == cw.CMBWS_FP32X2:
         return max(4e-12, 4e-16 * (lmax + 1) ** 2)
+    if prec == cw.CMBWS_TF32:
+        # recurrence values and coefficients rounded to TF32 (relative 2^-11 each) before an
+        # FP32-accumulated product: per-term error up to ~1e-3, averaging down over the sum
+        return 4e-3
+    if prec == cw.CMBWS_3XTF32:
+        # split TF32 drops only the lo x lo product (2^-22); the recurrence is the FP32 one
+        return 2 * max(1e-5, 5 * (lmax + 1) * 6e-8)
     return max(1e-5, 5 * (lmax + 1) * 6e-8)
 
 # (kind, n, lmax): tiny, ragged, several CTAs of the Legendre kernels, folded spectra
@@ -60,7 +67,8 @@ def test_grid_geometry_matches_oracle(kind, n, lmax):
     assert g.npix == o.npix
 
 
-PRECS = [cw.CMBWS_FP64, cw.CMBWS_FP32, cw.CMBWS_FP32X2]
+PRECS = [cw.CMBWS_FP64, cw.CMBWS_FP32, cw.CMBWS_FP32X2, cw.CMBWS_TF32, cw.CMBWS_3XTF32]
+TC_PRECS = [cw.CMBWS_TF32, cw.CMBWS_3XTF32]
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -112,6 +120,20 @@ def test_map_batches_of_any_size(nmaps):
         assert rel_err(gb[k], osht.adjoint(o, 23, got[k])) < tol(cw.CMBWS_FP64, 23)
 
 
+@pytest.mark.parametrize("prec", TC_PRECS)
+@pytest.mark.parametrize("nmaps", [1, 2, 3, 4, 5, 9])
+def test_tensor_core_synthesis_map_batches(nmaps, prec):
+    # every map-count variant of the tensor-core kernel (1..4 maps per launch, 16 columns)
+    g = cw.cmbws_plan_grid(cw.CMBWS_GRID_HEALPIX, 32, 95)
+    o = og.healpix(32)
+    alm = np.random.default_rng(50 + nmaps).standard_normal((nmaps, 96 ** 2))
+    out = to_dev(np.zeros((nmaps, g.npix)))
+    cw.cmbws_sht_synth(g, prec, to_dev(alm), out, nmaps)
+    got = to_host(out)
+    for k in range(nmaps):
+        assert rel_err(got[k], osht.synthesis(o, 95, alm[k])) < tol(prec, 95), k
+
+
 @pytest.mark.parametrize("lmax", [31, 255, 1023])
 def test_gl_round_trip_exact_on_gpu(lmax):
     # the double-float path must match FP64 accuracy
@@ -150,8 +172,15 @@ def test_adjointness_large_healpix():
     assert abs(lhs - rhs) <= 1e-10 * abs(lhs)
 
 
-@pytest.mark.parametrize("prec", [cw.CMBWS_FP64, cw.CMBWS_FP32X2])
+@pytest.mark.parametrize("prec", [cw.CMBWS_FP64, cw.CMBWS_FP32X2, cw.CMBWS_FP32, cw.CMBWS_TF32,
+                                  cw.CMBWS_3XTF32])
 def test_full_size_sampled_rings_nside1024(prec):
+    """FP64-accurate modes against the oracle on every sampled ring.  FP32-recurrence modes:
+    near the poles the rescaled three-term recurrence has an almost double characteristic
+    root, so FP32 rounding grows like l^2 eps there (the m = 0 functions of the first polar
+    ring are off by up to ~20 % at l ~ 3000 in FP32); they are compared with the oracle on
+    the rings at theta >= 0.1 rad, and the tensor-core modes with the FP32 CUDA-core path
+    (the same recurrence) on every sampled ring."""
     # Nside 1024, L = 3071 (the largest band grid of the multi-resolution workload):
     # the synthesis of a few rings recomputed by the oracle on a sub-grid of those rings
     g = cw.cmbws_plan_grid(cw.CMBWS_GRID_HEALPIX, 1024, 3071)
@@ -169,4 +198,20 @@ def test_full_size_sampled_rings_nside1024(prec):
                       np.concatenate([[0], np.cumsum(o.nphi[rings])]))
     ref = osht.synthesis(sub, L, a)
     gsub = np.concatenate([got[o.offset[r]:o.offset[r + 1]] for r in rings])
-    assert rel_err(gsub, ref) < tol(cw.CMBWS_FP64, L)
+    if prec in (cw.CMBWS_FP64, cw.CMBWS_FP32X2):
+        assert rel_err(gsub, ref) < tol(cw.CMBWS_FP64, L)
+        return
+    far = np.concatenate([np.full(o.nphi[r], o.theta[r] >= 0.1 and o.theta[r] <= np.pi - 0.1)
+                          for r in rings])
+    assert rel_err(gsub[far], ref[far]) < tol(prec if prec != cw.CMBWS_TF32 else cw.CMBWS_FP32, L) \
+        or (prec == cw.CMBWS_TF32 and rel_err(gsub[far], ref[far]) < tol(cw.CMBWS_TF32, L))
+    if prec != cw.CMBWS_FP32:
+        f32 = to_dev(np.zeros(g.npix))
+        cw.cmbws_sht_synth(g, cw.CMBWS_FP32, to_dev(a), f32, 1)
+        g32 = to_host(f32)
+        g32 = np.concatenate([g32[o.offset[r]:o.offset[r + 1]] for r in rings])
+        # the tensor cores replace only the contraction: TF32 rounding (2^-11 per factor), or
+        # split TF32 (2^-22) whose difference from the CUDA-core path is that of two FP32
+        # accumulations of L terms in different orders (the FP32 bound)
+        bound = tol(cw.CMBWS_TF32, L) if prec == cw.CMBWS_TF32 else tol(cw.CMBWS_FP32, L)
+        assert rel_err(gsub, g32) < bound, rel_err(gsub, g32)
