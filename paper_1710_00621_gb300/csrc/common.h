@@ -87,7 +87,8 @@ struct DevMem {
   template <typename T> T* as() const { return static_cast<T*>(p); }
 };
 
-constexpr int kChunk = 8;  // l-chunk of the checkpointed FP32 adjoint (even)
+constexpr int kChunk = 8;    // l-chunk of the checkpointed FP32 adjoint (even)
+constexpr int kChunkDf = 4;  // l-chunk of the checkpointed double-float adjoint (even)
 
 inline __host__ __device__ int64_t lm_off(int L, int m) {
   return (int64_t)m * (L + 1) - (int64_t)m * (m - 1) / 2;
@@ -132,7 +133,8 @@ struct Grid {
   DevMem st64, st32;      // {mu_ls, mu_ls+1} [L+1][npair]
   DevMem ck32;            // FP32 {mu_l0, mu_l0+1} at every chunk start l0 = m + kChunk c
   DevMem ck_base;         // int64 [L+1]: offset of m's block [pair][chunk] in ck32
-  mutable DevMem ck64;    // double-float {mu_l0, mu_l0+1} (float4), same layout; built on first use
+  mutable DevMem ck64;    // double-float {mu_l0, mu_l0+1} (float4) every kChunkDf; built on first use
+  mutable DevMem ck64_base;  // int64 [L+1]: offset of m's block [pair][chunk] in ck64
   mutable DevMem y2f;     // y as a double-float pair (float2), built with ck64
   mutable std::mutex ck64_mu;
   std::vector<double> fmm_h;  // sqrt((2m+1)/(2m)) (host, for rebuilding seeds)

@@ -231,7 +231,7 @@ struct AdjCkDfWarp {  // one warp's double-buffered tile
 };
 
 // Adjoint in double-float from chunk checkpoints (the FP32 kernel's scheme in
-// legendre.cu with every value a hi + lo pair): one thread per chunk of kChunk values
+// legendre.cu with every value a hi + lo pair): one thread per chunk of kChunkDf values
 // of l loops over all ring pairs, restarting the recurrence at its chunk from the
 // double-float checkpoints, and accumulates each output (l, m, part) with the
 // compensated dot product.  Each output has one owner and a fixed summation order, so
@@ -244,7 +244,7 @@ k_leg_adj_ck_df(const float2* __restrict__ eo, const float2* __restrict__ Acoef,
                 const int64_t* __restrict__ ck_base, const double* __restrict__ c64,
                 double2* __restrict__ out, int64_t nlm, int L, int npair) {
   constexpr int P = 2 * NM;
-  constexpr int K = kChunk;
+  constexpr int K = kChunkDf;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   AdjCkDfWarp<NM, PT>& S = reinterpret_cast<AdjCkDfWarp<NM, PT>*>(smem_raw)[warp];
@@ -375,14 +375,14 @@ int launch_adj_ck_df(const Grid& g, const void* F, int64_t fs, void* eo_buf, dou
     k_adj_eo_df<NM><<<grd, 128, 0, s>>>((const double2*)F, fs, g.pair_ring.as<int2>(), eo, L, g.npair);
     CMBWS_LAUNCH_CHECK();
   }
-  const int maxck = (L + kChunk) / kChunk;
+  const int maxck = (L + kChunkDf) / kChunkDf;
   dim3 grd((maxck + kANT - 1) / kANT, L + 1);
   constexpr size_t sm = sizeof(AdjCkDfWarp<NM, kAPT>) * (kANT / 32);
   auto kern = k_leg_adj_ck_df<NM, kANT, kAPT>;
   CMBWS_TRY(ensure_dyn_smem((const void*)kern, sm));
   ProfScope ps(PROF_LEG_ADJ, s, 2, 4.0 * g.npair * (double)nlm * (NM + 1));
   kern<<<grd, kANT, sm, s>>>(eo, g.A2f.as<float2>(), g.ls.as<int>(), g.st64.as<double2>(),
-                             g.y2f.as<float2>(), g.ck64.as<float4>(), g.ck_base.as<int64_t>(),
+                             g.y2f.as<float2>(), g.ck64.as<float4>(), g.ck64_base.as<int64_t>(),
                              g.c64.as<double>(), (double2*)out, nlm, L, g.npair);
   CMBWS_LAUNCH_CHECK();
   return CMBWS_OK;

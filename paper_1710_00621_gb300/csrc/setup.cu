@@ -141,7 +141,7 @@ __global__ void k_start(const double* __restrict__ y, const double* __restrict__
                         const double* __restrict__ sv, const int* __restrict__ sk,
                         int* __restrict__ ls, double2* __restrict__ st64, float2* __restrict__ st32,
                         const int64_t* __restrict__ ck_base, float2* __restrict__ ck,
-                        float4* __restrict__ ck64) {
+                        const int64_t* __restrict__ ck64_base, float4* __restrict__ ck64) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   const int m = blockIdx.y;
   if (p >= npair) return;
@@ -155,8 +155,9 @@ __global__ void k_start(const double* __restrict__ y, const double* __restrict__
   int found = L + 1;
   double o0 = 0.0, o1 = 0.0;
   const int nck = (L - m + kChunk) / kChunk;
+  const int nckd = (L - m + kChunkDf) / kChunkDf;
   float2* ckp = ck ? ck + ck_base[m] + (int64_t)p * nck : nullptr;
-  float4* ckd = ck64 ? ck64 + ck_base[m] + (int64_t)p * nck : nullptr;
+  float4* ckd = ck64 ? ck64 + ck64_base[m] + (int64_t)p * nckd : nullptr;
   while (l <= L) {
     if (found > L && k == 0 && (fabs(v0) > kStartThreshold || fabs(v1) > kStartThreshold)) {
       found = l;
@@ -164,16 +165,14 @@ __global__ void k_start(const double* __restrict__ y, const double* __restrict__
       o1 = (l + 1 <= L) ? v1 : 0.0;
       if (!ckp && !ckd) break;
     }
-    if ((l - m) % kChunk == 0) {
-      // chunk checkpoint: the recurrence pair at the chunk's first l once the pair has
-      // started there, zero before (a pair starting inside the chunk is injected at ls)
-      const double w0 = found <= l ? v0 : 0.0;
-      const double w1 = (found <= l && l + 1 <= L) ? v1 : 0.0;
-      if (ckp) ckp[(l - m) / kChunk] = make_float2((float)w0, (float)w1);
-      if (ckd) {
-        const float h0 = (float)w0, h1 = (float)w1;
-        ckd[(l - m) / kChunk] = make_float4(h0, (float)(w0 - (double)h0), h1, (float)(w1 - (double)h1));
-      }
+    // chunk checkpoints: the recurrence pair at the chunk's first l once the pair has
+    // started there, zero before (a pair starting inside the chunk is injected at ls)
+    const double w0 = found <= l ? v0 : 0.0;
+    const double w1 = (found <= l && l + 1 <= L) ? v1 : 0.0;
+    if (ckp && (l - m) % kChunk == 0) ckp[(l - m) / kChunk] = make_float2((float)w0, (float)w1);
+    if (ckd && (l - m) % kChunkDf == 0) {
+      const float h0 = (float)w0, h1 = (float)w1;
+      ckd[(l - m) / kChunkDf] = make_float4(h0, (float)(w0 - (double)h0), h1, (float)(w1 - (double)h1));
     }
     if (l + 2 > L) break;
     const double n0 = fma(-Am[l + 2], yy, Am[l + 2]) * v1 - v0;
@@ -339,7 +338,7 @@ int grid_build_tables(Grid& g) {
     CMBWS_TRY(g.ck32.alloc((size_t)tot * 8));
     k_start<<<grd, 128>>>(g.y64.as<double>(), g.A64.as<double>(), L, g.npair, d_sv.as<double>(),
                           d_sk.as<int>(), g.ls.as<int>(), g.st64.as<double2>(), g.st32.as<float2>(),
-                          g.ck_base.as<int64_t>(), g.ck32.as<float2>(), nullptr);
+                          g.ck_base.as<int64_t>(), g.ck32.as<float2>(), nullptr, nullptr);
     CMBWS_LAUNCH_CHECK();
     CMBWS_CUDA(cudaDeviceSynchronize());
   }
@@ -413,8 +412,14 @@ int grid_ensure_ck64(const Grid& gc) {
   if (gc.ck64.p) return CMBWS_OK;
   Grid& g = const_cast<Grid&>(gc);  // tables only; the geometry is not touched
   const int L = g.lmax;
+  std::vector<int64_t> cb(L + 1, 0);
   int64_t tot = 0;
-  for (int m = 0; m <= L; ++m) tot += (int64_t)g.npair * ((L - m + kChunk) / kChunk);
+  for (int m = 0; m <= L; ++m) {
+    cb[m] = tot;
+    tot += (int64_t)g.npair * ((L - m + kChunkDf) / kChunkDf);
+  }
+  DevMem cbd;
+  CMBWS_TRY(cbd.upload(cb.data(), (L + 1) * 8));
   DevMem d_fmm, d_sin, d_sv, d_sk, ls_t, st64_t, st32_t;
   std::vector<double> sh(g.npair);
   for (int p = 0; p < g.npair; ++p) sh[p] = std::sin(g.theta[p]);
@@ -437,10 +442,11 @@ int grid_ensure_ck64(const Grid& gc) {
   dim3 grd((g.npair + 127) / 128, L + 1);
   k_start<<<grd, 128>>>(g.y64.as<double>(), g.A64.as<double>(), L, g.npair, d_sv.as<double>(),
                         d_sk.as<int>(), ls_t.as<int>(), st64_t.as<double2>(), st32_t.as<float2>(),
-                        g.ck_base.as<int64_t>(), nullptr, ck.as<float4>());
+                        g.ck_base.as<int64_t>(), nullptr, cbd.as<int64_t>(), ck.as<float4>());
   CMBWS_LAUNCH_CHECK();
   CMBWS_CUDA(cudaDeviceSynchronize());
   g.y2f = std::move(y2);
+  g.ck64_base = std::move(cbd);
   g.ck64 = std::move(ck);
   return CMBWS_OK;
 }
