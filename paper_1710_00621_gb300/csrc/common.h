@@ -107,6 +107,7 @@ struct FftPlan {
   int pad;
   int64_t chirp;  // offset (complex entries) of b_t = exp(i pi t^2 / n), t < n
   int64_t filt;   // offset of the Bluestein filter spectrum (n2 entries, includes 1/n2)
+  int64_t phase;  // offset of exp(i pi k / n), k < n (ring offset phi0 = pi / n)
 };
 
 struct Grid {
@@ -142,7 +143,8 @@ struct Grid {
   // ring FFT tables (device)
   std::vector<FftPlan> plans;
   DevMem plans_d;
-  DevMem fft64, fft32;    // complex tables: chirps, filters, twiddles
+  DevMem fft64, fft32;    // complex tables: chirps, filters, phases, twiddles
+  DevMem fftdf;           // the same as double-float pairs (float4 per entry)
   int64_t tw_off = 0;     // offset of exp(-2 pi i k / nmax2), k < nmax2 / 2
   int nmax2 = 1;          // largest power-of-two transform size
   int max_n = 1;

@@ -10,78 +10,25 @@
 //     terms) is added to a hi accumulator with TwoSum, and the rounding errors
 //     of both go to a lo accumulator (the compensated dot product "Dot2" of
 //     Ogita, Rump and Oishi 2005), renormalised once at the end.
-// Inputs and outputs keep the FP64 layouts of the FP64 path (coefficients
-// double2, ring spectra double2, partial sums double), so only this stage
-// changes; the ring FFTs run in FP64.
+// Coefficients and adjoint outputs keep the FP64 layout (double2); the ring spectra
+// between this stage and the ring FFTs are double-float pairs (df2, 16 bytes like
+// double2), which the double-float ring FFT (ringfft.cu) reads and writes directly,
+// so no FP64 conversion sits between the two stages.
 #include <climits>
 
 #include "common.h"
+#include "dfloat.h"
 
 namespace cmbws {
 
 namespace {
 
-struct df {
-  float h, l;
-};
-
-__device__ __forceinline__ df two_sum(float a, float b) {
-  const float s = a + b;
-  const float bb = s - a;
-  const float e = (a - (s - bb)) + (b - bb);
-  return {s, e};
-}
-__device__ __forceinline__ df quick_two_sum(float a, float b) {
-  const float s = a + b;
-  return {s, b - (s - a)};
-}
-__device__ __forceinline__ df df_from(double v) {
-  const float h = (float)v;
-  return {h, (float)(v - (double)h)};
-}
-__device__ __forceinline__ double df_to(df a) { return (double)a.h + (double)a.l; }
-__device__ __forceinline__ df df_mul(df a, df b) {
-  const float p = a.h * b.h;
-  float e = fmaf(a.h, b.h, -p);
-  e = fmaf(a.h, b.l, e);
-  e = fmaf(a.l, b.h, e);
-  return quick_two_sum(p, e);
-}
-__device__ __forceinline__ df df_sub(df a, df b) {
-  const df s = two_sum(a.h, -b.h);
-  return quick_two_sum(s.h, s.l + (a.l - b.l));
-}
-// a * b - c
-__device__ __forceinline__ df df_fms(df a, df b, df c) {
-  const float p = a.h * b.h;
-  float e = fmaf(a.h, b.h, -p);
-  e = fmaf(a.h, b.l, e);
-  e = fmaf(a.l, b.h, e);
-  const df s = two_sum(p, -c.h);
-  return quick_two_sum(s.h, s.l + (e - c.l));
-}
-// compensated accumulation acc_h + acc_l += a * b
-__device__ __forceinline__ void dot2_acc(float& acc_h, float& acc_l, df a, df b) {
-  const float p = a.h * b.h;
-  float e = fmaf(a.h, b.h, -p);
-  e = fmaf(a.h, b.l, e);
-  e = fmaf(a.l, b.h, e);
-  const df s = two_sum(acc_h, p);
-  acc_h = s.h;
-  acc_l += s.l + e;
-}
-
-__device__ __forceinline__ df df_recur(df A, df y, df m1, df m2) {
-  const df ax = df_sub(A, df_mul(A, y));
-  return df_fms(ax, m1, m2);
-}
-
 template <int NM, int R, int NT, int CH>
 __global__ void __launch_bounds__(NT)
-k_leg_synth_df(const double2* __restrict__ alm, int64_t alm_stride, const double* __restrict__ Acoef,
+k_leg_synth_df(const double2* __restrict__ alm, int64_t alm_stride, const float2* __restrict__ Acoef,
                const int* __restrict__ ls_tab, const double2* __restrict__ st,
                const double* __restrict__ yr, const int2* __restrict__ pring,
-               double2* __restrict__ F, int64_t F_stride, int L, int npair) {
+               df2* __restrict__ F, int64_t F_stride, int L, int npair) {
   __shared__ __align__(16) float2 sA[CH];
   __shared__ __align__(16) float4 sa[NM][CH];
   __shared__ int s_lo;
@@ -126,8 +73,7 @@ k_leg_synth_df(const double2* __restrict__ alm, int64_t alm_stride, const double
     for (int j = threadIdx.x; j < CH; j += NT) {
       const int l = c0 + j;
       const bool ok = l <= L;
-      const df a = df_from(ok ? Acoef[lmo + l] : 0.0);
-      sA[j] = make_float2(a.h, a.l);
+      sA[j] = ok ? Acoef[lmo + l] : make_float2(0.f, 0.f);
 #pragma unroll
       for (int k = 0; k < NM; ++k) {
         double2 v = make_double2(0.0, 0.0);
@@ -185,12 +131,10 @@ k_leg_synth_df(const double2* __restrict__ alm, int64_t alm_stride, const double
     const int2 rr = pring[p];
 #pragma unroll
     for (int k = 0; k < NM; ++k) {
-      const double er = (double)eh[i][k][0] + (double)el[i][k][0];
-      const double ei = (double)eh[i][k][1] + (double)el[i][k][1];
-      const double orr = (double)oh[i][k][0] + (double)ol[i][k][0];
-      const double oi = (double)oh[i][k][1] + (double)ol[i][k][1];
-      F[k * F_stride + (int64_t)rr.x * (L + 1) + m] = make_double2(er + orr, ei + oi);
-      if (rr.y >= 0) F[k * F_stride + (int64_t)rr.y * (L + 1) + m] = make_double2(er - orr, ei - oi);
+      const df er{eh[i][k][0], el[i][k][0]}, ei{eh[i][k][1], el[i][k][1]};
+      const df orr{oh[i][k][0], ol[i][k][0]}, oi{oh[i][k][1], ol[i][k][1]};
+      F[k * F_stride + (int64_t)rr.x * (L + 1) + m] = df2{er + orr, ei + oi};
+      if (rr.y >= 0) F[k * F_stride + (int64_t)rr.y * (L + 1) + m] = df2{er - orr, ei - oi};
     }
   }
 }
@@ -198,7 +142,7 @@ k_leg_synth_df(const double2* __restrict__ alm, int64_t alm_stride, const double
 // E/O parts of every (pair, m) as double-float pairs: eo[(m * npair + p) * 2P + q],
 // q < P even-l parts (north + south), q >= P odd-l parts (north - south).
 template <int NM>
-__global__ void k_adj_eo_df(const double2* __restrict__ F, int64_t F_stride,
+__global__ void k_adj_eo_df(const df2* __restrict__ F, int64_t F_stride,
                             const int2* __restrict__ pring, float2* __restrict__ eo, int L, int npair) {
   constexpr int P = 2 * NM;
   const int m = blockIdx.y;
@@ -208,12 +152,11 @@ __global__ void k_adj_eo_df(const double2* __restrict__ F, int64_t F_stride,
   float2* e = eo + ((int64_t)m * npair + p) * 2 * P;
 #pragma unroll
   for (int k = 0; k < NM; ++k) {
-    const double2 gn = F[k * F_stride + (int64_t)rr.x * (L + 1) + m];
-    double2 gs = make_double2(0.0, 0.0);
+    const df2 gn = F[k * F_stride + (int64_t)rr.x * (L + 1) + m];
+    df2 gs{df(0.f, 0.f), df(0.f, 0.f)};
     if (rr.y >= 0) gs = F[k * F_stride + (int64_t)rr.y * (L + 1) + m];
-    const df er = df_from(gn.x + gs.x), ei = df_from(gn.y + gs.y);
-    const df orr = df_from(rr.y >= 0 ? gn.x - gs.x : gn.x);
-    const df oi = df_from(rr.y >= 0 ? gn.y - gs.y : gn.y);
+    const df er = gn.x + gs.x, ei = gn.y + gs.y;
+    const df orr = gn.x - gs.x, oi = gn.y - gs.y;
     e[2 * k] = make_float2(er.h, er.l);
     e[2 * k + 1] = make_float2(ei.h, ei.l);
     e[P + 2 * k] = make_float2(orr.h, orr.l);
@@ -356,8 +299,8 @@ int launch_synth_df(const Grid& g, const void* alm, int64_t as, void* F, int64_t
   dim3 grd((g.npair + kSNT * kSR - 1) / (kSNT * kSR), L + 1);
   ProfScope ps(PROF_LEG_SYNTH, s, 2, 4.0 * g.npair * (double)nlm_of(L) * (NM + 1));
   k_leg_synth_df<NM, kSR, kSNT, kSCH><<<grd, kSNT, 0, s>>>(
-      (const double2*)alm, as, g.A64.as<double>(), g.ls.as<int>(), g.st64.as<double2>(),
-      g.y64.as<double>(), g.pair_ring.as<int2>(), (double2*)F, fs, L, g.npair);
+      (const double2*)alm, as, g.A2f.as<float2>(), g.ls.as<int>(), g.st64.as<double2>(),
+      g.y64.as<double>(), g.pair_ring.as<int2>(), (df2*)F, fs, L, g.npair);
   CMBWS_LAUNCH_CHECK();
   return CMBWS_OK;
 }
@@ -372,7 +315,7 @@ int launch_adj_ck_df(const Grid& g, const void* F, int64_t fs, void* eo_buf, dou
   {
     dim3 grd((g.npair + 127) / 128, L + 1);
     ProfScope ps(PROF_LEG_RED, s, 2);
-    k_adj_eo_df<NM><<<grd, 128, 0, s>>>((const double2*)F, fs, g.pair_ring.as<int2>(), eo, L, g.npair);
+    k_adj_eo_df<NM><<<grd, 128, 0, s>>>((const df2*)F, fs, g.pair_ring.as<int2>(), eo, L, g.npair);
     CMBWS_LAUNCH_CHECK();
   }
   const int maxck = (L + kChunkDf) / kChunkDf;

@@ -17,7 +17,15 @@
 // >= 2n - 1) for every other n (GL rings of 2L+1 pixels, most polar rings).
 // The fused mode goes synthesis -> pixel multiply -> analysis without the
 // pixel map leaving shared memory.
+//
+// Arithmetic: FP32, FP64, or double-float (df, CMBWS_FP32X2: FP64-accurate on the
+// FP32 pipe, whose rate is 61 times the FP64 one on GB300).  The double-float
+// transform reads and writes double-float ring spectra (the layout of the
+// double-float Legendre stage), so FP64 conversions happen only at the pixels.
+#include <type_traits>
+
 #include "common.h"
+#include "dfloat.h"
 
 namespace cmbws {
 
@@ -26,6 +34,10 @@ namespace {
 template <typename T> struct V2;
 template <> struct V2<double> { using t = double2; };
 template <> struct V2<float> { using t = float2; };
+template <> struct V2<df> { using t = df2; };
+// storage type of pixel factors and ring weights
+template <typename T> struct PixT { using t = T; };
+template <> struct PixT<df> { using t = double; };
 
 template <typename T2>
 __device__ __forceinline__ T2 cmul(T2 a, T2 b) {
@@ -39,9 +51,6 @@ __device__ __forceinline__ T2 cconj(T2 a) {
   a.y = -a.y;
   return a;
 }
-
-__device__ __forceinline__ void sincospi_t(double x, double* s, double* c) { sincospi(x, s, c); }
-__device__ __forceinline__ void sincospi_t(float x, float* s, float* c) { sincospif(x, s, c); }
 
 // In-place power-of-two transform of size N (>= 1) in shared memory, decimation in
 // time after a bit-reversal permutation; two radix-2 stages per pass (each thread owns
@@ -161,15 +170,16 @@ __device__ void dft_inverse(T2* buf, const FftPlan& P, const T2* __restrict__ ta
 template <typename T, int MODE>
 __global__ void __launch_bounds__(256)
 k_ringfft(typename V2<T>::t* __restrict__ F, int64_t F_stride, double* __restrict__ map_out,
-          const double* __restrict__ map_in, int64_t npix, const T* __restrict__ ring_w,
-          PixPtrs<T> pix, const FftPlan* __restrict__ plans, const int* __restrict__ pair_plan,
+          const double* __restrict__ map_in, int64_t npix,
+          const typename PixT<T>::t* __restrict__ ring_w, PixPtrs<typename PixT<T>::t> pix,
+          const FftPlan* __restrict__ plans, const int* __restrict__ pair_plan,
           const int2* __restrict__ pring, const int* __restrict__ pphase,
           const int64_t* __restrict__ roff, const typename V2<T>::t* __restrict__ tab,
           int64_t tw_off, int nmax, int L) {
   using T2 = typename V2<T>::t;
+  using TP = typename PixT<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T2* buf = reinterpret_cast<T2*>(smem_raw);
-  T2* ptab = buf + nmax;  // exp(i pi k / n), k < n (shifted rings only)
 
   const int p = blockIdx.x;
   const int k = blockIdx.y;
@@ -185,18 +195,8 @@ k_ringfft(typename V2<T>::t* __restrict__ F, int64_t F_stride, double* __restric
   const T rs2 = T(0.70710678118654752440);  // 1/sqrt(2)
   const T sq2 = T(1.41421356237309504880);
   // Shifted rings (phi0 = pi / n): exp(i m phi0) = (-1)^(m div n) exp(i pi (m mod n) / n),
-  // so one table of n phases serves every alias of every frequency.
-  if (ph) {
-    for (int kk = threadIdx.x; kk < n; kk += blockDim.x) {
-      T s, c;
-      sincospi_t(T(kk) / T(n), &s, &c);
-      T2 e;
-      e.x = c;
-      e.y = s;
-      ptab[kk] = e;
-    }
-    __syncthreads();
-  }
+  // so the plan's table of n phases exp(i pi k / n) serves every alias of every frequency.
+  const T2* __restrict__ ptab = tab + P.phase;
 
   if (MODE == MODE_SYNTH || MODE == MODE_FUSED) {
     // fold the two-sided spectrum modulo n:
@@ -204,19 +204,19 @@ k_ringfft(typename V2<T>::t* __restrict__ F, int64_t F_stride, double* __restric
     //                                      + sum_{m = jn - k} s_j (Fc + i Fs)_m),
     // P_k = exp(i pi k / n), s_j = (-1)^j on shifted rings (P_k = s_j = 1 otherwise)
     for (int kk = threadIdx.x; kk < n; kk += blockDim.x) {
-      T anx = 0, any = 0, asx = 0, asy = 0;
+      T anx = T(0), any = T(0), asx = T(0), asy = T(0);
       // +m frequencies, m = kk + j n >= 1: sum of s_j (Fc, -Fs)
       {
         int j = kk == 0 ? 1 : 0;
         for (int m = kk + j * n; m <= L; m += n, ++j) {
-          const T sg = (ph && (j & 1)) ? T(-1) : T(1);
+          const bool neg = ph && (j & 1);
           const T2 a = FN[m];
-          anx += sg * a.x;
-          any -= sg * a.y;
+          anx += neg ? -a.x : a.x;
+          any -= neg ? -a.y : a.y;
           if (has_s) {
             const T2 b = FS[m];
-            asx += sg * b.x;
-            asy -= sg * b.y;
+            asx += neg ? -b.x : b.x;
+            asy -= neg ? -b.y : b.y;
           }
         }
       }
@@ -224,18 +224,18 @@ k_ringfft(typename V2<T>::t* __restrict__ F, int64_t F_stride, double* __restric
       {
         int j = 1;
         for (int m = n - kk; m <= L; m += n, ++j) {
-          const T sg = (ph && (j & 1)) ? T(-1) : T(1);
+          const bool neg = ph && (j & 1);
           const T2 a = FN[m];
-          anx += sg * a.x;
-          any += sg * a.y;
+          anx += neg ? -a.x : a.x;
+          any += neg ? -a.y : a.y;
           if (has_s) {
             const T2 b = FS[m];
-            asx += sg * b.x;
-            asy += sg * b.y;
+            asx += neg ? -b.x : b.x;
+            asy += neg ? -b.y : b.y;
           }
         }
       }
-      T cp = 1, sp = 0;
+      T cp = T(1), sp = T(0);
       if (ph) {
         const T2 e = ptab[kk];
         cp = e.x;
@@ -265,23 +265,23 @@ k_ringfft(typename V2<T>::t* __restrict__ F, int64_t F_stride, double* __restric
       return;
     }
     // pixel multiply in place
-    const T* pk = pix.p[k];
+    const TP* pk = pix.p[k];
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
       T2 z = buf[j];
-      z.x *= pk[offN + j];
-      z.y = has_s ? z.y * pk[offS + j] : T(0);
+      z.x *= T(pk[offN + j]);
+      z.y = has_s ? z.y * T(pk[offS + j]) : T(0);
       buf[j] = z;
     }
     __syncthreads();
   } else {
     // analysis: load (optionally weighted) pixels
     const double* mi = map_in + k * npix;
-    const T wN = ring_w ? ring_w[rr.x] : T(1);
-    const T wS = (ring_w && has_s) ? ring_w[rr.y] : T(1);
+    const T wN = ring_w ? T(ring_w[rr.x]) : T(1);
+    const T wS = (ring_w && has_s) ? T(ring_w[rr.y]) : T(1);
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
       T2 z;
-      z.x = (T)mi[offN + j] * wN;
-      z.y = has_s ? (T)mi[offS + j] * wS : T(0);
+      z.x = T(mi[offN + j]) * wN;
+      z.y = has_s ? T(mi[offS + j]) * wS : T(0);
       buf[j] = z;
     }
     __syncthreads();
@@ -297,12 +297,12 @@ k_ringfft(typename V2<T>::t* __restrict__ F, int64_t F_stride, double* __restric
     const T2 zc = cconj(buf[kc]);
     T xnx = T(0.5) * (zk.x + zc.x), xny = T(0.5) * (zk.y + zc.y);
     T xsx = T(0.5) * (zk.y - zc.y), xsy = T(-0.5) * (zk.x - zc.x);
-    T c = 1, s = 0;
+    T c = T(1), s = T(0);
     if (ph) {
       const T2 e = ptab[kk];
-      const T sg = ((m / n) & 1) ? T(-1) : T(1);
-      c = sg * e.x;
-      s = sg * e.y;
+      const bool neg = ((m / n) & 1) != 0;
+      c = neg ? -e.x : e.x;
+      s = neg ? -e.y : e.y;
     }
     const T cm = m == 0 ? T(1) : sq2;
     // G = (c - i s) X
@@ -324,8 +324,7 @@ k_ringfft(typename V2<T>::t* __restrict__ F, int64_t F_stride, double* __restric
 
 template <typename T>
 size_t smem_bytes(const Grid& g) {
-  // transform buffer (nmax2) + phase table (max ring length)
-  return (size_t)(g.nmax2 + g.max_n) * sizeof(typename V2<T>::t);
+  return (size_t)g.nmax2 * sizeof(typename V2<T>::t);  // the transform buffer
 }
 
 template <typename T, int MODE>
@@ -340,18 +339,19 @@ int launch(const Grid& g, int nmaps, void* F, double* map_out, const double* map
   }
   auto kern = k_ringfft<T, MODE>;
   CMBWS_TRY(ensure_dyn_smem((const void*)kern, sm));
+  using TP = typename PixT<T>::t;
   const int64_t fs = (int64_t)g.nring * (g.lmax + 1);
-  const bool dbl = sizeof(T) == 8;
-  const T* rw = nullptr;
-  if (MODE == MODE_ANALYSIS && weighted) rw = dbl ? (const T*)g.ring_w64.p : (const T*)g.ring_w32.p;
-  const T2* tab = dbl ? (const T2*)g.fft64.p : (const T2*)g.fft32.p;
+  constexpr bool f32 = std::is_same<T, float>::value, f64 = std::is_same<T, double>::value;
+  const TP* rw = nullptr;
+  if (MODE == MODE_ANALYSIS && weighted) rw = f32 ? (const TP*)g.ring_w32.p : (const TP*)g.ring_w64.p;
+  const T2* tab = f32 ? (const T2*)g.fft32.p : f64 ? (const T2*)g.fft64.p : (const T2*)g.fftdf.p;
   for (int k0 = 0; k0 < nmaps; k0 += kMaxPix) {
     const int nm = nmaps - k0 < kMaxPix ? nmaps - k0 : kMaxPix;
-    PixPtrs<T> pp{};
+    PixPtrs<TP> pp{};
     if (MODE == MODE_FUSED)
-      for (int i = 0; i < nm; ++i) pp.p[i] = (const T*)pix[k0 + i];
+      for (int i = 0; i < nm; ++i) pp.p[i] = (const TP*)pix[k0 + i];
     dim3 grd(g.npair, nm);
-    ProfScope ps(PROF_FFT, s, dbl ? 1 : 0);
+    ProfScope ps(PROF_FFT, s, f32 ? 0 : f64 ? 1 : 2);
     kern<<<grd, 256, sm, s>>>((T2*)F + k0 * fs, fs, map_out ? map_out + k0 * g.npix : nullptr,
                               map_in ? map_in + k0 * g.npix : nullptr, g.npix, rw, pp,
                               g.plans_d.as<FftPlan>(), g.pair_plan.as<int>(),
@@ -369,14 +369,19 @@ int ringfft_smem_ok(const Grid& g, int prec) {
   return sm <= 227 * 1024;
 }
 
+// Spectra F: float2 (FP32 modes), double2 (FP64) or double-float pairs (FP32X2).
+// Pixel factors: float (FP32 modes) or double.
 int ringfft_synth(const Grid& g, int prec, int nmaps, const void* F, double* map, cudaStream_t s) {
-  if (!is_f32(prec))
-    return launch<double, MODE_SYNTH>(g, nmaps, const_cast<void*>(F), map, nullptr, 0, nullptr, s);
-  return launch<float, MODE_SYNTH>(g, nmaps, const_cast<void*>(F), map, nullptr, 0, nullptr, s);
+  void* f = const_cast<void*>(F);
+  if (prec == CMBWS_FP32X2) return launch<df, MODE_SYNTH>(g, nmaps, f, map, nullptr, 0, nullptr, s);
+  if (!is_f32(prec)) return launch<double, MODE_SYNTH>(g, nmaps, f, map, nullptr, 0, nullptr, s);
+  return launch<float, MODE_SYNTH>(g, nmaps, f, map, nullptr, 0, nullptr, s);
 }
 
 int ringfft_analysis(const Grid& g, int prec, int nmaps, const double* map, int weighted, void* F,
                      cudaStream_t s) {
+  if (prec == CMBWS_FP32X2)
+    return launch<df, MODE_ANALYSIS>(g, nmaps, F, nullptr, map, weighted, nullptr, s);
   if (!is_f32(prec))
     return launch<double, MODE_ANALYSIS>(g, nmaps, F, nullptr, map, weighted, nullptr, s);
   return launch<float, MODE_ANALYSIS>(g, nmaps, F, nullptr, map, weighted, nullptr, s);
@@ -384,8 +389,8 @@ int ringfft_analysis(const Grid& g, int prec, int nmaps, const double* map, int 
 
 int ringfft_fused(const Grid& g, int prec, int nmaps, void* F, const void* const* pix,
                   cudaStream_t s) {
-  if (!is_f32(prec))
-    return launch<double, MODE_FUSED>(g, nmaps, F, nullptr, nullptr, 0, pix, s);
+  if (prec == CMBWS_FP32X2) return launch<df, MODE_FUSED>(g, nmaps, F, nullptr, nullptr, 0, pix, s);
+  if (!is_f32(prec)) return launch<double, MODE_FUSED>(g, nmaps, F, nullptr, nullptr, 0, pix, s);
   return launch<float, MODE_FUSED>(g, nmaps, F, nullptr, nullptr, 0, pix, s);
 }
 

@@ -376,6 +376,11 @@ int grid_build_tables(Grid& g) {
       } else {
         P.filt = 0;
       }
+      P.phase = (int64_t)tab.size();
+      for (int k = 0; k < n; ++k) {
+        const double ang = M_PI * (double)k / n;
+        tab.emplace_back(std::cos(ang), std::sin(ang));
+      }
       g.plans.push_back(P);
       if (P.n2 > g.nmax2) g.nmax2 = P.n2;
       if (n > g.max_n) g.max_n = n;
@@ -392,8 +397,17 @@ int grid_build_tables(Grid& g) {
       tf[2 * i] = (float)tab[i].real();
       tf[2 * i + 1] = (float)tab[i].imag();
     }
+    std::vector<float> td(4 * tab.size());  // (re hi, re lo, im hi, im lo)
+    for (size_t i = 0; i < tab.size(); ++i) {
+      const double re = tab[i].real(), im = tab[i].imag();
+      td[4 * i] = (float)re;
+      td[4 * i + 1] = (float)(re - (double)(float)re);
+      td[4 * i + 2] = (float)im;
+      td[4 * i + 3] = (float)(im - (double)(float)im);
+    }
     CMBWS_TRY(g.fft64.upload(tab.data(), tab.size() * 16));
     CMBWS_TRY(g.fft32.upload(tf.data(), tf.size() * 4));
+    CMBWS_TRY(g.fftdf.upload(td.data(), td.size() * 4));
     CMBWS_TRY(g.plans_d.upload(g.plans.data(), g.plans.size() * sizeof(FftPlan)));
     CMBWS_TRY(g.pair_plan.upload(pplan.data(), pplan.size() * 4));
   }
