@@ -128,11 +128,13 @@ def barrier(world):
 
 
 def max_over_ranks(v, world):
+    """Maximum of a per-rank value over all ranks (NCCL on GPUs, gloo on the host)."""
     if world == 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
