@@ -134,6 +134,12 @@ struct Grid {
   DevMem st64, st32;      // {mu_ls, mu_ls+1} [L+1][npair]
   DevMem ck32;            // FP32 {mu_l0, mu_l0+1} at every chunk start l0 = m + kChunk c
   DevMem ck_base;         // int64 [L+1]: offset of m's block [pair][chunk] in ck32
+  // warp tasks of the checkpointed adjoints: int2 {m, first chunk} per 32 consecutive
+  // chunks of one m, m ascending (FP32 chunking; the double-float list is built with ck64)
+  DevMem wt32;
+  int nwt32 = 0;
+  mutable DevMem wtdf;
+  mutable int nwtdf = 0;
   mutable DevMem ck64;    // double-float {mu_l0, mu_l0+1} (float4) every kChunkDf; built on first use
   mutable DevMem ck64_base;  // int64 [L+1]: offset of m's block [pair][chunk] in ck64
   mutable DevMem y2f;     // y as a double-float pair (float2), built with ck64
@@ -171,6 +177,9 @@ int ringfft_analysis(const Grid& g, int prec, int nmaps, const double* map, int 
 int ringfft_fused(const Grid& g, int prec, int nmaps, void* F, const void* const* pix,
                   cudaStream_t s);
 int ringfft_smem_ok(const Grid& g, int prec);
+
+// warp-task list {m, first chunk} for chunks of `chunk` values of l (adjoint scheduling)
+std::vector<int2> adjoint_warp_tasks(int L, int chunk);
 
 // ---- grid setup (setup.cu) ----
 int grid_build_tables(Grid& g);

@@ -354,17 +354,21 @@ __global__ void __launch_bounds__(NT)
 k_leg_adj_ck(const float* __restrict__ eo, const float* __restrict__ Acoef,
              const int* __restrict__ ls_tab, const float2* __restrict__ st,
              const float* __restrict__ yr, const float2* __restrict__ ck,
-             const int64_t* __restrict__ ck_base, const double* __restrict__ c64,
-             double2* __restrict__ out, int64_t nlm, int L, int npair) {
+             const int64_t* __restrict__ ck_base, const int2* __restrict__ tasks, int ntask,
+             const double* __restrict__ c64, double2* __restrict__ out, int64_t nlm, int L,
+             int npair) {
   constexpr int P = 2 * NM;
   constexpr int K = kChunk;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   AdjCkWarp<NM, PT>& S = reinterpret_cast<AdjCkWarp<NM, PT>*>(smem_raw)[warp];
-  const int m = blockIdx.y;
+  // every warp takes one task (32 consecutive chunks of one m); warps of a CTA are independent
+  const int task = blockIdx.x * (NT / 32) + warp;
+  if (task >= ntask) return;  // warp-uniform: no block barrier below
+  const int2 tk = tasks[task];
+  const int m = tk.x;
   const int nck = (L - m + K) / K;
-  const int cw = blockIdx.x * NT + warp * 32;  // first chunk of this warp
-  if (cw >= nck) return;                       // warp-uniform: no block barrier below
+  const int cw = tk.y;  // first chunk of this warp
   const int c = cw + lane;
   const bool valid = c < nck;
   const int l0 = m + K * c;
@@ -531,15 +535,15 @@ int launch_adj_ck(const Grid& g, const void* F, int64_t F_stride, void* part, do
                                      g.npair);
     CMBWS_LAUNCH_CHECK();
   }
-  const int maxck = (L + kChunk) / kChunk;
-  dim3 grd((maxck + NT - 1) / NT, L + 1);
+  dim3 grd((g.nwt32 + NT / 32 - 1) / (NT / 32));
   constexpr size_t sm = sizeof(AdjCkWarp<NM, PT>) * (NT / 32);
   auto kern = k_leg_adj_ck<NM, NT, PT>;
   CMBWS_TRY(ensure_dyn_smem((const void*)kern, sm));
   ProfScope ps(PROF_LEG_ADJ, s, 0, 4.0 * g.npair * (double)nlm * (NM + 1));
   kern<<<grd, NT, sm, s>>>(eo, g.A32.as<float>(), g.ls.as<int>(), g.st32.as<float2>(),
                            g.y32.as<float>(), g.ck32.as<float2>(), g.ck_base.as<int64_t>(),
-                           g.c64.as<double>(), (double2*)out, nlm, L, g.npair);
+                           g.wt32.as<int2>(), g.nwt32, g.c64.as<double>(), (double2*)out, nlm, L,
+                           g.npair);
   CMBWS_LAUNCH_CHECK();
   return CMBWS_OK;
 }

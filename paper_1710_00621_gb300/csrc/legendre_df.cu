@@ -184,17 +184,21 @@ __global__ void __launch_bounds__(NT)
 k_leg_adj_ck_df(const float2* __restrict__ eo, const float2* __restrict__ Acoef,
                 const int* __restrict__ ls_tab, const double2* __restrict__ st,
                 const float2* __restrict__ yr, const float4* __restrict__ ck,
-                const int64_t* __restrict__ ck_base, const double* __restrict__ c64,
-                double2* __restrict__ out, int64_t nlm, int L, int npair) {
+                const int64_t* __restrict__ ck_base, const int2* __restrict__ tasks, int ntask,
+                const double* __restrict__ c64, double2* __restrict__ out, int64_t nlm, int L,
+                int npair) {
   constexpr int P = 2 * NM;
   constexpr int K = kChunkDf;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   AdjCkDfWarp<NM, PT>& S = reinterpret_cast<AdjCkDfWarp<NM, PT>*>(smem_raw)[warp];
-  const int m = blockIdx.y;
+  // every warp takes one task (32 consecutive chunks of one m); warps of a CTA are independent
+  const int task = blockIdx.x * (NT / 32) + warp;
+  if (task >= ntask) return;  // warp-uniform: no block barrier below
+  const int2 tk = tasks[task];
+  const int m = tk.x;
   const int nck = (L - m + K) / K;
-  const int cw = blockIdx.x * NT + warp * 32;  // first chunk of this warp
-  if (cw >= nck) return;                       // warp-uniform: no block barrier below
+  const int cw = tk.y;  // first chunk of this warp
   const int c = cw + lane;
   const bool valid = c < nck;
   const int l0 = m + K * c;
@@ -318,15 +322,15 @@ int launch_adj_ck_df(const Grid& g, const void* F, int64_t fs, void* eo_buf, dou
     k_adj_eo_df<NM><<<grd, 128, 0, s>>>((const df2*)F, fs, g.pair_ring.as<int2>(), eo, L, g.npair);
     CMBWS_LAUNCH_CHECK();
   }
-  const int maxck = (L + kChunkDf) / kChunkDf;
-  dim3 grd((maxck + kANT - 1) / kANT, L + 1);
+  dim3 grd((g.nwtdf + kANT / 32 - 1) / (kANT / 32));
   constexpr size_t sm = sizeof(AdjCkDfWarp<NM, kAPT>) * (kANT / 32);
   auto kern = k_leg_adj_ck_df<NM, kANT, kAPT>;
   CMBWS_TRY(ensure_dyn_smem((const void*)kern, sm));
   ProfScope ps(PROF_LEG_ADJ, s, 2, 4.0 * g.npair * (double)nlm * (NM + 1));
   kern<<<grd, kANT, sm, s>>>(eo, g.A2f.as<float2>(), g.ls.as<int>(), g.st64.as<double2>(),
                              g.y2f.as<float2>(), g.ck64.as<float4>(), g.ck64_base.as<int64_t>(),
-                             g.c64.as<double>(), (double2*)out, nlm, L, g.npair);
+                             g.wtdf.as<int2>(), g.nwtdf, g.c64.as<double>(), (double2*)out, nlm, L,
+                             g.npair);
   CMBWS_LAUNCH_CHECK();
   return CMBWS_OK;
 }

@@ -335,6 +335,11 @@ int grid_build_tables(Grid& g) {
       tot += (int64_t)g.npair * ((L - m + kChunk) / kChunk);
     }
     CMBWS_TRY(g.ck_base.upload(cb.data(), (L + 1) * 8));
+    {
+      const std::vector<int2> wt = adjoint_warp_tasks(L, kChunk);
+      CMBWS_TRY(g.wt32.upload(wt.data(), wt.size() * sizeof(int2)));
+      g.nwt32 = (int)wt.size();
+    }
     CMBWS_TRY(g.ck32.alloc((size_t)tot * 8));
     k_start<<<grd, 128>>>(g.y64.as<double>(), g.A64.as<double>(), L, g.npair, d_sv.as<double>(),
                           d_sk.as<int>(), g.ls.as<int>(), g.st64.as<double2>(), g.st32.as<float2>(),
@@ -421,6 +426,15 @@ __global__ void k_to_df(const double* __restrict__ v, float2* __restrict__ o, in
   o[i] = make_float2(h, (float)(v[i] - (double)h));
 }
 
+std::vector<int2> adjoint_warp_tasks(int L, int chunk) {
+  std::vector<int2> t;
+  for (int m = 0; m <= L; ++m) {
+    const int nck = (L - m + chunk) / chunk;
+    for (int c = 0; c < nck; c += 32) t.push_back(make_int2(m, c));
+  }
+  return t;
+}
+
 int grid_ensure_ck64(const Grid& gc) {
   std::lock_guard<std::mutex> lk(gc.ck64_mu);
   if (gc.ck64.p) return CMBWS_OK;
@@ -459,6 +473,13 @@ int grid_ensure_ck64(const Grid& gc) {
                         g.ck_base.as<int64_t>(), nullptr, cbd.as<int64_t>(), ck.as<float4>());
   CMBWS_LAUNCH_CHECK();
   CMBWS_CUDA(cudaDeviceSynchronize());
+  {
+    const std::vector<int2> wt = adjoint_warp_tasks(L, kChunkDf);
+    DevMem w;
+    CMBWS_TRY(w.upload(wt.data(), wt.size() * sizeof(int2)));
+    g.wtdf = std::move(w);
+    g.nwtdf = (int)wt.size();
+  }
   g.y2f = std::move(y2);
   g.ck64_base = std::move(cbd);
   g.ck64 = std::move(ck);
