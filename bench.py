@@ -255,6 +255,12 @@ FP32_FLOPS_PER_ELEM = {("legendre_synth", "fp32"): 16.0, ("legendre_adjoint", "f
                        ("legendre_adjoint", "fp32x2"): 0.5 * 39.0 + 6 * 15.0}
 
 
+# DRAM bytes (read + write) per element from one ncu capture of the kernel as it stands,
+# on the Nside 512, L = 1535, 3-map case (profiles/k_leg_adj_ck_df_healpix512_l1535_3maps.md):
+# 5.50 GB / 1.209e9 elements; the checkpoint table dominates, so it scales with the elements.
+DRAM_BYTES_PER_ELEM = {("legendre_adjoint", "fp32x2"): 4.55}
+
+
 def roofline(prof):
     """Dominant kernel (by summed time) among the Legendre stages, with its achieved rate.
 
@@ -275,9 +281,11 @@ def roofline(prof):
     if per is None:
         return None
     achieved = elems * per / (ms * 1e-3) / 1e12
+    bpe = DRAM_BYTES_PER_ELEM.get((stage, prec))
+    traffic = round(bpe * elems / n) if bpe else None
     out = {"bound": "alu", "kernel": f"{stage}_{prec}", "achieved": round(achieved, 3),
            "peak": round(FP32_PEAK_TFLOPS, 2), "unit": "TFLOP/s",
-           "frac": round(achieved / FP32_PEAK_TFLOPS, 4), "traffic": None, "launches": n,
+           "frac": round(achieved / FP32_PEAK_TFLOPS, 4), "traffic": traffic, "launches": n,
            "avg_launch_ms": round(ms / n, 4),
            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (of derived)",
            "flops_per_element": per}
