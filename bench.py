@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--no-fp64-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-precision", action="store_true",
+                    help="skip the per-precision synthesis time / error report")
     ap.add_argument("--inner-tol", type=float, default=1e-3,
                     help="relative residual reduction per refinement pass (FP32 solves)")
     ap.add_argument("--with-batched", type=int, default=0, metavar="NPROB",
@@ -244,6 +246,41 @@ def batched_measure(nprob, tol, fmax=0.0):
                          + "FP32 transforms + FP32X2 certification, 8 worker streams")}
 
 
+def precision_report(nside=1024, nmaps=3, reps=3):
+    """Synthesis of one full-size band grid (HEALPix Nside 1024, L = 3071, three maps) in every
+    transform precision: time per call (CUDA events) and the max-relative difference from the
+    FP64 synthesis of the same coefficients (a 1/(l+1) spectrum)."""
+    import torch
+    import paper_1710_00621_gb300 as cw
+    L = 3 * nside - 1
+    g = cw.cmbws_plan_grid(cw.CMBWS_GRID_HEALPIX, nside, L)
+    ell = skygen.ell_of_index(L)
+    rng = np.random.default_rng(11)
+    a = torch.as_tensor(rng.standard_normal((nmaps, ell.size)) / (1.0 + ell), device="cuda")
+    out = {}
+    ref = None
+    precs = [("fp64", cw.CMBWS_FP64), ("fp32x2", cw.CMBWS_FP32X2), ("fp32", cw.CMBWS_FP32),
+             ("3xtf32", cw.CMBWS_3XTF32), ("tf32", cw.CMBWS_TF32)]
+    for name, p in precs:
+        m = torch.empty((nmaps, g.npix), dtype=torch.float64, device="cuda")
+        cw.cmbws_sht_synth(g, p, a, m, nmaps)  # warm-up (lazy tables)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            cw.cmbws_sht_synth(g, p, a, m, nmaps)
+        e1.record()
+        torch.cuda.synchronize()
+        if ref is None:
+            ref = m.clone()
+        err = float((m - ref).abs().max() / ref.abs().max())
+        out[name] = {"ms": round(e0.elapsed_time(e1) / reps, 3), "max_rel_err_vs_fp64": err}
+    out["case"] = f"synthesis, HEALPix Nside {nside}, L = {L}, {nmaps} maps, 1/(l+1) spectrum"
+    out["note"] = ("tf32 / 3xtf32: Legendre contraction on the tcgen05 tensor cores (the recurrence "
+                   "on the CUDA cores in FP32, as for fp32); fp32x2: double-float on the FP32 pipe")
+    return out
+
+
 # FP32-pipe flops per (l, m, ring pair) element with three maps per grid group (six real
 # parts): FP32 kernels 2 FMA for the recurrence + 6 for the contraction (16 flops, the SHT
 # flop count itself); double-float kernels: a double-float recurrence step costs 39 FP32
@@ -435,6 +472,7 @@ def main():
         out["iters_fp64_plain"] = r64["iters"]
 
     batched = batched_measure(args.with_batched, args.tol) if args.with_batched else None
+    precision = precision_report() if (not args.no_precision and args.scale == 1) else None
 
     if rank != 0:
         return
@@ -454,7 +492,8 @@ def main():
                                       if args.prec == "fp32" else "FP64"),
                        "l2": "inputs larger than L2, no flush",
                        "parallelism": f"replicas x{world}"},
-            "solve": out, "fp64_plain": fp64, "batched": batched, "roofline": rl, "cpu_baseline": cb, "e2e": e2e,
+            "solve": out, "fp64_plain": fp64, "batched": batched, "precision": precision,
+            "roofline": rl, "cpu_baseline": cb, "e2e": e2e,
             "gpu_launches": launches, "stages": stages, "clocks": clk}
     print(json.dumps(line))
 

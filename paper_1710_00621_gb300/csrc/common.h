@@ -87,6 +87,14 @@ struct DevMem {
   template <typename T> T* as() const { return static_cast<T*>(p); }
 };
 
+// FP32 synthesis near the poles: the rescaled recurrence mu_l = A_l x mu_{l-1} - mu_{l-2}
+// has an almost double characteristic root there (x -> 1, A_l alternating around 2 rho and
+// 2 / rho), so FP32 rounding grows like l^2 eps.  Warps holding a ring pair with
+// theta < kPolarTheta run the difference form e_l = mu_l - R_l mu_{l-1}, R_l = c_{l-1} / c_l:
+//   e_l = ((B_l - A_l y) mu_{l-1} + S_l e_{l-1},  mu_l = R_l mu_{l-1} + e_l,
+// B_l = A_l - R_l - 1 / R_{l-1}, S_l = 1 / R_{l-1}, whose increments stay small there.
+constexpr double kPolarTheta = 0.2;
+constexpr float kPolarY = 0.019933422f;  // 1 - cos(kPolarTheta): polar iff y < kPolarY
 constexpr int kChunk = 8;    // l-chunk of the checkpointed FP32 adjoint (even)
 constexpr int kChunkDf = 4;  // l-chunk of the checkpointed double-float adjoint (even)
 
@@ -129,6 +137,7 @@ struct Grid {
   // Legendre recurrence tables (device), index lm(m, l)
   DevMem A64, A32;        // A_lm of the rescaled recurrence mu_l = A_l x mu_{l-1} - mu_{l-2}
   DevMem A2f;             // A_lm as a double-float pair (float2 hi, lo) for the FP32X2 kernels
+  DevMem BRS32;           // {B, R, S}_lm (FP32) of the difference form used near the poles
   DevMem c64;             // lambda_lm = c_lm mu_lm
   DevMem ls;              // int [L+1][npair] first l (same parity as m) that is injected
   DevMem st64, st32;      // {mu_ls, mu_ls+1} [L+1][npair]

@@ -38,13 +38,16 @@ constexpr unsigned kFull = 0xffffffffu;
 template <typename T, int NM, int R, int NT, int CH>
 __global__ void __launch_bounds__(NT)
 k_leg_synth(const typename V2<T>::t* __restrict__ alm, int64_t alm_stride,
-            const T* __restrict__ Acoef, const int* __restrict__ ls_tab,
+            const T* __restrict__ Acoef, const float* __restrict__ brs,
+            const int* __restrict__ ls_tab,
             const typename V2<T>::t* __restrict__ st, const T* __restrict__ yr,
             const int2* __restrict__ pring, typename V2<T>::t* __restrict__ F, int64_t F_stride,
             int L, int npair, int nring) {
   using T2 = typename V2<T>::t;
+  constexpr bool kF32 = std::is_same<T, float>::value;
   __shared__ __align__(16) T sA[CH];
   __shared__ __align__(16) T2 sa[NM][CH];
+  __shared__ __align__(16) float sBRS[kF32 ? 3 : 1][kF32 ? CH : 1];  // difference form (FP32)
   __shared__ int s_lo;
 
   const int m = blockIdx.y;
@@ -79,6 +82,14 @@ k_leg_synth(const typename V2<T>::t* __restrict__ alm, int64_t alm_stride,
   __syncthreads();
   const int lo = s_lo;
   int nxt = mylo;  // next l at which one of this thread's pairs starts
+  // warps holding a polar ring pair run the difference form (FP32 only; warp-uniform)
+  bool polar = false;
+  if constexpr (kF32) {
+    bool mine = false;
+#pragma unroll
+    for (int i = 0; i < R; ++i) mine |= (pbase + i * NT < npair) && (float)y[i] < kPolarY;
+    polar = __any_sync(kFull, mine);
+  }
 
   for (int c0 = lo; c0 <= L; c0 += CH) {
     __syncthreads();
@@ -86,6 +97,10 @@ k_leg_synth(const typename V2<T>::t* __restrict__ alm, int64_t alm_stride,
       const int l = c0 + j;
       const bool ok = l <= L;
       sA[j] = ok ? Acoef[lmo + l] : T(0);
+      if constexpr (kF32) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) sBRS[q][j] = ok ? brs[3 * (lmo + l) + q] : 0.f;
+      }
 #pragma unroll
       for (int k = 0; k < NM; ++k) {
         T2 v;
@@ -95,6 +110,54 @@ k_leg_synth(const typename V2<T>::t* __restrict__ alm, int64_t alm_stride,
       }
     }
     __syncthreads();
+    if constexpr (kF32) {
+      if (polar) {
+        // mu2 holds e_{l-1} = mu_{l-1} - R_{l-1} mu_{l-2} in this form
+#pragma unroll 2
+        for (int j = 0; j < CH; j += 2) {
+          const int l = c0 + j;
+          const T A0 = sA[j], A1 = sA[j + 1];
+          const float B0 = sBRS[0][j], B1 = sBRS[0][j + 1], R0 = sBRS[1][j], R1 = sBRS[1][j + 1];
+          const float S0 = sBRS[2][j], S1 = sBRS[2][j + 1];
+          T ma[R], mb[R];
+#pragma unroll
+          for (int i = 0; i < R; ++i) {
+            T e = fmaf(fmaf(-A0, y[i], B0), mu1[i], S0 * mu2[i]);
+            ma[i] = fmaf(R0, mu1[i], e);
+            e = fmaf(fmaf(-A1, y[i], B1), ma[i], S1 * e);
+            mb[i] = fmaf(R1, ma[i], e);
+            mu2[i] = e;
+          }
+          if (l == nxt) {
+            int nn = INT_MAX;
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+              if (ls[i] == l) {
+                ma[i] = inj[i].x;
+                mb[i] = inj[i].y;
+                mu2[i] = fmaf(-R1, inj[i].x, inj[i].y);
+              }
+              if (ls[i] > l) nn = min(nn, ls[i]);
+            }
+            nxt = nn;
+          }
+#pragma unroll
+          for (int i = 0; i < R; ++i) mu1[i] = mb[i];
+#pragma unroll
+          for (int k = 0; k < NM; ++k) {
+            const T2 a0 = sa[k][j], a1 = sa[k][j + 1];
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+              eR[i][k] += ma[i] * a0.x;
+              eI[i][k] += ma[i] * a0.y;
+              oR[i][k] += mb[i] * a1.x;
+              oI[i][k] += mb[i] * a1.y;
+            }
+          }
+        }
+        continue;
+      }
+    }
 #pragma unroll 2
     for (int j = 0; j < CH; j += 2) {
       const int l = c0 + j;
@@ -509,8 +572,8 @@ int launch_synth(const Grid& g, const void* alm, int64_t alm_stride, void* F, in
   const T* yr = std::is_same<T, double>::value ? (const T*)g.y64.p : (const T*)g.y32.p;
   ProfScope ps(PROF_LEG_SYNTH, s, sizeof(T) == 8, 4.0 * g.npair * (double)nlm_of(L) * (NM + 1));
   k_leg_synth<T, NM, C::SR, C::SNT, C::SCH><<<grd, C::SNT, 0, s>>>(
-      (const T2*)alm, alm_stride, A, g.ls.as<int>(), st, yr, g.pair_ring.as<int2>(), (T2*)F,
-      F_stride, L, g.npair, g.nring);
+      (const T2*)alm, alm_stride, A, g.BRS32.as<float>(), g.ls.as<int>(), st, yr,
+      g.pair_ring.as<int2>(), (T2*)F, F_stride, L, g.npair, g.nring);
   CMBWS_LAUNCH_CHECK();
   return CMBWS_OK;
 }

@@ -90,8 +90,8 @@ template <int SPLIT>
 struct TcLayout {
   static constexpr int kBStage = 4 * 512;                         // one 16 x 32 TF32 tile
   static constexpr int kStage = (SPLIT ? 2 : 1) * kBStage;        // hi (+ lo) per stage
-  static constexpr int kOffA = 2 * kStage;                        // float sAc[2][32]
-  static constexpr int kOffBar = kOffA + 2 * kTcKB * 4;           // uint64_t mbar[2]
+  static constexpr int kOffA = 2 * kStage;                        // float sAc[2][4][32]: A, B, R, S
+  static constexpr int kOffBar = kOffA + 2 * 4 * kTcKB * 4;       // uint64_t mbar[2]
   static constexpr int kOffT = kOffBar + 16;                      // uint32_t tmem base, bad flag
   static constexpr int kUsed = kOffT + 16;
   // Shared memory requested per CTA: caps residency so that the CTAs of an SM never ask
@@ -109,7 +109,8 @@ __device__ __forceinline__ int b_off(int n, int k) {
 template <int NM, int SPLIT>
 __global__ void __launch_bounds__(kTcNT)
 k_leg_synth_tc(const float2* __restrict__ alm, int64_t alm_stride, const float* __restrict__ Acoef,
-               const int* __restrict__ ls_tab, const float2* __restrict__ st,
+               const float* __restrict__ brs, const int* __restrict__ ls_tab,
+               const float2* __restrict__ st,
                const float* __restrict__ yr, const int2* __restrict__ pring, float2* __restrict__ F,
                int64_t F_stride, int L, int npair) {
   using LY = TcLayout<SPLIT>;
@@ -179,12 +180,17 @@ k_leg_synth_tc(const float2* __restrict__ alm, int64_t alm_stride, const float* 
     if (jj < NM && l <= L) v = alm[jj * alm_stride + lmo + l];
     return v;
   };
+  // recurrence coefficients of a block: thread tid loads A (tid < 32) or B, R, S (the
+  // difference form near the poles) of l = lo + 32 b + tid % 32
   auto load_A = [&](int b) {
-    const int l = lo + b * kTcKB + tid;
-    return (tid < kTcKB && l <= L) ? Acoef[lmo + l] : 0.f;
+    const int l = lo + b * kTcKB + (tid & 31);
+    if (l > L) return 0.f;
+    return tid < kTcKB ? Acoef[lmo + l] : brs[3 * (lmo + l) + (tid / kTcKB - 1)];
   };
   float2 cnext = load_coef(0);
   float anext = load_A(0);
+  // warps holding a polar ring pair run the difference form (warp-uniform)
+  const bool polar = __any_sync(0xffffffffu, valid && y < kPolarY);
 
   float mu1 = 0.f, mu2 = 0.f;
   bool bad = false;
@@ -207,7 +213,7 @@ k_leg_synth_tc(const float2* __restrict__ alm, int64_t alm_stride, const float* 
               tf32_bits(cnext.y - __uint_as_float(hi));
         }
       }
-      if (tid < kTcKB) sAc[s * kTcKB + tid] = anext;
+      sAc[s * 4 * kTcKB + tid] = anext;
     }
     if (b + 1 < nb) {  // prefetch the next block (consumed next iteration)
       cnext = load_coef(b + 1);
@@ -225,19 +231,41 @@ k_leg_synth_tc(const float2* __restrict__ alm, int64_t alm_stride, const float* 
       mu2 = ma;
       mu1 = mb;
     };
-    auto emit = [&](int j) {
+    auto emit2 = [&](int j, float ma, float mb) {
       if constexpr (SPLIT) {
-        vh[j] = tf32_rna(mu2);
-        vh[j + 1] = tf32_rna(mu1);
-        vl[j] = tf32_bits(mu2 - __uint_as_float(vh[j]));
-        vl[j + 1] = tf32_bits(mu1 - __uint_as_float(vh[j + 1]));
+        vh[j] = tf32_rna(ma);
+        vh[j + 1] = tf32_rna(mb);
+        vl[j] = tf32_bits(ma - __uint_as_float(vh[j]));
+        vl[j + 1] = tf32_bits(mb - __uint_as_float(vh[j + 1]));
       } else {
-        vh[j] = tf32_bits(mu2);
-        vh[j + 1] = tf32_bits(mu1);
+        vh[j] = tf32_bits(ma);
+        vh[j + 1] = tf32_bits(mb);
       }
     };
-    const float* sa = &sAc[s * kTcKB];
-    if (__any_sync(0xffffffffu, jinj >= 0 && jinj < kTcKB)) {
+    auto emit = [&](int j) { emit2(j, mu2, mu1); };
+    const float* sa = &sAc[s * 4 * kTcKB];
+    if (polar) {
+      // difference form: mu2 holds e_{l-1} = mu_{l-1} - R_{l-1} mu_{l-2}
+#pragma unroll
+      for (int j = 0; j < kTcKB; j += 2) {
+        const float2 a2 = *reinterpret_cast<const float2*>(sa + j);
+        const float2 b2 = *reinterpret_cast<const float2*>(sa + kTcKB + j);
+        const float2 r2 = *reinterpret_cast<const float2*>(sa + 2 * kTcKB + j);
+        const float2 s2 = *reinterpret_cast<const float2*>(sa + 3 * kTcKB + j);
+        float e = fmaf(fmaf(-a2.x, y, b2.x), mu1, s2.x * mu2);
+        float ma = fmaf(r2.x, mu1, e);
+        e = fmaf(fmaf(-a2.y, y, b2.y), ma, s2.y * e);
+        float mb = fmaf(r2.y, ma, e);
+        if (j == jinj) {
+          ma = inj.x;
+          mb = inj.y;
+          e = fmaf(-r2.y, inj.x, inj.y);
+        }
+        mu2 = e;
+        mu1 = mb;
+        emit2(j, ma, mb);
+      }
+    } else if (__any_sync(0xffffffffu, jinj >= 0 && jinj < kTcKB)) {
       // a pair of this warp starts in the block: inject its start values at jinj
 #pragma unroll
       for (int j = 0; j < kTcKB; j += 2) {
@@ -321,7 +349,8 @@ int launch_synth_tc(const Grid& g, const void* alm, int64_t as, void* F, int64_t
   auto kern = k_leg_synth_tc<NM, SPLIT>;
   CMBWS_TRY(ensure_dyn_smem((const void*)kern, LY::kSmem));
   ProfScope ps(PROF_LEG_SYNTH, s, SPLIT ? 4 : 3, 4.0 * g.npair * (double)nlm_of(L) * (NM + 1));
-  kern<<<grd, kTcNT, LY::kSmem, s>>>((const float2*)alm, as, g.A32.as<float>(), g.ls.as<int>(),
+  kern<<<grd, kTcNT, LY::kSmem, s>>>((const float2*)alm, as, g.A32.as<float>(), g.BRS32.as<float>(),
+                                     g.ls.as<int>(),
                                      g.st32.as<float2>(), g.y32.as<float>(), g.pair_ring.as<int2>(),
                                      (float2*)F, fs, L, g.npair);
   CMBWS_LAUNCH_CHECK();

@@ -299,6 +299,22 @@ int grid_build_tables(Grid& g) {
   CMBWS_TRY(g.A64.upload(A.data(), nlm * 8));
   CMBWS_TRY(g.A32.upload(Af.data(), nlm * 4));
   {
+    // difference form of the recurrence near the poles (FP32 synthesis):
+    // R_l = c_{l-1} / c_l, S_l = 1 / R_{l-1}, B_l = A_l - R_l - S_l
+    std::vector<float> brs(3 * nlm, 0.f);
+    for (int m = 0; m <= L; ++m) {
+      const int64_t o = lm_off(L, m) - m;
+      for (int l = m + 2; l <= L; ++l) {
+        const double R = c[o + l - 1] / c[o + l], S = c[o + l - 1] / c[o + l - 2];
+        brs[3 * (o + l)] = (float)(A[o + l] - R - S);
+        brs[3 * (o + l) + 1] = (float)R;
+        brs[3 * (o + l) + 2] = (float)S;
+      }
+      if (m + 1 <= L) brs[3 * (o + m + 1) + 1] = (float)(c[o + m] / c[o + m + 1]);
+    }
+    CMBWS_TRY(g.BRS32.upload(brs.data(), nlm * 12));
+  }
+  {
     std::vector<float> A2(2 * nlm);
     for (int64_t i = 0; i < nlm; ++i) {
       const float h = (float)A[i];
