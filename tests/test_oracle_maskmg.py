@@ -1,0 +1,137 @@
+"""Pins of the mask-restricted multigrid preconditioner of the oracle (oracle/maskmg.py)."""
+import numpy as np
+import pytest
+
+import skygen
+from oracle import alm as oalm
+from oracle import cg as ocg
+from oracle import grids as og
+from oracle import maskmg as mg
+from oracle import model as omodel
+from oracle import precond as oprec
+from oracle import sht as osht
+
+
+@pytest.mark.parametrize("nside", [1, 2, 4, 8, 16, 32])
+def test_ang2pix_returns_every_pixel_centre(nside):
+    g = og.healpix(nside)
+    th, ph = g.pixel_angles()
+    np.testing.assert_array_equal(mg.ang2pix_ring(nside, th, ph), np.arange(g.npix))
+
+
+@pytest.mark.parametrize("nside", [2, 4, 8, 16, 32])
+def test_every_coarse_pixel_has_four_nearby_children(nside):
+    par = mg.coarse_parent(nside)
+    assert np.all(np.bincount(par, minlength=12 * (nside // 2) ** 2) == 4)
+    # children lie within one coarse pixel size of their parent's centre
+    g, gc = og.healpix(nside), og.healpix(nside // 2)
+    th, ph = g.pixel_angles()
+    tc, pc = gc.pixel_angles()
+    v = np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)], 1)
+    vc = np.stack([np.sin(tc) * np.cos(pc), np.sin(tc) * np.sin(pc), np.cos(tc)], 1)
+    ang = np.arccos(np.clip(np.sum(v * vc[par], 1), -1, 1))
+    assert ang.max() < 1.5 * np.sqrt(4 * np.pi / gc.npix)
+
+
+def _band_mask(nside, zcut=0.35):
+    g = og.healpix(nside)
+    th, _ = g.pixel_angles()
+    return np.abs(np.cos(th)) < zcut
+
+
+def _cinv(L):
+    c = skygen.cl_shape("cmb", L) * 1e3
+    return 1.0 / c
+
+
+def test_bottom_is_a_pseudo_inverse_of_the_dense_G():
+    nside, L = 4, 11
+    lv = mg.build_levels(nside, L, _band_mask(nside), _cinv(L), max_bottom=10 ** 6)
+    assert len(lv) == 1
+    b = lv[0]
+    Y = osht.dense_Y(b.grid, L)[b.idx]
+    G = (Y * b.d[oalm.ell_of_index(L)][None, :]) @ Y.T
+    # eigenvalues kept down to 1e-10 of the largest: the identity holds to eps x 1e10
+    np.testing.assert_allclose(G @ b.Gp @ G, G, atol=1e-6 * np.abs(G).max())
+    # the operator form of G agrees with the dense matrix
+    x = np.zeros(b.grid.npix)
+    x[b.idx] = np.random.default_rng(0).standard_normal(b.idx.size)
+    np.testing.assert_allclose(b.G(x)[b.idx], G @ x[b.idx], atol=1e-10 * np.abs(G).max())
+
+
+def test_vcycle_is_symmetric_and_accelerates_cg():
+    nside, L = 16, 47
+    mask = _band_mask(nside)
+    lv = mg.build_levels(nside, L, mask, _cinv(L), max_bottom=60)
+    assert len(lv) >= 3
+    h = lv[0]
+    idx = np.where(h.mask)[0]
+    rng = np.random.default_rng(1)
+
+    def rand():
+        v = np.zeros(h.grid.npix)
+        v[idx] = rng.standard_normal(idx.size)
+        return v
+
+    # the V-cycle is a symmetric operator: u . V v = v . V u
+    for _ in range(3):
+        u, v = rand(), rand()
+        a, b = u @ mg.vcycle(lv, v), v @ mg.vcycle(lv, u)
+        assert abs(a - b) <= 1e-10 * max(abs(a), abs(b))
+    # the coarse-grid correction removes large-scale error: for smooth fields (l <= 8) one
+    # V-cycle leaves < 20 % error, against the same two smoothing sweeps without it
+    a = rng.standard_normal((L + 1) ** 2) * (oalm.ell_of_index(L) <= 8)
+    x = np.where(h.mask, osht.synthesis(h.grid, L, a), 0.0)
+    b = h.G(x)
+    e_mg = np.linalg.norm(x - mg.vcycle(lv, b)) / np.linalg.norm(x)
+    y = h.smooth * b
+    y = y + h.smooth * np.where(h.mask, b - h.G(y), 0.0)
+    e_sm = np.linalg.norm(x - y) / np.linalg.norm(x)
+    assert e_mg < 0.2 and e_mg < 0.5 * e_sm, (e_mg, e_sm)
+
+
+def _masked_model(nside=8, L=23, zcut=0.35):
+    w = skygen.tiny_plain()
+    w.comps = w.comps[:1]                            # CMB only, as in the paper's masked benchmark
+    gs = [og.healpix(nside) for _ in w.bands]
+    for b in w.bands:
+        b.grid, b.n, b.lmax = "healpix", nside, L
+    w.comps[0].lmax = L
+    coords = [(np.cos(g.pixel_angles()[0]), g.pixel_angles()[1]) for g in gs]
+    inp = skygen.make_inputs(w, coords, [g.pixel_weights() for g in gs])
+    mask = _band_mask(nside, zcut)
+    mgrid = og.healpix(nside)
+    mmaps = [[np.where(mask, 0.0, 1.0) * inp["q"][nu, 0]] for nu in range(3)]
+    m = omodel.Model(lmax_comp=[L], grids=gs, lmax_band=[L] * 3, beam=inp["beams"], cl=inp["cl"],
+                     tau=inp["tau"], q=inp["q"], mix_grid=[[mgrid]] * 3, mix_map=mmaps)
+    return m, inp, mask
+
+
+def test_mask_precond_with_exact_inner_inverse_is_eq_M_mask():
+    m, inp, mask = _masked_model(nside=4, L=11)
+    mp = mg.MaskPrecond(m, 0, 4, mask, max_bottom=10 ** 6)
+    h = mp.levels[0]
+    assert h.Gp is not None
+    Y = osht.dense_Y(h.grid, mp.L0)[h.idx]
+    Z = Y * mp.r0[oalm.ell_of_index(mp.L0)][None, :]
+    Sinv = omodel.prior_inv_diag(m)
+    M = Z.T @ np.linalg.pinv(Z @ np.diag(Sinv) @ Z.T, rcond=1e-10) @ Z
+    rng = np.random.default_rng(2)
+    r = rng.standard_normal(m.nvec())
+    # both sides are pseudo-inverses of an ill-conditioned G (cut-offs at 1e-10 of the
+    # largest eigen- / singular value): they agree to eps x 1e10; a wrong factor would be O(1)
+    np.testing.assert_allclose(mp.apply(m, r), M @ r, rtol=1e-5, atol=1e-5 * np.abs(M @ r).max())
+
+
+def test_M_add_speeds_up_the_masked_solve():
+    m, inp, mask = _masked_model()
+    mp = mg.MaskPrecond(m, 0, 8, mask, max_bottom=60)
+    x_true = inp["x_true"]
+    b = omodel.apply_A(m, x_true)
+    Up = oprec.pinv_blocks(oprec.U_blocks(m))
+    _, rep_pi = ocg.pcg(lambda v: omodel.apply_A(m, v), b,
+                        apply_M=lambda v: oprec.apply_precond(m, v, Up), tol=1e-6, maxiter=3000)
+    x, rep_add = ocg.pcg(lambda v: omodel.apply_A(m, v), b,
+                         apply_M=lambda v: mg.apply_M_add(m, [mp], v, Up), tol=1e-6, maxiter=3000)
+    assert rep_add["iters"] * 2 < rep_pi["iters"], (rep_add["iters"], rep_pi["iters"])
+    assert np.linalg.norm(x - x_true) < 1e-4 * np.linalg.norm(x_true)
