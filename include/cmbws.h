@@ -204,6 +204,30 @@ int cmbws_apply_A(cmbws_model m, const double* x, double* y, void* stream);
 int cmbws_apply_precond(cmbws_model m, const double* r, double* z, void* stream);
 
 /*
+ * Mask-restricted preconditioner for component `comp` (Sec. 4):
+ *   M_mask = Z^T (Z S^-1 Z^T)^-1 Z   (Eq. M_mask),   Z = (pixels in the mask) Y R,
+ * R = diag(r_l) the low-pass filter of Eq. rl, r_l = exp(-beta l^2 (l+1)^2) with r^2 = 0.05
+ * at L/2.  (Z S^-1 Z^T)^-1 is approximated by one multigrid V-cycle (Sec. 4.4): HEALPix
+ * levels with Nside and band-limit halved per level, a coarse pixel kept when its four
+ * children are all in the mask, harmonic restriction Y_H R_H Y_h^T W_h, damped constant
+ * smoother (omega = 0.2), SVD pseudo-inverse of the dense system at the bottom.  Solves
+ * with cmbws_cg_opts.precond = 2 use M_add = M_PI + M_mask (Sec. 4.2).
+ *   nside: HEALPix resolution of the mask, normally that of the mixing maps that carry it;
+ *     level 0 has band-limit min(3 nside - 1, L_comp).
+ *   mask: device map of 12 nside^2 doubles (ring order), nonzero inside the mask (the pixels
+ *     whose data the mixing maps exclude).  Copied; the caller may free it.
+ *   max_bottom: the coarsest level holds at most this many mask pixels (1..4096; e.g. 400).
+ * Several calls add several preconditioners (summed).  Synchronises `stream`.
+ * Errors: CMBWS_ERR_ARG (no prior on the component, bad arguments),
+ * CMBWS_ERR_SINGULAR (a bottom pixel without coupling).
+ */
+int cmbws_model_add_mask_precond(cmbws_model m, int comp, int nside, const double* mask,
+                                 int max_bottom, void* stream);
+
+/* z = M_add r = M_PI r + sum of the model's mask preconditioners (Sec. 4.2).  r, z distinct. */
+int cmbws_apply_M_add(cmbws_model m, const double* r, double* z, void* stream);
+
+/*
  * b = P^T N^-1 d + P^T N^-1/2 omega1 + S^-1/2 omega2 (Sec. 2.3; the printed S^-1 omega2
  * is read as S^-1/2 omega2, for which Var(b) = A).  b is FP64-accurate for every model:
  * its transforms run in FP64 for FP64 models and in CMBWS_FP32X2 otherwise.
@@ -266,7 +290,8 @@ int cmbws_profile_read(double* ms, int64_t* launches, double* flops, int reset);
 typedef struct {
   double tol;         /* stop when ||b - A x||_2 / ||b||_2 <= tol, certified by an FP64 apply */
   int maxiter;        /* cap on CG iterations (all inner iterations counted) */
-  int precond;        /* 0 = none, 1 = M_PI */
+  int precond;        /* 0 = none, 1 = M_PI, 2 = M_add = M_PI + the model's mask
+                         preconditioners (cmbws_model_add_mask_precond) */
   double inner_tol;   /* FP32 models: relative reduction per refinement pass (e.g. 1e-3) */
   int max_outer;      /* FP32 models: cap on refinement passes */
   double timeout_s;   /* wall-clock budget, <= 0 for none */

@@ -24,6 +24,7 @@ from .binding import (  # noqa: F401
     Grid,
     Model,
     cmbws_apply_A,
+    cmbws_apply_M_add,
     cmbws_apply_precond,
     cmbws_cg_solve,
     cmbws_cg_solve_batched,
@@ -31,6 +32,7 @@ from .binding import (  # noqa: F401
     cmbws_grid_destroy,
     cmbws_grid_info,
     cmbws_grid_rings,
+    cmbws_model_add_mask_precond,
     cmbws_model_create,
     cmbws_model_destroy,
     cmbws_model_info,

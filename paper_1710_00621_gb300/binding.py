@@ -96,6 +96,8 @@ def load_library(path=None):
     lib.cmbws_rhs.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp, vp, vp]
     lib.cmbws_project.argtypes = [vp, vp, ctypes.POINTER(vp), vp]
     lib.cmbws_grad_terms.argtypes = [vp, vp, vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp, vp, vp]
+    lib.cmbws_model_add_mask_precond.argtypes = [vp, i, i, vp, i, vp]
+    lib.cmbws_apply_M_add.argtypes = [vp, vp, vp, vp]
     lib.cmbws_profile_enable.argtypes = [i]
     lib.cmbws_profile_read.argtypes = [ctypes.POINTER(d), ctypes.POINTER(ctypes.c_int64),
                                        ctypes.POINTER(d), i]
@@ -353,6 +355,20 @@ def cmbws_grad_terms(model, x, lam, d, out, omega1=None, omega2=None, stream=Non
     _check(load_library().cmbws_grad_terms(model.handle, _dptr(x, model.nvec, "x"),
                                            _dptr(lam, model.nvec, "lam"), dp, w1, w2,
                                            _dptr(out, nobs * ncomp + ncomp, "out"), _stream(stream)))
+
+
+def cmbws_model_add_mask_precond(model, comp, nside, mask, max_bottom=400, stream=None):
+    """Attach the mask-restricted multigrid preconditioner of component `comp` (HEALPix mask map
+    of 12 nside^2 CUDA float64, nonzero inside the mask); solves with precond=2 use M_PI + M_mask."""
+    _check(load_library().cmbws_model_add_mask_precond(
+        model.handle, int(comp), int(nside), _dptr(mask, 12 * nside * nside, "mask"),
+        int(max_bottom), _stream(stream)))
+
+
+def cmbws_apply_M_add(model, r, z, stream=None):
+    """z = M_PI r + the mask preconditioners' M_mask r."""
+    _check(load_library().cmbws_apply_M_add(model.handle, _dptr(r, model.nvec, "r"),
+                                            _dptr(z, model.nvec, "z"), _stream(stream)))
 
 
 def cmbws_project(model, x, d, stream=None):

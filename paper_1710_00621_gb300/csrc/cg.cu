@@ -152,6 +152,19 @@ struct Solver {
 
 }  // namespace
 
+// z = M r: identity (use_M = 0), M_PI (1) or M_add = M_PI + the model's mask preconditioners (2)
+static int precondition(Model& M, int use_M, int prec, const double* r, double* z, int64_t n,
+                        cudaStream_t s) {
+  if (!use_M) {
+    CMBWS_CUDA(cudaMemcpyAsync(z, r, n * 8, cudaMemcpyDeviceToDevice, s));
+    return CMBWS_OK;
+  }
+  CMBWS_TRY(M.apply_precond(r, z, prec, s));
+  if (use_M == 2)
+    for (MaskMG* mg : M.masks) CMBWS_TRY(mask_mg_apply(*mg, M, r, z, s));
+  return CMBWS_OK;
+}
+
 // PCG on A d = r0 (d starts at zero), operator precision `prec`; stops when
 // ||r|| <= stop_abs or after maxit iterations.  r0 is overwritten with the final residual.
 static int pcg_core(Solver& S, int prec, int use_M, double* d, double* r, double stop_abs, int maxit,
@@ -167,8 +180,7 @@ static int pcg_core(Solver& S, int prec, int use_M, double* d, double* r, double
   *rr_out = rr;
   *iters = 0;
   if (std::sqrt(rr) <= stop_abs) return CMBWS_OK;
-  if (use_M) CMBWS_TRY(M.apply_precond(r, z, prec, S.s));
-  else CMBWS_CUDA(cudaMemcpyAsync(z, r, n * 8, cudaMemcpyDeviceToDevice, S.s));
+  CMBWS_TRY(precondition(M, use_M, prec, r, z, n, S.s));
   CMBWS_CUDA(cudaMemcpyAsync(p, z, n * 8, cudaMemcpyDeviceToDevice, S.s));
   double rz;
   CMBWS_TRY(S.dot(r, z, &rz));
@@ -198,8 +210,7 @@ static int pcg_core(Solver& S, int prec, int use_M, double* d, double* r, double
       set_error("CG: wall-clock budget of %g s exhausted", timeout);
       return CMBWS_ERR_TIMEOUT;
     }
-    if (use_M) CMBWS_TRY(M.apply_precond(r, z, prec, S.s));
-    else CMBWS_CUDA(cudaMemcpyAsync(z, r, n * 8, cudaMemcpyDeviceToDevice, S.s));
+    CMBWS_TRY(precondition(M, use_M, prec, r, z, n, S.s));
     double rz_new;
     CMBWS_TRY(S.dot(r, z, &rz_new));
     const double beta = rz_new / rz;
@@ -319,7 +330,8 @@ extern "C" int cmbws_cg_solve(cmbws_model mh, const double* b, double* x, const 
                               cmbws_cg_report* report, void* stream) {
   clear_error();
   Model* M = reinterpret_cast<Model*>(mh);
-  if (!M || !b || !x || !opts || b == x || !(opts->tol > 0.0) || opts->maxiter < 1) {
+  if (!M || !b || !x || !opts || b == x || !(opts->tol > 0.0) || opts->maxiter < 1 ||
+      opts->precond < 0 || opts->precond > 2) {
     set_error("cmbws_cg_solve: invalid arguments");
     return CMBWS_ERR_ARG;
   }
@@ -339,7 +351,8 @@ extern "C" int cmbws_cg_solve_batched(const cmbws_model* models, int nprob, cons
                                       double* const* x, const cmbws_cg_opts* opts,
                                       cmbws_cg_report* reports, int nworkers, void* stream) {
   clear_error();
-  if (!models || nprob < 1 || !b || !x || !opts || !(opts->tol > 0.0) || opts->maxiter < 1) {
+  if (!models || nprob < 1 || !b || !x || !opts || !(opts->tol > 0.0) || opts->maxiter < 1 ||
+      opts->precond < 0 || opts->precond > 2) {
     set_error("cmbws_cg_solve_batched: invalid arguments");
     return CMBWS_ERR_ARG;
   }

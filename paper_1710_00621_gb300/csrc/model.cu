@@ -351,6 +351,9 @@ __global__ void k_add_scaled_prior(HarmDev h, const double* __restrict__ w2, dou
   if (m > 0) b[base + (Lk - m + 1) + (l - m)] += s * w2[base + (Lk - m + 1) + (l - m)];
 }
 
+
+}  // namespace
+
 // One-sided Jacobi SVD pseudo-inverse of an (nr x nc) matrix U (row-major), out (nc x nr).
 // Returns false if a column of U is zero.
 bool pinv_jacobi(const std::vector<double>& Uin, int nr, int nc, double rcond,
@@ -413,7 +416,6 @@ bool pinv_jacobi(const std::vector<double>& Uin, int nr, int nc, double rcond,
   return true;
 }
 
-}  // namespace
 
 // ---- the chain of one grid group: synthesis -> fused FFT/pixel multiply -> adjoint ----
 int Model::group_chain(Group& G, int prec, int which, cudaStream_t s) {

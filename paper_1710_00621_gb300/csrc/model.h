@@ -12,6 +12,8 @@ constexpr int kMaxComp = 8;    // components
 constexpr int kMaxBands = 16;  // observations
 constexpr int kMaxMaps = 8;    // bands transformed together on one grid
 
+struct MaskMG;  // mask-restricted multigrid preconditioner (maskmg.cu)
+
 // Variable mixing pair (nu, k), device view (array of nobs * ncomp in device memory).
 struct PairDev {
   const double2* out;  // chain output of the pair (internal layout of its mixing grid, FP64)
@@ -98,6 +100,10 @@ struct Model {
   std::vector<DevMem> pixQ64, pixQ32;     // q_{nu,k}(n) w(n) per pair id (empty if scalar)
   DevMem d_pairs;                         // PairDev [nobs * ncomp]
 
+  // mask-restricted preconditioners (Sec. 4), applied with M_PI when precond = 2
+  std::vector<MaskMG*> masks;
+  ~Model();
+
   HarmDev harm() const;
   BandDev bands_dev(int prec) const;
   int group_chain(Group& G, int prec, int which, cudaStream_t s);
@@ -113,5 +119,13 @@ struct Model {
 };
 
 int model_create(const cmbws_model_desc* desc, int prec, cudaStream_t s, Model** out);
+
+// One-sided Jacobi SVD pseudo-inverse of an (nr x nc) row-major matrix, out (nc x nr);
+// singular values below rcond * max are dropped.  false if a column is zero.
+bool pinv_jacobi(const std::vector<double>& Uin, int nr, int nc, double rcond,
+                 std::vector<double>& out);
+
+void mask_mg_destroy(MaskMG* p);
+int mask_mg_apply(MaskMG& mg, const Model& M, const double* r, double* z, cudaStream_t s);
 
 }  // namespace cmbws
