@@ -184,33 +184,45 @@ def solve_step(P, model, tol, x, b, cert="fp32x2"):
                              inner_tol=INNER_TOL[0], max_outer=30, cert_prec=cp)
 
 
-def batched_measure(nprob, tol, fmax=0.0):
-    """Independent uneven problems (Ncomp 2, Nobs 3, GL L_p ~ U{128..1024}; fmax > 0 adds a
-    galactic-band mask of sky fraction U[0, fmax] through the mixing maps): one
-    cmbws_cg_solve_batched call vs the same solves one after the other.  Masked systems need
-    the mask-restricted preconditioner to converge quickly, so the default is full sky."""
+def batched_measure(nprob, tol, fmax=0.3, max_bottom=200):
+    """Independent uneven problems (Ncomp 2, Nobs 3, GL bands L_p ~ U{128..1024}) with a
+    galactic-band mask of sky fraction U[0, fmax] carried by the mixing maps on a HEALPix
+    mixing grid (Nside_p: the smallest power of two with 3 Nside_p - 1 >= L_p), solved with
+    M_add = M_PI + the mask-restricted multigrid preconditioner of each component: one
+    cmbws_cg_solve_batched call vs the same solves one after the other.  Every solve has a
+    wall-clock budget; progress goes to stderr."""
     import torch
     import paper_1710_00621_gb300 as cw
     dev = torch.device("cuda")
-    models, bs = [], []
+    models, bs, masked = [], [], []
     keep = []
-    lsum = 0
+    t_setup = time.perf_counter()
     for work, f in skygen.batched_uneven(nprob=nprob, fmax=fmax):
         L = work.bands[0].lmax
-        lsum += L ** 3
         g = cw.cmbws_plan_grid(cw.CMBWS_GRID_GL, L + 1, L)
         z, ph = g.pixel_coords()
         w = g.pixel_weights()
         inp = skygen.make_inputs(work, [(z, ph)] * 3, [w] * 3)
         q = inp["q"]
         ninv = [torch.as_tensor(t, device=dev) for t in inp["tau"]]
-        mg = maps = None
+        mg = maps = mask = None
+        nside = 1
+        while 3 * nside - 1 < L:
+            nside *= 2
         if f > 0:
-            mask = torch.as_tensor(skygen.galactic_mask(z, f), device=dev)
-            maps = [[float(q[nu, k]) * mask for k in range(2)] for nu in range(3)]
-            mg = [[g, g]] * 3
+            hg = cw.cmbws_plan_grid(cw.CMBWS_GRID_HEALPIX, nside, L)
+            hz, _ = hg.pixel_coords()
+            inside = 1.0 - skygen.galactic_mask(hz, f)          # 1 inside the band |b| < b0
+            mask = torch.as_tensor(inside, device=dev)
+            keepmap = torch.as_tensor(1.0 - inside, device=dev)
+            maps = [[float(q[nu, k]) * keepmap for k in range(2)] for nu in range(3)]
+            mg = [[hg, hg]] * 3
         m = cw.cmbws_model_create([c.lmax for c in work.comps], [g] * 3, inp["beams"], inp["cl"],
                                   ninv, q, cw.CMBWS_FP32, mix_grids=mg, mix_maps=maps)
+        npx = float(mask.sum()) if mask is not None else 0.0
+        if npx > 0:
+            for k in range(2):
+                cw.cmbws_model_add_mask_precond(m, k, nside, mask, max_bottom)
         x_true = torch.as_tensor(inp["x_true"], device=dev)
         d = [torch.empty(g.npix, dtype=torch.float64, device=dev) for _ in range(3)]
         cw.cmbws_project(m, x_true, d)
@@ -220,11 +232,16 @@ def batched_measure(nprob, tol, fmax=0.0):
         cw.cmbws_rhs(m, d, b)
         models.append(m)
         bs.append(b)
-        keep.append((g, maps, ninv))
+        masked.append(npx)
+        keep.append((g, maps, ninv, mask, mg))
+        print(f"[batched] setup L={L} f={f:.3f} nside={nside}", file=sys.stderr, flush=True)
+    t_setup = time.perf_counter() - t_setup
     xs = [torch.zeros(m.nvec, dtype=torch.float64, device=dev) for m in models]
-    kw = dict(tol=tol, maxiter=20000, cert_prec=cw.CMBWS_FP32X2, inner_tol=1e-3, max_outer=30)
-    cw.cmbws_cg_solve_batched(models, bs, xs, **kw)        # warm-up (workspaces)
+    kw = dict(tol=tol, maxiter=3000, cert_prec=cw.CMBWS_FP32X2, inner_tol=1e-3, max_outer=10,
+              precond=2, timeout_s=60.0)
+    cw.cmbws_cg_solve_batched(models, bs, xs, check=False, **kw)   # warm-up (workspaces)
     torch.cuda.synchronize()
+    print("[batched] warm-up done", file=sys.stderr, flush=True)
     for x in xs:
         x.zero_()
     t0 = time.perf_counter()
@@ -237,13 +254,26 @@ def batched_measure(nprob, tol, fmax=0.0):
         cw.cmbws_cg_solve(m, bs[i], xs[i], check=False, **kw)
     torch.cuda.synchronize()
     tseq = time.perf_counter() - t0
+    print("[batched] timed solves done", file=sys.stderr, flush=True)
+    # the same masked problems with M_PI alone, on the three largest masks (budget-bounded)
+    big = sorted(range(len(models)), key=lambda i: -masked[i])[:3]
+    cmp = []
+    for i in big:
+        x = torch.zeros_like(xs[i])
+        r1 = cw.cmbws_cg_solve(models[i], bs[i], x, check=False,
+                               **{**kw, "precond": 1, "maxiter": 1000, "timeout_s": 20.0})
+        cmp.append({"L": int(models[i].lmax_comp[0]), "iters_M_PI": r1["iters"],
+                    "M_PI_certified": r1["status"] == 0, "iters_M_add": reps[i]["iters"]})
     its = [r["iters"] for r in reps]
     return {"nprob": nprob, "batched_s": round(tb, 3), "sequential_s": round(tseq, 3),
             "speedup": round(tseq / tb, 2), "iters_min_median_max": [min(its), int(np.median(its)), max(its)],
             "all_certified": all(r["status"] == 0 and r["rel_res"] <= tol for r in reps),
-            "workload": (f"GL L 128..1024, Ncomp 2, Nobs 3, "
-                         + (f"galactic-band masks 0-{fmax:.0%} via mixing maps, " if fmax > 0 else "full sky, ")
-                         + "FP32 transforms + FP32X2 certification, 8 worker streams")}
+            "n_certified": sum(r["status"] == 0 and r["rel_res"] <= tol for r in reps),
+            "setup_s": round(t_setup, 1), "M_PI_vs_M_add_largest_masks": cmp,
+            "workload": (f"GL L 128..1024 with resolution-matched beams, Ncomp 2, Nobs 3, galactic-"
+                         f"band masks of sky fraction U[0, {fmax}] in HEALPix mixing maps, M_add = "
+                         "M_PI + multigrid M_mask, FP32 transforms + FP32X2 certification, "
+                         "8 worker streams")}
 
 
 def precision_report(nside=1024, nmaps=3, reps=3):

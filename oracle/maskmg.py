@@ -16,8 +16,12 @@ mask pixels), is approximated by one multigrid V-cycle (Sec. 4.4, the basic V-cy
   interpolation its transpose;
 * coarse operators G_H = Y_H D_H Y_H^T with d_H = r_H^2 d_h;
 * smoother M_h = omega diag(G_h)^-1, omega = 0.2, diag(G_h) = sum_l (2l+1)/(4 pi) d_{h,l}
-  (constant: G is rotation invariant);
-* bottom level: SVD (here: symmetric eigen-) pseudo-inverse of the dense G.
+  (constant: G is rotation invariant).  The paper picks omega = 0.2 so that omega M G has
+  eigenvalues below 2 on its grids (L = 3 Nside); since lambda_max(G) <= max_l d_l Npix/(4 pi),
+  omega is capped at diag(G) / (max_l d_l Npix / (4 pi)) on grids with more pixels per mode;
+* bottom level: SVD (here: symmetric eigen-) pseudo-inverse of the dense G, eigenvalues
+  below 1e-5 of the largest dropped (the scales the bottom solve is for lie well above;
+  the filtered high-l directions below would only amplify rounding).
 
 The coarse-pixel rule needs the parent of a fine pixel: the coarse pixel containing the
 fine pixel's centre, found with HEALPix ang2pix (Gorski et al. 2005 geometry: in the
@@ -118,7 +122,12 @@ class Level:
         self.d = d                                           # d_l, l <= L
         self.w = 4.0 * np.pi / (12 * nside * nside)          # HEALPix quadrature weight
         l = np.arange(L + 1)
-        self.smooth = OMEGA / float(np.sum((2 * l + 1) / (4 * np.pi) * d))
+        dg = float(np.sum((2 * l + 1) / (4 * np.pi) * d))
+        # omega M G must stay below 2 (Sec. 4.4); lambda_max(G) <= max d_l Npix / (4 pi), so on
+        # grids with more pixels per harmonic mode than the paper's (L = 3 Nside) omega is capped
+        bound = float(np.max(d)) * self.grid.npix / (4 * np.pi)
+        omega = min(OMEGA, dg / bound) if bound > 0 else OMEGA
+        self.smooth = omega / dg
         self.rH = None                                       # restriction filter to the next level
         self.Gp = None                                       # bottom: pseudo-inverse on mask pixels
 
@@ -130,7 +139,7 @@ class Level:
         return np.where(self.mask, y, 0.0)
 
 
-def build_levels(nside0, L0, mask0, cinv, max_bottom=400, rcond=1e-10):
+def build_levels(nside0, L0, mask0, cinv, max_bottom=400, rcond=1e-5):
     """The level hierarchy for component prior C^-1 = cinv[l] (l <= L0)."""
     r0 = rl_filter(L0, L0)
     d = r0 * r0 * np.asarray(cinv[:L0 + 1], dtype=np.float64)

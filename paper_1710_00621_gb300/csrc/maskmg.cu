@@ -11,7 +11,8 @@
 //     child's centre);
 //   * restriction Y_H R_H Y_h^T W_h (R_H the Eq. rl filter at L_H), interpolation its transpose;
 //   * coarse operators d_H = r_H^2 d_h;
-//   * smoother omega / diag(G_h), omega = 0.2, diag(G_h) = sum_l (2l+1) / (4 pi) d_{h,l};
+//   * smoother omega / diag(G_h), omega = 0.2, diag(G_h) = sum_l (2l+1) / (4 pi) d_{h,l}, with
+//     omega capped so that omega lambda_max(G_h) / diag(G_h) <= 1 on oversampled grids;
 //   * bottom: the SVD pseudo-inverse of the dense G on the mask pixels.
 // Maps live full-sky on each level (zero outside the mask), as the paper's "zero padding".
 // The transforms are the library's own (cmbws_sht_synth / cmbws_sht_analysis) on level grids
@@ -25,7 +26,12 @@ namespace cmbws {
 namespace {
 
 constexpr double kOmega = 0.2;
-constexpr double kBottomRcond = 1e-10;
+// Bottom pseudo-inverse cut-off, relative to the largest singular value.  The compounded
+// Eq. rl filters make d_l span ~20 orders of magnitude, so G has eigenvalues far below the
+// large scales the bottom solve is for (those stay within ~1e-3 of the largest); keeping
+// eigenvalues down to 1e-10 would amplify the FP32 rounding of the right-hand side by up to
+// 1e10 and make the preconditioner noisy (no longer a fixed symmetric operator).
+constexpr double kBottomRcond = 1e-5;
 
 // out[i] = mask[i] ? ca * a[i] + cb * b[i] : 0   (b may be null)
 __global__ void k_map_lincomb(double* __restrict__ out, double ca, const double* a, double cb,
@@ -246,9 +252,17 @@ int add_level(MaskMG& mg, int nside, int L, const std::vector<uint8_t>& mask,
   h.w = 4.0 * M_PI / (double)h.npix;
   h.mask_h = mask;
   h.d_h = d;
-  double dg = 0.0;
-  for (int l = 0; l <= L; ++l) dg += (2.0 * l + 1.0) / (4.0 * M_PI) * d[l];
-  h.smooth = dg > 0 ? kOmega / dg : 0.0;
+  // damped smoother omega / diag(G): the paper's omega = 0.2 keeps omega M G below 2 on its
+  // grids (L = 3 Nside); lambda_max(G) <= max_l d_l Npix / (4 pi), so on grids with more
+  // pixels per harmonic mode omega is capped at diag(G) / (max_l d_l Npix / (4 pi)) (<= 1)
+  double dg = 0.0, dmax = 0.0;
+  for (int l = 0; l <= L; ++l) {
+    dg += (2.0 * l + 1.0) / (4.0 * M_PI) * d[l];
+    dmax = std::max(dmax, d[l]);
+  }
+  const double lmax_bound = dmax * (double)h.npix / (4.0 * M_PI);
+  const double omega = lmax_bound > 0 ? std::min(kOmega, dg / lmax_bound) : kOmega;
+  h.smooth = dg > 0 ? omega / dg : 0.0;
   std::vector<double> mk(h.npix);
   for (int64_t i = 0; i < h.npix; ++i) mk[i] = mask[i] ? 1.0 : 0.0;
   CMBWS_TRY(h.mask.upload(mk.data(), h.npix * 8));

@@ -238,13 +238,17 @@ def batched_uneven(nprob=64, lmin=128, lmax=1024, fmax=0.3, seed_offset=0):
     """Independent problems (Ncomp = 2: CMB + dust beta 1.6; Nobs = 3: 30/100/353 GHz) with
     band-limits L_p ~ U{lmin..lmax} on Gauss-Legendre grids and a galactic-band mask
     |b| < b0, sin b0 = f_p ~ U[0, fmax] (sky fraction f_p), applied through the mixing maps.
-    Returns [(workload, f_p)]."""
+    Beams follow the resolution, as for maps downgraded to L_p: sigma_b = c_nu / L_p with
+    c = 2.0 / 1.6 / 1.3, so the inverse-noise term has decayed by ~0.1 where the dust prior
+    takes over (0.75 L_p).  Returns [(workload, f_p)]."""
     rng = np.random.default_rng([SEED_BASE + 3, seed_offset])
     out = []
+    fwhm_per_sigma = np.sqrt(8.0 * np.log(2.0)) / ARCMIN
     for p in range(nprob):
         L = int(rng.integers(lmin, lmax + 1))
         f = float(rng.uniform(0.0, fmax))
-        bands = [Band(fr, "gl", L, L, fw, 10.0) for fr, fw in ((30.0, 60.0), (100.0, 40.0), (353.0, 30.0))]
+        bands = [Band(fr, "gl", L, L, c / L * fwhm_per_sigma, 10.0)
+                 for fr, c in ((30.0, 2.0), (100.0, 1.6), (353.0, 1.3))]
         comps = [Comp("cmb", L, "cmb", None, 1.0, 0.40), Comp("dust", L, "dust", 1.6, 353.0, 0.75)]
         w = Workload(f"batched_p{p}_gl{L}_f{f:.3f}", SEED_BASE + 3 + 1000 * (p + 1) + seed_offset,
                      bands, comps)

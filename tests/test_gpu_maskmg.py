@@ -40,9 +40,10 @@ def test_M_mask_parity(prec):
     cw.cmbws_apply_precond(gm, to_dev(r), zpi)
     got = to_host(zadd - zpi)
     ref = mp.apply(m, r)
-    # the bottom pseudo-inverses (Jacobi SVD here, eigen-decomposition in the oracle) of an
-    # ill-conditioned G agree to eps x 1e10 (cut-off 1e-10); FP32 transforms add ~1e-5 per level
-    assert rel_err(got, ref) < (1e-5 if prec == "fp64" else 2e-3), rel_err(got, ref)
+    # the bottom pseudo-inverses (Jacobi SVD here, eigen-decomposition in the oracle, both cut
+    # at 1e-5) agree to eps x 1e5; FP32 transforms add ~1e-5 per level, amplified by <= 1e5
+    # only in the weakest kept directions
+    assert rel_err(got, ref) < (1e-9 if prec == "fp64" else 2e-3), rel_err(got, ref)
 
 
 def test_masked_solve_with_M_add():
