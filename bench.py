@@ -53,7 +53,7 @@ def parse():
                     help="skip the per-precision synthesis time / error report")
     ap.add_argument("--inner-tol", type=float, default=1e-3,
                     help="relative residual reduction per refinement pass (FP32 solves)")
-    ap.add_argument("--with-batched", type=int, default=0, metavar="NPROB",
+    ap.add_argument("--with-batched", type=int, default=32, metavar="NPROB",
                     help="also time NPROB independent uneven masked problems (GL L 128..1024), "
                          "batched vs sequential, reported under 'batched'")
     ap.add_argument("--cert", default="fp32x2", choices=["fp32x2", "fp64"],
@@ -501,7 +501,12 @@ def main():
                 "mixed_vs_fp64_rel_diff": diff}
         out["iters_fp64_plain"] = r64["iters"]
 
-    batched = batched_measure(args.with_batched, args.tol) if args.with_batched else None
+    batched = None
+    if args.with_batched and args.scale == 1:
+        try:
+            batched = batched_measure(args.with_batched, args.tol)
+        except Exception as e:  # noqa: BLE001 - reported in the line instead of losing it
+            batched = {"error": f"{type(e).__name__}: {e}"[:300]}
     precision = precision_report() if (not args.no_precision and args.scale == 1) else None
 
     if rank != 0:
