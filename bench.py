@@ -34,6 +34,7 @@ sys.path.insert(0, ROOT)
 
 import skygen  # noqa: E402
 
+SEED_CR = skygen.SEED_BASE + 3
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # FP32 FMA lanes x 2 flops x max SM clock
 FP64_PEAK_TFLOPS = 1.25                               # GB300 FP64 (profiling recipe, nominal)
 
@@ -49,6 +50,8 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--no-fp64-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-masked-cr", action="store_true",
+                    help="skip the masked constrained-realization solve (FP32 vs FP64, M_add)")
     ap.add_argument("--no-precision", action="store_true",
                     help="skip the per-precision synthesis time / error report")
     ap.add_argument("--inner-tol", type=float, default=1e-3,
@@ -274,6 +277,79 @@ def batched_measure(nprob, tol, fmax=0.3, max_bottom=200):
                          f"band masks of sky fraction U[0, {fmax}] in HEALPix mixing maps, M_add = "
                          "M_PI + multigrid M_mask, FP32 transforms + FP32X2 certification, "
                          "8 worker streams")}
+
+
+def masked_cr_measure(tol=1e-6, scale=1, max_bottom=200):
+    """Planck-shaped masked constrained realization at reduced resolution (skygen.masked_cr:
+    4 components, 9 HEALPix bands at Nside 128/256, galactic band |b| < 20 deg and 200 disks
+    carried by every mixing map on a HEALPix Nside 256 mixing grid, CR right-hand side with
+    omega_1, omega_2): FP32 transforms with double-float certification against the FP64
+    solver, both with M_add; M_PI alone within a budget for contrast."""
+    import torch
+    import paper_1710_00621_gb300 as cw
+    dev = torch.device("cuda")
+    work = skygen.masked_cr(scale)
+    grids = {}
+    for bnd in work.bands:
+        if bnd.n not in grids:
+            grids[bnd.n] = cw.cmbws_plan_grid(cw.CMBWS_GRID_HEALPIX, bnd.n, bnd.lmax)
+    bg = [grids[bnd.n] for bnd in work.bands]
+    nmix = max(bnd.n for bnd in work.bands)
+    Lmix = max(3 * nmix - 1, max(c.lmax for c in work.comps))
+    mgrid = cw.cmbws_plan_grid(cw.CMBWS_GRID_HEALPIX, nmix, Lmix)
+    inp = skygen.make_inputs(work, [g.pixel_coords() for g in bg], [g.pixel_weights() for g in bg])
+    mz, mph = mgrid.pixel_coords()
+    inside = skygen.planck_like_mask(mz, mph)
+    mask = torch.as_tensor(inside, device=dev)
+    keepmap = torch.as_tensor(1.0 - inside, device=dev)
+    q = inp["q"]
+    nb, nc = len(work.bands), len(work.comps)
+    maps = [[float(q[nu, k]) * keepmap for k in range(nc)] for nu in range(nb)]
+    mgs = [[mgrid] * nc for _ in range(nb)]
+    ninv = [torch.as_tensor(t, device=dev) for t in inp["tau"]]
+    models = {}
+    for name, p in (("fp32", cw.CMBWS_FP32), ("fp64", cw.CMBWS_FP64)):
+        m = cw.cmbws_model_create([c.lmax for c in work.comps], bg, inp["beams"], inp["cl"], ninv, q, p,
+                                  mix_grids=mgs, mix_maps=maps)
+        for k in range(nc):
+            cw.cmbws_model_add_mask_precond(m, k, nmix, mask, max_bottom)
+        models[name] = m
+    m64 = models["fp64"]
+    x_true = torch.as_tensor(inp["x_true"], device=dev)
+    d = [torch.empty(g.npix, dtype=torch.float64, device=dev) for g in bg]
+    cw.cmbws_project(m64, x_true, d)
+    gen = torch.Generator(device=dev).manual_seed(SEED_CR)
+    for nu in range(nb):
+        d[nu] += torch.as_tensor(inp["noise"][nu], device=dev)
+    w1 = [torch.randn(g.npix, dtype=torch.float64, device=dev, generator=gen) for g in bg]
+    w2 = torch.randn(m64.nvec, dtype=torch.float64, device=dev, generator=gen)
+    b = torch.empty(m64.nvec, dtype=torch.float64, device=dev)
+    cw.cmbws_rhs(m64, d, b, omega1=w1, omega2=w2)
+    out = {}
+    xs = {}
+    for name, cert in (("fp32", cw.CMBWS_FP32X2), ("fp64", cw.CMBWS_FP64)):
+        x = torch.zeros_like(b)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = cw.cmbws_cg_solve(models[name], b, x, tol=tol, maxiter=3000, precond=2, inner_tol=1e-3,
+                              max_outer=10, cert_prec=cert, timeout_s=240.0, check=False)
+        torch.cuda.synchronize()
+        out[name] = {"s": round(time.perf_counter() - t0, 3), "iters": r["iters"], "outer": r["outer"],
+                     "rel_res": r["rel_res"], "certified": r["status"] == 0}
+        xs[name] = x
+        print(f"[masked_cr] {name} done", file=sys.stderr, flush=True)
+    out["fp32_vs_fp64_rel_diff"] = float(torch.linalg.vector_norm(xs["fp32"] - xs["fp64"])
+                                         / torch.linalg.vector_norm(xs["fp64"]))
+    x = torch.zeros_like(b)
+    r = cw.cmbws_cg_solve(models["fp32"], b, x, tol=tol, maxiter=600, precond=1, inner_tol=1e-3,
+                          max_outer=4, cert_prec=cw.CMBWS_FP32X2, timeout_s=30.0, check=False)
+    out["M_PI_alone_fp32"] = {"iters": r["iters"], "certified": r["status"] == 0, "rel_res": r["rel_res"]}
+    nsht_A = models["fp32"].nsht_A
+    out["workload"] = (f"{work.name}: Ncomp {nc}, Nobs {nb} (Nside 128/256), L_k {work.comps[0].lmax}, "
+                       f"mask {inside.mean():.1%} of the sky (|b| < 20 deg + 200 disks) in all "
+                       f"{nb * nc} mixing maps on HEALPix Nside {nmix}, {nsht_A} SHTs per apply of A, "
+                       "CR right-hand side, M_add = M_PI + one multigrid M_mask per component")
+    return out
 
 
 def precision_report(nside=1024, nmaps=3, reps=3):
@@ -508,6 +584,12 @@ def main():
         except Exception as e:  # noqa: BLE001 - reported in the line instead of losing it
             batched = {"error": f"{type(e).__name__}: {e}"[:300]}
     precision = precision_report() if (not args.no_precision and args.scale == 1) else None
+    masked_cr = None
+    if not args.no_masked_cr and args.scale == 1:
+        try:
+            masked_cr = masked_cr_measure(args.tol)
+        except Exception as e:  # noqa: BLE001 - reported in the line instead of losing it
+            masked_cr = {"error": f"{type(e).__name__}: {e}"[:300]}
 
     if rank != 0:
         return
@@ -527,7 +609,8 @@ def main():
                                       if args.prec == "fp32" else "FP64"),
                        "l2": "inputs larger than L2, no flush",
                        "parallelism": f"replicas x{world}"},
-            "solve": out, "fp64_plain": fp64, "batched": batched, "precision": precision,
+            "solve": out, "fp64_plain": fp64, "batched": batched, "masked_cr": masked_cr,
+            "precision": precision,
             "roofline": rl, "cpu_baseline": cb, "e2e": e2e,
             "gpu_launches": launches, "stages": stages, "clocks": clk}
     print(json.dumps(line))

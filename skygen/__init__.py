@@ -259,3 +259,41 @@ def batched_uneven(nprob=64, lmin=128, lmax=1024, fmax=0.3, seed_offset=0):
 def galactic_mask(z, f):
     """1 outside the band |b| < b0 with sin b0 = f (b = 90 deg - theta, so sin b = z), 0 inside."""
     return (np.abs(z) >= f).astype(np.float64)
+
+
+def masked_cr(scale=1):
+    """Planck-shaped masked constrained realization at reduced resolution: Ncomp = 4 (CMB,
+    synchrotron beta -3.0, dust beta 1.6, free-free beta -2.1 at nu_0 = 30 GHz), L_k = 511 / scale;
+    Nobs = 9 HEALPix bands (30/44/70 GHz at Nside 128 / scale, 100-857 GHz at 256 / scale,
+    L_nu = 3 Nside - 1), FWHM 33' -> 5' scaled by 4 scale (the downgrade), noise rms x3 smooth
+    pattern.  The mask (``planck_like_mask``) enters through every mixing map."""
+    nsides = (128, 128, 128, 256, 256, 256, 256, 256, 256)
+    bands = []
+    for i, (f, ns) in enumerate(zip(PLANCK_FREQS, nsides)):
+        ns = ns // scale
+        fw = 33.0 * (5.0 / 33.0) ** (i / 8.0) * 4 * scale
+        bands.append(Band(f, "healpix", ns, 3 * ns - 1, fw, 1.0, contrast=3.0))
+    L = 511 // scale
+    comps = [Comp("cmb", L, "cmb", None, 1.0, 0.40),
+             Comp("synch", L, "synch", -3.0, 30.0, 0.35),
+             Comp("dust", L, "dust", 1.6, 353.0, 0.75),
+             Comp("freefree", L, "freefree", -2.1, 30.0, 0.35)]
+    return Workload(f"masked_cr_4comp_nside{128 // scale}-{256 // scale}", SEED_BASE + 3, bands, comps)
+
+
+def planck_like_mask(z, phi, seed=SEED_BASE + 3, ndisk=200, band_deg=20.0):
+    """1 inside the mask: the galactic band |b| < band_deg (sin b = z) and ndisk disks with
+    centres uniform on the sphere and radii U[0.5, 3] degrees."""
+    rng = np.random.default_rng([seed, 11])
+    inside = np.abs(z) < np.sin(np.radians(band_deg))
+    st = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    v = np.stack([st * np.cos(phi), st * np.sin(phi), z], axis=-1)
+    cz = rng.uniform(-1.0, 1.0, ndisk)
+    cp = rng.uniform(0.0, 2 * np.pi, ndisk)
+    cs = np.sqrt(1.0 - cz * cz)
+    c = np.stack([cs * np.cos(cp), cs * np.sin(cp), cz], axis=-1)
+    rad = np.radians(rng.uniform(0.5, 3.0, ndisk))
+    for k in range(ndisk):
+        inside |= (v @ c[k]) >= np.cos(rad[k])
+    return inside.astype(np.float64)
+

@@ -89,3 +89,15 @@ def test_mask_precond_needs_a_prior():
                                inp["q"], cw.CMBWS_FP64)
     with pytest.raises(cw.CmbwsError):
         cw.cmbws_model_add_mask_precond(gm, 0, 4, to_dev(mask.astype(np.float64)), 60)
+
+
+def test_masked_constrained_realization_fp32_matches_fp64():
+    """The masked CR workload (4 components, 9 bands, band + disks mask in all 36 mixing maps,
+    omega_1 / omega_2 right-hand side) at reduced size: the FP32-refined solution with M_add
+    agrees with the FP64 one, both certified, and M_PI alone needs more iterations."""
+    import bench
+    out = bench.masked_cr_measure(tol=1e-8, scale=8, max_bottom=100)
+    assert out["fp32"]["certified"] and out["fp64"]["certified"], out
+    # two solutions certified to 1e-8 in residual differ by at most ~cond x 1e-8
+    assert out["fp32_vs_fp64_rel_diff"] < 1e-5, out
+    assert out["M_PI_alone_fp32"]["iters"] > out["fp32"]["iters"], out
