@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--no-fp64-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the tiny-problem and differentiable-solve measurements")
     ap.add_argument("--no-masked-cr", action="store_true",
                     help="skip the masked constrained-realization solve (FP32 vs FP64, M_add)")
     ap.add_argument("--no-precision", action="store_true",
@@ -352,6 +354,87 @@ def masked_cr_measure(tol=1e-6, scale=1, max_bottom=200):
     return out
 
 
+def _gl_problem(work, prec=None):
+    """Library model + synthetic data for a workload whose bands share one GL grid."""
+    import torch
+    import paper_1710_00621_gb300 as cw
+    dev = torch.device("cuda")
+    L = work.bands[0].lmax
+    g = cw.cmbws_plan_grid(cw.CMBWS_GRID_GL, L + 1, L)
+    z, ph = g.pixel_coords()
+    w = g.pixel_weights()
+    nb = len(work.bands)
+    inp = skygen.make_inputs(work, [(z, ph)] * nb, [w] * nb)
+    ninv = [torch.as_tensor(t, device=dev) for t in inp["tau"]]
+    m64 = cw.cmbws_model_create([c.lmax for c in work.comps], [g] * nb, inp["beams"], inp["cl"], ninv,
+                                inp["q"], cw.CMBWS_FP64)
+    d = [torch.empty(g.npix, dtype=torch.float64, device=dev) for _ in range(nb)]
+    cw.cmbws_project(m64, torch.as_tensor(inp["x_true"], device=dev), d)
+    for nu in range(nb):
+        d[nu] += torch.as_tensor(inp["noise"][nu], device=dev)
+    return g, inp, ninv, m64, d
+
+
+def tiny_measure(reps=5):
+    """The tiny two-component GL problem (L = 63, 3 bands): FP64 solve to 1e-8, launch-bound."""
+    import torch
+    import paper_1710_00621_gb300 as cw
+    work = skygen.tiny_plain()
+    g, inp, ninv, m64, d = _gl_problem(work)
+    b = torch.empty(m64.nvec, dtype=torch.float64, device="cuda")
+    x = torch.zeros_like(b)
+    cw.cmbws_rhs(m64, d, b)
+    cw.cmbws_cg_solve(m64, b, x, tol=1e-8, maxiter=1000)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        x.zero_()
+        r = cw.cmbws_cg_solve(m64, b, x, tol=1e-8, maxiter=1000)
+    torch.cuda.synchronize()
+    return {"s": round((time.perf_counter() - t0) / reps, 5), "iters": r["iters"],
+            "rel_res": r["rel_res"], "workload": work.name + ", FP64, M_PI, tol 1e-8"}
+
+
+def differentiable_measure(L=511):
+    """Gradient of ||W x||^2 of the Wiener solution with respect to the two spectral indices and
+    the three prior log-amplitudes (autodiff.WienerSolution: forward solve, adjoint solve and
+    cmbws_grad_terms), FP32 transforms with FP64 scalars against FP64, wall time of one
+    forward + backward."""
+    import torch
+    import paper_1710_00621_gb300 as cw
+    from paper_1710_00621_gb300.autodiff import WienerProblem, power_law_q, wiener_solution
+    work = skygen.differentiable(lmax=L)
+    g, inp, ninv, m64, d = _gl_problem(work)
+    wgt = torch.as_tensor(skygen.harmonic_weight([c.lmax for c in work.comps]), device="cuda")
+    out = {}
+    grads = {}
+    for name, prec, tol in (("fp32", cw.CMBWS_FP32, 1e-10), ("fp64", cw.CMBWS_FP64, 1e-10)):
+        prob = WienerProblem([c.lmax for c in work.comps], [g] * len(work.bands), inp["beams"],
+                             inp["cl"], ninv, d, prec=prec, tol=tol, maxiter=5000)
+        ts = []
+        for _ in range(2):  # the first pass builds the double-float tables
+            betas = torch.tensor([0.0 if c.beta is None else c.beta for c in work.comps],
+                                 dtype=torch.float64, requires_grad=True)
+            logamp = torch.zeros(len(work.comps), dtype=torch.float64, requires_grad=True)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            q = power_law_q([bd.freq for bd in work.bands], [c.nu0 for c in work.comps], betas,
+                            [c.beta is None for c in work.comps])
+            loss = ((wgt * wiener_solution(q, logamp, prob)) ** 2).sum()
+            loss.backward()
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        gv = np.concatenate([betas.grad.numpy()[[c.beta is not None for c in work.comps]],
+                             logamp.grad.numpy()])
+        grads[name] = gv
+        out[name] = {"forward_backward_s": round(ts[-1], 3)}
+    out["max_rel_grad_diff_fp32_vs_fp64"] = float(np.max(np.abs(grads["fp32"] - grads["fp64"])
+                                                         / np.abs(grads["fp64"])))
+    out["workload"] = (f"{work.name}: loss ||W x||^2, gradients w.r.t. beta_synch, beta_dust and "
+                       "3 prior log-amplitudes; solves certified to 1e-10")
+    return out
+
+
 def precision_report(nside=1024, nmaps=3, reps=3):
     """Synthesis of one full-size band grid (HEALPix Nside 1024, L = 3071, three maps) in every
     transform precision: time per call (CUDA events) and the max-relative difference from the
@@ -584,6 +667,13 @@ def main():
         except Exception as e:  # noqa: BLE001 - reported in the line instead of losing it
             batched = {"error": f"{type(e).__name__}: {e}"[:300]}
     precision = precision_report() if (not args.no_precision and args.scale == 1) else None
+    extras = {}
+    if not args.no_extras and args.scale == 1:
+        for key, fn in (("tiny", tiny_measure), ("differentiable", differentiable_measure)):
+            try:
+                extras[key] = fn()
+            except Exception as e:  # noqa: BLE001
+                extras[key] = {"error": f"{type(e).__name__}: {e}"[:300]}
     masked_cr = None
     if not args.no_masked_cr and args.scale == 1:
         try:
@@ -610,6 +700,7 @@ def main():
                        "l2": "inputs larger than L2, no flush",
                        "parallelism": f"replicas x{world}"},
             "solve": out, "fp64_plain": fp64, "batched": batched, "masked_cr": masked_cr,
+            "tiny": extras.get("tiny"), "differentiable": extras.get("differentiable"),
             "precision": precision,
             "roofline": rl, "cpu_baseline": cb, "e2e": e2e,
             "gpu_launches": launches, "stages": stages, "clocks": clk}
