@@ -660,6 +660,30 @@ def main():
                 "mixed_vs_fp64_rel_diff": diff}
         out["iters_fp64_plain"] = r64["iters"]
 
+    # the paper's comparison (Sec. 5): the same solve with the block-diagonal preconditioner
+    mdiag = None
+    if not args.no_extras:
+        try:
+            xd = torch.zeros(n, dtype=torch.float64, device=dev)
+            cwd = cw.CMBWS_FP32X2 if cert == "fp32x2" else cw.CMBWS_FP64
+            kwd = dict(tol=args.tol, maxiter=3000, precond=3, inner_tol=args.inner_tol,
+                       max_outer=20, cert_prec=cwd, timeout_s=120.0, check=False)
+            cw.cmbws_cg_solve(model, b, xd, **kwd)  # builds M_diag
+            res = {}
+            for name, pc in (("M_PI", 1), ("M_diag", 3)):
+                xd.zero_()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                rd = cw.cmbws_cg_solve(model, b, xd, **{**kwd, "precond": pc})
+                torch.cuda.synchronize()
+                res[name] = {"s": round(time.perf_counter() - t0, 3), "iters": rd["iters"],
+                             "outer": rd["outer"], "certified": rd["status"] == 0}
+            mdiag = {**res, "time_ratio_M_diag_over_M_PI": round(res["M_diag"]["s"] / res["M_PI"]["s"], 2),
+                     "note": ("the step's solve (right-hand side given) with M_PI and with the "
+                              "block-diagonal M_diag = (U^T diag(T) U)^-1, same certification")}
+        except Exception as e:  # noqa: BLE001
+            mdiag = {"error": f"{type(e).__name__}: {e}"[:300]}
+
     batched = None
     if args.with_batched and args.scale == 1:
         try:
@@ -701,6 +725,7 @@ def main():
                        "parallelism": f"replicas x{world}"},
             "solve": out, "fp64_plain": fp64, "batched": batched, "masked_cr": masked_cr,
             "tiny": extras.get("tiny"), "differentiable": extras.get("differentiable"),
+            "M_diag_comparison": mdiag,
             "precision": precision,
             "roofline": rl, "cpu_baseline": cb, "e2e": e2e,
             "gpu_launches": launches, "stages": stages, "clocks": clk}

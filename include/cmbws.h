@@ -228,6 +228,17 @@ int cmbws_model_add_mask_precond(cmbws_model m, int comp, int nside, const doubl
 int cmbws_apply_M_add(cmbws_model m, const double* r, double* z, void* stream);
 
 /*
+ * z = M_diag r, the block-diagonal preconditioner the paper compares M_PI with (Sec. 5):
+ * M_diag = (U^T diag(T) U)^-1, i.e. for every real coefficient (l, m, cos / sin) the inverse of
+ * the Ncomp x Ncomp block C_{k,l}^-1 delta_kk' + sum_nu b_{nu,l}^2 q_{nu,k} q_{nu,k'}
+ * diag(Y_nu^T N_nu^-1 Y_nu)_lm, with q the scalars of M_PI (Eq. optimal-q for variable maps)
+ * and the diagonal from ring sums of lambda_lm^2 and the ring Fourier sums of tau at even
+ * frequencies (FP64 ring sums, FP32 lambda^2 sums, FP64 blocks).  Built on the first call
+ * (or the first solve with precond = 3) and kept by the model.  r, z distinct.
+ */
+int cmbws_apply_M_diag(cmbws_model m, const double* r, double* z, void* stream);
+
+/*
  * b = P^T N^-1 d + P^T N^-1/2 omega1 + S^-1/2 omega2 (Sec. 2.3; the printed S^-1 omega2
  * is read as S^-1/2 omega2, for which Var(b) = A).  b is FP64-accurate for every model:
  * its transforms run in FP64 for FP64 models and in CMBWS_FP32X2 otherwise.
@@ -291,7 +302,8 @@ typedef struct {
   double tol;         /* stop when ||b - A x||_2 / ||b||_2 <= tol, certified by an FP64 apply */
   int maxiter;        /* cap on CG iterations (all inner iterations counted) */
   int precond;        /* 0 = none, 1 = M_PI, 2 = M_add = M_PI + the model's mask
-                         preconditioners (cmbws_model_add_mask_precond) */
+                         preconditioners (cmbws_model_add_mask_precond), 3 = the block-
+                         diagonal M_diag (cmbws_apply_M_diag) */
   double inner_tol;   /* FP32 models: relative reduction per refinement pass (e.g. 1e-3) */
   int max_outer;      /* FP32 models: cap on refinement passes */
   double timeout_s;   /* wall-clock budget, <= 0 for none */

@@ -25,6 +25,7 @@ from .binding import (  # noqa: F401
     Model,
     cmbws_apply_A,
     cmbws_apply_M_add,
+    cmbws_apply_M_diag,
     cmbws_apply_precond,
     cmbws_cg_solve,
     cmbws_cg_solve_batched,

@@ -98,6 +98,7 @@ def load_library(path=None):
     lib.cmbws_grad_terms.argtypes = [vp, vp, vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp, vp, vp]
     lib.cmbws_model_add_mask_precond.argtypes = [vp, i, i, vp, i, vp]
     lib.cmbws_apply_M_add.argtypes = [vp, vp, vp, vp]
+    lib.cmbws_apply_M_diag.argtypes = [vp, vp, vp, vp]
     lib.cmbws_profile_enable.argtypes = [i]
     lib.cmbws_profile_read.argtypes = [ctypes.POINTER(d), ctypes.POINTER(ctypes.c_int64),
                                        ctypes.POINTER(d), i]
@@ -369,6 +370,12 @@ def cmbws_apply_M_add(model, r, z, stream=None):
     """z = M_PI r + the mask preconditioners' M_mask r."""
     _check(load_library().cmbws_apply_M_add(model.handle, _dptr(r, model.nvec, "r"),
                                             _dptr(z, model.nvec, "z"), _stream(stream)))
+
+
+def cmbws_apply_M_diag(model, r, z, stream=None):
+    """z = M_diag r (block-diagonal comparison preconditioner)."""
+    _check(load_library().cmbws_apply_M_diag(model.handle, _dptr(r, model.nvec, "r"),
+                                             _dptr(z, model.nvec, "z"), _stream(stream)))
 
 
 def cmbws_project(model, x, d, stream=None):

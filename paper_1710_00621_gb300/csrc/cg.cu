@@ -152,13 +152,15 @@ struct Solver {
 
 }  // namespace
 
-// z = M r: identity (use_M = 0), M_PI (1) or M_add = M_PI + the model's mask preconditioners (2)
+// z = M r: identity (use_M = 0), M_PI (1), M_add = M_PI + the model's mask preconditioners (2)
+// or the block-diagonal M_diag (3)
 static int precondition(Model& M, int use_M, int prec, const double* r, double* z, int64_t n,
                         cudaStream_t s) {
   if (!use_M) {
     CMBWS_CUDA(cudaMemcpyAsync(z, r, n * 8, cudaMemcpyDeviceToDevice, s));
     return CMBWS_OK;
   }
+  if (use_M == 3) return M.apply_diag(r, z, s);
   CMBWS_TRY(M.apply_precond(r, z, prec, s));
   if (use_M == 2)
     for (MaskMG* mg : M.masks) CMBWS_TRY(mask_mg_apply(*mg, M, r, z, s));
@@ -331,7 +333,7 @@ extern "C" int cmbws_cg_solve(cmbws_model mh, const double* b, double* x, const 
   clear_error();
   Model* M = reinterpret_cast<Model*>(mh);
   if (!M || !b || !x || !opts || b == x || !(opts->tol > 0.0) || opts->maxiter < 1 ||
-      opts->precond < 0 || opts->precond > 2) {
+      opts->precond < 0 || opts->precond > 3) {
     set_error("cmbws_cg_solve: invalid arguments");
     return CMBWS_ERR_ARG;
   }
@@ -352,7 +354,7 @@ extern "C" int cmbws_cg_solve_batched(const cmbws_model* models, int nprob, cons
                                       cmbws_cg_report* reports, int nworkers, void* stream) {
   clear_error();
   if (!models || nprob < 1 || !b || !x || !opts || !(opts->tol > 0.0) || opts->maxiter < 1 ||
-      opts->precond < 0 || opts->precond > 2) {
+      opts->precond < 0 || opts->precond > 3) {
     set_error("cmbws_cg_solve_batched: invalid arguments");
     return CMBWS_ERR_ARG;
   }

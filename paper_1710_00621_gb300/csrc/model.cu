@@ -876,6 +876,7 @@ int model_create(const cmbws_model_desc* desc, int prec, cudaStream_t s, Model**
   CMBWS_TRY(M->d_cisq.upload(cisq.data(), cisq.size() * 8));
   CMBWS_TRY(M->d_clOff.upload(clOff.data(), nc * 8));
   CMBWS_TRY(M->d_Up.upload(Up.data(), Up.size() * 8));
+  CMBWS_TRY(M->d_qpre.upload(qpre.data(), qpre.size() * 8));
 
   // ---- workspaces ----
   size_t part_bytes = 0;

@@ -100,6 +100,14 @@ struct Model {
   std::vector<DevMem> pixQ64, pixQ32;     // q_{nu,k}(n) w(n) per pair id (empty if scalar)
   DevMem d_pairs;                         // PairDev [nobs * ncomp]
 
+  // block-diagonal comparison preconditioner M_diag (diagprec.cu), built on first use:
+  // per band diag(Y^T N^-1 Y) as (cos, sin) per (l, m), and the inverse blocks
+  DevMem d_qpre;                 // [nobs][ncomp] scalars of the preconditioners (Eq. optimal-q)
+  DevMem dg_D, dg_inv;
+  bool dg_ready = false;
+  int build_diag(cudaStream_t s);
+  int apply_diag(const double* r, double* z, cudaStream_t s);
+
   // mask-restricted preconditioners (Sec. 4), applied with M_PI when precond = 2
   std::vector<MaskMG*> masks;
   ~Model();
