@@ -189,6 +189,46 @@ def solve_step(P, model, tol, x, b, cert="fp32x2"):
                              inner_tol=INNER_TOL[0], max_outer=30, cert_prec=cp)
 
 
+def cr_chain_measure(model, P, xmean, tol, inner_tol, cert, nsamp=3):
+    """A chain of constrained realizations (Sec. 2.3) on the bench model: omega_1, omega_2
+    drawn on the device (cmbws_cr_sample), each solve started from zero, from the previous
+    sample, or from the Wiener-filter mean xmean."""
+    import torch
+    import paper_1710_00621_gb300 as cw
+    cp = cw.CMBWS_FP32X2 if cert == "fp32x2" else cw.CMBWS_FP64
+    kw = dict(tol=tol, maxiter=3000, precond=1, inner_tol=inner_tol, max_outer=20,
+              cert_prec=cp, timeout_s=120.0, check=False)
+    xs = torch.zeros_like(xmean)
+    res = {}
+    for start in ("zero", "previous", "mean"):
+        its, secs, ok = [], [], []
+        xs.zero_()
+        for s in range(nsamp):
+            if start == "zero":
+                xs.zero_()
+            elif start == "mean":
+                xs.copy_(xmean)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = cw.cmbws_cr_sample(model, P["d"], SEED_CR, s, xs, **kw)
+            torch.cuda.synchronize()
+            secs.append(round(time.perf_counter() - t0, 3))
+            its.append(r["iters"])
+            ok.append(r["status"] == 0)
+        res[start] = {"s": secs, "iters": its, "certified": all(ok)}
+    b2 = torch.empty_like(xmean)
+    cw.cmbws_cr_rhs(model, P["d"], SEED_CR, nsamp, b2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    cw.cmbws_cr_rhs(model, P["d"], SEED_CR, nsamp + 1, b2)
+    torch.cuda.synchronize()
+    t_rhs = time.perf_counter() - t0
+    return {"samples": nsamp, "start": res, "draw_and_rhs_s": round(t_rhs, 4),
+            "note": ("constrained realizations with on-device Philox4x64-10 / Box-Muller "
+                     "variates; 'previous' starts each solve from the chain's last sample "
+                     "(the first from zero)")}
+
+
 def batched_measure(nprob, tol, fmax=0.3, max_bottom=200):
     """Independent uneven problems (Ncomp 2, Nobs 3, GL bands L_p ~ U{128..1024}) with a
     galactic-band mask of sky fraction U[0, fmax] carried by the mixing maps on a HEALPix
@@ -684,6 +724,13 @@ def main():
         except Exception as e:  # noqa: BLE001
             mdiag = {"error": f"{type(e).__name__}: {e}"[:300]}
 
+    crchain = None
+    if not args.no_extras:
+        try:
+            crchain = cr_chain_measure(model, P, x, args.tol, args.inner_tol, cert)
+        except Exception as e:  # noqa: BLE001
+            crchain = {"error": f"{type(e).__name__}: {e}"[:300]}
+
     batched = None
     if args.with_batched and args.scale == 1:
         try:
@@ -726,6 +773,7 @@ def main():
             "solve": out, "fp64_plain": fp64, "batched": batched, "masked_cr": masked_cr,
             "tiny": extras.get("tiny"), "differentiable": extras.get("differentiable"),
             "M_diag_comparison": mdiag,
+            "cr_chain": crchain,
             "precision": precision,
             "roofline": rl, "cpu_baseline": cb, "e2e": e2e,
             "gpu_launches": launches, "stages": stages, "clocks": clk}

@@ -347,6 +347,49 @@ int cmbws_cg_solve_batched(const cmbws_model* models, int nprob, const double* c
                            double* const* x, const cmbws_cg_opts* opts, cmbws_cg_report* reports,
                            int nworkers, void* stream);
 
+/*
+ * Variates of a counter-based stream, for constrained realizations (Sec. 2.3) drawn on the
+ * device.  Generator: Philox4x64-10 (Salmon, Moraes, Dror and Shaw, SC'11).  Variate j of
+ * stream `stream_id` is word j % 4 of Philox4x64-10(counter (j / 4, stream_id, 0, 0),
+ * key (seed, sample)); a word w gives the uniform u = ((w >> 12) + 1/2) 2^-52 in (0, 1), and
+ * the uniform pairs (u0, u1), (u2, u3) of a counter give standard normals by the Box-Muller
+ * transform, z = sqrt(-2 ln u_a) (cos 2 pi u_b, sin 2 pi u_b).  So a variate depends only on
+ * (seed, sample, stream_id, j), whatever range a call covers.
+ *   out[t] = variate offset + t, t = 0 .. n-1 (device, FP64); kind 0 = standard normal,
+ *   1 = uniform.  offset, n >= 0; n = 0 does nothing.
+ * Errors: CMBWS_ERR_ARG for a negative offset or n, a bad kind, or out NULL with n > 0.
+ */
+int cmbws_draw(uint64_t seed, uint64_t sample, uint64_t stream_id, int64_t offset, int64_t n,
+               int kind, double* out, void* stream);
+
+/*
+ * Right-hand side of constrained realization `sample` (Sec. 2.3): omega_2 = stream 0 of
+ * cmbws_draw(seed, sample) over the stacked coefficient vector, omega_1 of band nu = stream
+ * 1 + nu over its pixels (ring order), both standard normal, drawn on the device into the
+ * model's workspace; then b as cmbws_rhs(d, omega_1, omega_2).
+ *   d: host array [nobs] of device maps.  b: device stacked vector, written.
+ */
+int cmbws_cr_rhs(cmbws_model m, const double* const* d, uint64_t seed, uint64_t sample,
+                 double* b, void* stream);
+
+/*
+ * One constrained realization: b of cmbws_cr_rhs, then A x = b solved as cmbws_cg_solve,
+ * starting from the initial guess held in x (e.g. the previous sample of a chain, or the
+ * Wiener-filter mean; zero for none).  x: device stacked vector, in/out.  Errors and report
+ * as cmbws_cg_solve.
+ */
+int cmbws_cr_sample(cmbws_model m, const double* const* d, uint64_t seed, uint64_t sample,
+                    double* x, const cmbws_cg_opts* opts, cmbws_cg_report* report, void* stream);
+
+/*
+ * Mixing map of a power-law SED with a spatially variable spectral index (Eq. Q):
+ * q[i] = m[i] (nu / nu_0)^beta[i], m[i] = 0 where mask[i] == 0 and 1 elsewhere (mask NULL:
+ * no mask).  beta, mask, q: device arrays of n doubles on a mixing grid, for the mix_map of
+ * cmbws_model_desc.  nu_ratio = nu / nu_0 > 0.
+ */
+int cmbws_powerlaw_mixing(double nu_ratio, const double* beta, const double* mask, int64_t n,
+                          double* q, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -5,13 +5,15 @@ CMB component separation with the pseudo-inverse preconditioner of Seljebotn et 
 The compute path is the C-ABI library ``libcmbws.so`` (hand-written CUDA kernels); this
 package is a thin ctypes binding with the same call names (``cmbws_plan_grid``,
 ``cmbws_sht_synth``, ``cmbws_sht_analysis``, ``cmbws_model_create``, ``cmbws_apply_A``,
-``cmbws_apply_precond``, ``cmbws_rhs``, ``cmbws_cg_solve``, ``cmbws_grad_terms``; the
+``cmbws_apply_precond``, ``cmbws_rhs``, ``cmbws_cg_solve``, ``cmbws_cr_sample``, ``cmbws_grad_terms``; the
 autograd wrapper is in ``autodiff``).  PyTorch only supplies
 device memory and streams.  There is no CPU fallback: loading fails loudly when the
 library has not been built.
 """
 from .binding import (  # noqa: F401
     CMBWS_3XTF32,
+    CMBWS_DRAW_NORMAL,
+    CMBWS_DRAW_UNIFORM,
     CMBWS_FP32,
     CMBWS_FP32X2,
     CMBWS_FP64,
@@ -29,6 +31,9 @@ from .binding import (  # noqa: F401
     cmbws_apply_precond,
     cmbws_cg_solve,
     cmbws_cg_solve_batched,
+    cmbws_cr_rhs,
+    cmbws_cr_sample,
+    cmbws_draw,
     cmbws_grad_terms,
     cmbws_grid_destroy,
     cmbws_grid_info,
@@ -38,6 +43,7 @@ from .binding import (  # noqa: F401
     cmbws_model_destroy,
     cmbws_model_info,
     cmbws_plan_grid,
+    cmbws_powerlaw_mixing,
     cmbws_profile_enable,
     cmbws_profile_read,
     cmbws_project,

@@ -99,6 +99,12 @@ def load_library(path=None):
     lib.cmbws_model_add_mask_precond.argtypes = [vp, i, i, vp, i, vp]
     lib.cmbws_apply_M_add.argtypes = [vp, vp, vp, vp]
     lib.cmbws_apply_M_diag.argtypes = [vp, vp, vp, vp]
+    u64 = ctypes.c_uint64
+    lib.cmbws_draw.argtypes = [u64, u64, u64, ctypes.c_int64, ctypes.c_int64, i, vp, vp]
+    lib.cmbws_cr_rhs.argtypes = [vp, ctypes.POINTER(vp), u64, u64, vp, vp]
+    lib.cmbws_cr_sample.argtypes = [vp, ctypes.POINTER(vp), u64, u64, vp, ctypes.POINTER(CgOpts),
+                                    ctypes.POINTER(CgReport), vp]
+    lib.cmbws_powerlaw_mixing.argtypes = [d, vp, vp, ctypes.c_int64, vp, vp]
     lib.cmbws_profile_enable.argtypes = [i]
     lib.cmbws_profile_read.argtypes = [ctypes.POINTER(d), ctypes.POINTER(ctypes.c_int64),
                                        ctypes.POINTER(d), i]
@@ -339,6 +345,55 @@ def cmbws_rhs(model, d, b, omega1=None, omega2=None, stream=None):
     w2 = _dptr(omega2, model.nvec, "omega2") if omega2 is not None else ctypes.c_void_p()
     _check(load_library().cmbws_rhs(model.handle, dp, w1, w2, _dptr(b, model.nvec, "b"),
                                     _stream(stream)))
+
+
+CMBWS_DRAW_NORMAL = 0
+CMBWS_DRAW_UNIFORM = 1
+
+
+def cmbws_draw(seed, sample, stream_id, offset, out, kind=CMBWS_DRAW_NORMAL, stream=None):
+    """out[t] = variate offset + t of the counter-based stream (seed, sample, stream_id);
+    out: CUDA float64 tensor (its length is n)."""
+    n = int(out.numel())
+    _check(load_library().cmbws_draw(int(seed), int(sample), int(stream_id), int(offset), n,
+                                     int(kind), _dptr(out, n, "out") if n else ctypes.c_void_p(),
+                                     _stream(stream)))
+
+
+def _band_ptrs(model, d, name):
+    nobs = len(model.grids)
+    return (ctypes.c_void_p * nobs)(*[_dptr(d[nu], model.grids[nu].npix, f"{name}[{nu}]").value
+                                      for nu in range(nobs)])
+
+
+def cmbws_cr_rhs(model, d, seed, sample, b, stream=None):
+    """b of constrained realization `sample` with omega_1, omega_2 drawn on the device."""
+    _check(load_library().cmbws_cr_rhs(model.handle, _band_ptrs(model, d, "d"), int(seed),
+                                       int(sample), _dptr(b, model.nvec, "b"), _stream(stream)))
+
+
+def cmbws_cr_sample(model, d, seed, sample, x, tol=1e-6, maxiter=1000, precond=1, inner_tol=1e-3,
+                    max_outer=20, timeout_s=0.0, cert_prec=CMBWS_FP64, stream=None, check=True):
+    """Draw constrained realization `sample` into x (x holds the initial guess)."""
+    opts = CgOpts(float(tol), int(maxiter), int(precond), float(inner_tol), int(max_outer),
+                  float(timeout_s), int(cert_prec))
+    rep = CgReport()
+    code = load_library().cmbws_cr_sample(model.handle, _band_ptrs(model, d, "d"), int(seed),
+                                          int(sample), _dptr(x, model.nvec, "x"),
+                                          ctypes.byref(opts), ctypes.byref(rep), _stream(stream))
+    if check:
+        _check(code)
+    out = rep.as_dict()
+    out["code"] = code
+    return out
+
+
+def cmbws_powerlaw_mixing(nu_ratio, beta, q, mask=None, stream=None):
+    """q = mask (nu / nu_0)^beta on the device (beta, mask, q: CUDA float64 of equal length)."""
+    n = int(q.numel())
+    mp = _dptr(mask, n, "mask") if mask is not None else ctypes.c_void_p()
+    _check(load_library().cmbws_powerlaw_mixing(float(nu_ratio), _dptr(beta, n, "beta"), mp, n,
+                                                _dptr(q, n, "q"), _stream(stream)))
 
 
 def cmbws_grad_terms(model, x, lam, d, out, omega1=None, omega2=None, stream=None):

@@ -108,6 +108,12 @@ struct Model {
   int build_diag(cudaStream_t s);
   int apply_diag(const double* r, double* z, cudaStream_t s);
 
+  // constrained-realization draws (sampling.cu): on-device omega_2 and omega_1 of every band,
+  // and the right-hand side of the draw
+  DevMem cr_w, cr_b;
+  int cr_draw_rhs(const double* const* d, uint64_t seed, uint64_t sample, double* b,
+                  cudaStream_t s);
+
   // mask-restricted preconditioners (Sec. 4), applied with M_PI when precond = 2
   std::vector<MaskMG*> masks;
   ~Model();
