@@ -48,3 +48,20 @@ def tiny_workload(L=15):
 
 def multires_small(scale=64):
     return skygen.multires_fullsky(scale=scale)
+
+
+def split_model(m, fractions=(0.5, 0.5)):
+    """Each band of an oracle Model split into detector subsets: the same grid, beam and
+    mixing, inverse noise c_h tau (sum of c_h = 1 for a split of one channel's hits).
+    Returns (model, groups) with groups[nu] the indices of band nu's subsets."""
+    from dataclasses import replace
+    nb = len(fractions)
+    idx = [nu for nu in range(m.nobs) for _ in range(nb)]
+    sm = replace(m, grids=[m.grids[nu] for nu in idx], lmax_band=[m.lmax_band[nu] for nu in idx],
+                 beam=[m.beam[nu] for nu in idx],
+                 tau=[c * m.tau[nu] for nu in range(m.nobs) for c in fractions],
+                 q=np.repeat(np.asarray(m.q), nb, axis=0),
+                 mix_grid=None if m.mix_grid is None else [m.mix_grid[nu] for nu in idx],
+                 mix_map=None if m.mix_map is None else [m.mix_map[nu] for nu in idx])
+    groups = [list(range(nu * nb, (nu + 1) * nb)) for nu in range(m.nobs)]
+    return sm, groups
