@@ -35,6 +35,7 @@ sys.path.insert(0, ROOT)
 import skygen  # noqa: E402
 
 SEED_CR = skygen.SEED_BASE + 3
+SEED_SPLIT = skygen.SEED_BASE + 5
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # FP32 FMA lanes x 2 flops x max SM clock
 FP64_PEAK_TFLOPS = 1.25                               # GB300 FP64 (profiling recipe, nominal)
 
@@ -227,6 +228,58 @@ def cr_chain_measure(model, P, xmean, tol, inner_tol, cert, nsamp=3):
             "note": ("constrained realizations with on-device Philox4x64-10 / Box-Muller "
                      "variates; 'previous' starts each solve from the chain's last sample "
                      "(the first from zero)")}
+
+
+def split_measure(P, xref, tol, inner_tol, cert):
+    """Detector splits (App. A.3): every band of the bench model as two half-hit subsets,
+    inverse noise tau / 2 each and data d + e, d - e with e ~ N(0, 1 / tau), so each half has
+    noise variance 2 / tau, the halves are independent and their mean is d.  The 18-band
+    system has the same A and b as the 9-band one; it is solved with one preconditioner row
+    per band (36 SHTs per apply of M_PI) and with the halves merged (18)."""
+    import torch
+    import paper_1710_00621_gb300 as cw
+    inp, grids = P["inp"], P["grids"]
+    dev = torch.device("cuda")
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(SEED_SPLIT)
+    ninv, d2, grids2, beams2 = [], [], [], []
+    for nu, t in enumerate(inp["tau"]):
+        tau = torch.as_tensor(t, device=dev)
+        e = torch.randn(tau.shape, generator=gen, device=dev, dtype=torch.float64) / torch.sqrt(tau)
+        for sgn in (1.0, -1.0):
+            ninv.append(0.5 * tau)
+            d2.append(P["d"][nu] + sgn * e)
+            grids2.append(grids[nu])
+            beams2.append(inp["beams"][nu])
+    q2 = np.repeat(np.asarray(inp["q"], dtype=np.float64), 2, axis=0)
+    lk = list(P["model"].lmax_comp)
+    model = cw.cmbws_model_create(lk, grids2, beams2, inp["cl"], ninv, q2, cw.CMBWS_FP32)
+    cp = cw.CMBWS_FP32X2 if cert == "fp32x2" else cw.CMBWS_FP64
+    kw = dict(tol=tol, maxiter=3000, precond=1, inner_tol=inner_tol, max_outer=20,
+              cert_prec=cp, timeout_s=120.0, check=False)
+    b = torch.zeros_like(xref)
+    x = torch.zeros_like(xref)
+    out = {"bands": len(d2)}
+    try:
+        for name, group in (("per_band", None), ("merged", [nu // 2 for nu in range(len(d2))])):
+            cw.cmbws_model_merge_precond(model, group)
+            cw.cmbws_rhs(model, d2, b)
+            for _ in range(2):          # the first solve allocates the model's workspaces
+                x.zero_()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                r = cw.cmbws_cg_solve(model, b, x, **kw)
+                torch.cuda.synchronize()
+                ts = time.perf_counter() - t0
+            diff = float(torch.linalg.vector_norm(x - xref) / torch.linalg.vector_norm(xref))
+            out[name] = {"s": round(ts, 3), "iters": r["iters"], "outer": r["outer"],
+                         "certified": r["status"] == 0, "n_sht": r["n_sht"],
+                         "nsht_M": model.nsht_M, "rel_diff_vs_9_band_solution": diff}
+    finally:
+        model.close()
+    out["note"] = ("each band split into two half-hit detector subsets; merged = App. A.3 "
+                   "row merge in the preconditioner")
+    return out
 
 
 def batched_measure(nprob, tol, fmax=0.3, max_bottom=200):
@@ -731,6 +784,13 @@ def main():
         except Exception as e:  # noqa: BLE001
             crchain = {"error": f"{type(e).__name__}: {e}"[:300]}
 
+    split = None
+    if not args.no_extras:
+        try:
+            split = split_measure(P, x, args.tol, args.inner_tol, cert)
+        except Exception as e:  # noqa: BLE001
+            split = {"error": f"{type(e).__name__}: {e}"[:300]}
+
     batched = None
     if args.with_batched and args.scale == 1:
         try:
@@ -774,6 +834,7 @@ def main():
             "tiny": extras.get("tiny"), "differentiable": extras.get("differentiable"),
             "M_diag_comparison": mdiag,
             "cr_chain": crchain,
+            "detector_splits": split,
             "precision": precision,
             "roofline": rl, "cpu_baseline": cb, "e2e": e2e,
             "gpu_launches": launches, "stages": stages, "clocks": clk}

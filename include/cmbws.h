@@ -155,8 +155,8 @@ int cmbws_sht_analysis_noalloc(cmbws_grid g, cmbws_prec prec, const double* map,
  * after cmbws_model_create returns.
  */
 typedef struct {
-  int ncomp;                     /* Ncomp >= 1 */
-  int nobs;                      /* Nobs >= 1 */
+  int ncomp;                     /* 1 <= Ncomp <= 8 */
+  int nobs;                      /* 1 <= Nobs <= 64 */
   const int* lmax_comp;          /* [ncomp] L_k */
   const cmbws_grid* band_grid;   /* [nobs] grid of d_nu; L_nu = that grid's lmax. Bands
                                     sharing a grid handle are transformed together. */
@@ -223,6 +223,24 @@ int cmbws_apply_precond(cmbws_model m, const double* r, double* z, void* stream)
  */
 int cmbws_model_add_mask_precond(cmbws_model m, int comp, int nside, const double* mask,
                                  int max_bottom, void* stream);
+
+/*
+ * Observation merging in the preconditioner (App. A.3).  group[nu] (host array of nobs ints)
+ * assigns band nu to merged row group[nu] of U; the ids must be 0..G-1 (each used), and the
+ * bands of a row must share one grid handle.  Afterwards M_PI (cmbws_apply_precond, and the
+ * M_PI part of precond 1 and 2 of the solvers) runs one SHT pair per row instead of per band:
+ *   row G of U, per l: the best rank-one fit u_G u_G^T of sum_{nu in G} U_nu^T U_nu (for rows
+ *     U_nu = gamma_nu U_1, as for detector splits of one channel, u_G = sqrt(sum gamma^2) U_1,
+ *     the exact merge; the paper prints the factor as (gamma + 1)^1/2);
+ *   T_G^+ = alpha_G^2 Y^T W N_G W Y with the co-added inverse noise tau_G = sum_{nu in G} tau_nu
+ *     and alpha_G of Eq. optimal-alpha (for exact splits T_G^+ equals each band's T^+, and the
+ *     merged preconditioner equals M_PI).
+ * A is unchanged.  group = NULL restores one row per band.  cmbws_model_info then reports
+ * nsht_M = 2 G.  Synchronises `stream`.
+ * Errors: CMBWS_ERR_ARG (ids outside 0..nobs-1, an unused id, bands of a row on different
+ * grids), CMBWS_ERR_SINGULAR (a component without data or prior at some l).
+ */
+int cmbws_model_merge_precond(cmbws_model m, const int* group, void* stream);
 
 /* z = M_add r = M_PI r + sum of the model's mask preconditioners (Sec. 4.2).  r, z distinct. */
 int cmbws_apply_M_add(cmbws_model m, const double* r, double* z, void* stream);

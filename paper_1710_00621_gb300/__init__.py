@@ -42,6 +42,7 @@ from .binding import (  # noqa: F401
     cmbws_model_create,
     cmbws_model_destroy,
     cmbws_model_info,
+    cmbws_model_merge_precond,
     cmbws_plan_grid,
     cmbws_powerlaw_mixing,
     cmbws_profile_enable,

@@ -99,6 +99,7 @@ def load_library(path=None):
     lib.cmbws_model_add_mask_precond.argtypes = [vp, i, i, vp, i, vp]
     lib.cmbws_apply_M_add.argtypes = [vp, vp, vp, vp]
     lib.cmbws_apply_M_diag.argtypes = [vp, vp, vp, vp]
+    lib.cmbws_model_merge_precond.argtypes = [vp, ctypes.POINTER(i), vp]
     u64 = ctypes.c_uint64
     lib.cmbws_draw.argtypes = [u64, u64, u64, ctypes.c_int64, ctypes.c_int64, i, vp, vp]
     lib.cmbws_cr_rhs.argtypes = [vp, ctypes.POINTER(vp), u64, u64, vp, vp]
@@ -345,6 +346,24 @@ def cmbws_rhs(model, d, b, omega1=None, omega2=None, stream=None):
     w2 = _dptr(omega2, model.nvec, "omega2") if omega2 is not None else ctypes.c_void_p()
     _check(load_library().cmbws_rhs(model.handle, dp, w1, w2, _dptr(b, model.nvec, "b"),
                                     _stream(stream)))
+
+
+def cmbws_model_merge_precond(model, group, stream=None):
+    """Merge bands in the preconditioner (App. A.3): group[nu] = merged row of band nu
+    (ids 0..G-1, bands of a row on one grid), or None for one row per band."""
+    lib = load_library()
+    if group is None:
+        gp = ctypes.POINTER(ctypes.c_int)()
+    else:
+        if len(group) != model.nobs:
+            raise ValueError(f"group needs {model.nobs} entries")
+        gp = (ctypes.c_int * model.nobs)(*[int(g) for g in group])
+    _check(lib.cmbws_model_merge_precond(model.handle, gp, _stream(stream)))
+    nvec = ctypes.c_int64()
+    na = ctypes.c_int()
+    nm = ctypes.c_int()
+    _check(lib.cmbws_model_info(model.handle, ctypes.byref(nvec), ctypes.byref(na), ctypes.byref(nm)))
+    model.nsht_M = nm.value
 
 
 CMBWS_DRAW_NORMAL = 0

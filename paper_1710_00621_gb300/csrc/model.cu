@@ -575,7 +575,49 @@ int Model::apply_A(const double* x, double* y, int prec, cudaStream_t s) {
   return CMBWS_OK;
 }
 
+int Model::apply_precond_merged(const double* r, double* z, int prec, cudaStream_t s) {
+  MergedPrec& P = *merged;
+  HarmDev h = harm();
+  h.nobs = P.nrow;  // rows of U' in place of the bands
+  h.Up = P.d_Up.as<double>();
+  BandDev bd{};
+  for (int row = 0; row < P.nrow; ++row) {
+    const Group& G = P.groups[P.row_group[row]];
+    const int j = P.row_slot[row];
+    const int64_t nlm = nlm_of(G.grid->lmax);
+    bd.L[row] = G.grid->lmax;
+    bd.out[row] = G.out.as<double2>() + j * nlm;
+    bd.c[row] = G.grid->c64.as<double>();
+    bd.alm[row] = (char*)G.alm.p + (size_t)j * nlm * 2 * prec_size(prec);
+  }
+  {
+    dim3 grd((Lall + 1 + 127) / 128, Lall + 1);
+    ProfScope ps(PROF_HARM, s, is_f32(prec) ? 0 : 1);
+    if (!is_f32(prec)) k_pinv_T<double2><<<grd, 128, 0, s>>>(h, bd, r, tprior.as<double>(), Lall);
+    else k_pinv_T<float2><<<grd, 128, 0, s>>>(h, bd, r, tprior.as<double>(), Lall);
+    CMBWS_LAUNCH_CHECK();
+  }
+  for (Group& G : P.groups) {
+    const Grid& g = *G.grid;
+    const void* pix[kMaxMaps];
+    for (int j = 0; j < G.nmaps; ++j)
+      pix[j] = !is_f32(prec) ? P.pixM64[G.bands[j]].p : P.pixM32[G.bands[j]].p;
+    CMBWS_TRY(legendre_synth(g, prec, G.nmaps, G.alm.p, G.F.p, s));
+    CMBWS_TRY(ringfft_fused(g, prec, G.nmaps, G.F.p, pix, s));
+    CMBWS_TRY(legendre_adjoint(g, prec, G.nmaps, G.F.p, part.p, part.bytes, G.out.as<double>(), s));
+  }
+  {
+    dim3 grd((Lcomp + 1 + 127) / 128, Lcomp + 1);
+    ProfScope ps(PROF_HARM, s, is_f32(prec) ? 0 : 1);
+    k_pinv<<<grd, 128, 0, s>>>(h, bd, tprior.as<double>(), z, Lcomp);
+    CMBWS_LAUNCH_CHECK();
+  }
+  n_sht += nsht_M;
+  return CMBWS_OK;
+}
+
 int Model::apply_precond(const double* r, double* z, int prec, cudaStream_t s) {
+  if (merged) return apply_precond_merged(r, z, prec, s);
   const HarmDev h = harm();
   const BandDev bd = bands_dev(prec);
   {
@@ -877,6 +919,10 @@ int model_create(const cmbws_model_desc* desc, int prec, cudaStream_t s, Model**
   CMBWS_TRY(M->d_clOff.upload(clOff.data(), nc * 8));
   CMBWS_TRY(M->d_Up.upload(Up.data(), Up.size() * 8));
   CMBWS_TRY(M->d_qpre.upload(qpre.data(), qpre.size() * 8));
+  M->beam_h = beam;
+  M->cisq_h = cisq;
+  M->qpre_h = qpre;
+  M->clOff_h = clOff;
 
   // ---- workspaces ----
   size_t part_bytes = 0;

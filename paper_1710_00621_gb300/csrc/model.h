@@ -9,7 +9,7 @@
 namespace cmbws {
 
 constexpr int kMaxComp = 8;    // components
-constexpr int kMaxBands = 16;  // observations
+constexpr int kMaxBands = 64;  // observations (e.g. detector subsets of the frequency channels)
 constexpr int kMaxMaps = 8;    // bands transformed together on one grid
 
 struct MaskMG;  // mask-restricted multigrid preconditioner (maskmg.cu)
@@ -71,6 +71,18 @@ struct Group {
   DevMem out;  // [nmaps][nlm] complex FP64
 };
 
+// Observation merging in the preconditioner (App. A.3, merge.cu): M_PI over merged rows of U
+// (groups of bands on one grid) instead of one row per band.
+struct MergedPrec {
+  int nrow = 0;
+  std::vector<int> row_of_band;
+  std::vector<Group> groups;              // rows sharing a grid; bands[] holds row ids
+  std::vector<int> row_group, row_slot;
+  std::vector<DevMem> pixM64, pixM32;     // T^+ pixel factors alpha_G^2 w^2 / tau_G per row
+  std::vector<double> alpha;              // alpha_G (Eq. optimal-alpha of tau_G)
+  DevMem d_Up;                            // U'^+ [Lup+1][ncomp][nrow + ncomp]
+};
+
 struct Model {
   int ncomp = 0, nobs = 0, prec = 0;
   std::vector<int> Lk, Lnu;
@@ -113,6 +125,13 @@ struct Model {
   DevMem cr_w, cr_b;
   int cr_draw_rhs(const double* const* d, uint64_t seed, uint64_t sample, double* b,
                   cudaStream_t s);
+
+  // observation merging (merge.cu): when set, apply_precond runs over the merged rows
+  std::unique_ptr<MergedPrec> merged;
+  std::vector<double> beam_h, cisq_h, qpre_h;  // host copies of b_{nu,l}, C^-1/2, q (U rows)
+  std::vector<int64_t> clOff_h;
+  int merge_precond(const int* group, cudaStream_t s);
+  int apply_precond_merged(const double* r, double* z, int prec, cudaStream_t s);
 
   // mask-restricted preconditioners (Sec. 4), applied with M_PI when precond = 2
   std::vector<MaskMG*> masks;
