@@ -242,6 +242,18 @@ int cmbws_model_add_mask_precond(cmbws_model m, int comp, int nside, const doubl
  */
 int cmbws_model_merge_precond(cmbws_model m, const int* group, void* stream);
 
+/*
+ * V-cycle of the model's mask preconditioners (Sec. 4.4, Fig. code:mg).
+ *   kind 0 (default): the basic V-cycle, 8 SHTs per level.
+ *   kind 1: the optimized V-cycle: I_h^H = Y_H R_H Y_h^T W_h and G_h = P Y_h D_h Y_h^T P
+ *     inserted so that restriction and interpolation share transforms with G_h, and
+ *     J = Y_h^T W_h P Y_h approximated by I as the paper does; 6 SHTs per level, two of them
+ *     at the coarser level's band-limit on the finer grid (planned on first use, kept by the
+ *     preconditioner).  Still a symmetric operator; not identical to the basic cycle.
+ * Errors: CMBWS_ERR_ARG for another kind.
+ */
+int cmbws_model_set_vcycle(cmbws_model m, int kind);
+
 /* z = M_add r = M_PI r + sum of the model's mask preconditioners (Sec. 4.2).  r, z distinct. */
 int cmbws_apply_M_add(cmbws_model m, const double* r, double* z, void* stream);
 

@@ -20,6 +20,8 @@ from .binding import (  # noqa: F401
     CMBWS_GRID_GL,
     CMBWS_GRID_HEALPIX,
     CMBWS_TF32,
+    CMBWS_VCYCLE_BASIC,
+    CMBWS_VCYCLE_OPTIMIZED,
     CmbwsError,
     CgOpts,
     CgReport,
@@ -43,6 +45,7 @@ from .binding import (  # noqa: F401
     cmbws_model_destroy,
     cmbws_model_info,
     cmbws_model_merge_precond,
+    cmbws_model_set_vcycle,
     cmbws_plan_grid,
     cmbws_powerlaw_mixing,
     cmbws_profile_enable,

@@ -136,15 +136,22 @@ struct MgLevel {
   std::vector<uint8_t> mask_h;
   DevMem mask, d, rH, idx, Gp, vb, vb2;
   DevMem b, x, t, y, a;             // maps (b, x, t, y) and packed coefficients a
+  // optimized V-cycle (planned on first use): this level's grid at the next level's
+  // band-limit L_H, packed coefficients at L_H, and the factors 1 and -d_l (l <= L_H)
+  Grid* gH = nullptr;
+  DevMem aH, ones, dneg;
 };
 
 struct MaskMG {
   int comp = 0, Lk = 0, L0 = 0, prec = CMBWS_FP64;
   std::vector<MgLevel> lv;
   DevMem r0;
+  long long nsht = 0;  // SHTs of the applications (the paper's counting)
   ~MaskMG() {
-    for (MgLevel& l : lv)
+    for (MgLevel& l : lv) {
       if (l.g) cmbws_grid_destroy(reinterpret_cast<cmbws_grid>(l.g));
+      if (l.gH) cmbws_grid_destroy(reinterpret_cast<cmbws_grid>(l.gH));
+    }
   }
 };
 
@@ -156,12 +163,20 @@ Model::~Model() {
 
 namespace {
 
+int synth_on(MaskMG& mg, Grid* g, const double* a, double* map, cudaStream_t s) {
+  ++mg.nsht;
+  return cmbws_sht_synth(reinterpret_cast<cmbws_grid>(g), (cmbws_prec)mg.prec, a, map, 1, s);
+}
+int adjoint_on(MaskMG& mg, Grid* g, const double* map, double* a, int weighted, cudaStream_t s) {
+  ++mg.nsht;
+  return cmbws_sht_analysis(reinterpret_cast<cmbws_grid>(g), (cmbws_prec)mg.prec, map, a, 1,
+                            weighted, s);
+}
 int synth(MaskMG& mg, MgLevel& h, const double* a, double* map, cudaStream_t s) {
-  return cmbws_sht_synth(reinterpret_cast<cmbws_grid>(h.g), (cmbws_prec)mg.prec, a, map, 1, s);
+  return synth_on(mg, h.g, a, map, s);
 }
 int adjoint(MaskMG& mg, MgLevel& h, const double* map, double* a, int weighted, cudaStream_t s) {
-  return cmbws_sht_analysis(reinterpret_cast<cmbws_grid>(h.g), (cmbws_prec)mg.prec, map, a, 1,
-                            weighted, s);
+  return adjoint_on(mg, h.g, map, a, weighted, s);
 }
 
 int lincomb(MgLevel& h, double* out, double ca, const double* a, double cb, const double* b,
@@ -188,19 +203,22 @@ int apply_G(MaskMG& mg, MgLevel& h, const double* x, double* y, cudaStream_t s) 
   return lincomb(h, y, 1.0, y, 0.0, nullptr, s);
 }
 
+// bottom level: x = G^+ b with the dense pseudo-inverse on the mask pixels
+int bottom_solve(MgLevel& h, const double* b, double* x, cudaStream_t s) {
+  ProfScope ps(PROF_HARM, s, 1);
+  CMBWS_CUDA(cudaMemsetAsync(x, 0, h.npix * 8, s));
+  k_gather<<<nblk(h.nb), 256, 0, s>>>(b, h.idx.as<int>(), h.nb, h.vb.as<double>());
+  k_dense_mv<<<nblk(h.nb, 8), 256, 0, s>>>(h.Gp.as<double>(), h.nb, h.vb.as<double>(),
+                                          h.vb2.as<double>());
+  k_scatter<<<nblk(h.nb), 256, 0, s>>>(h.vb2.as<double>(), h.idx.as<int>(), h.nb, x);
+  CMBWS_LAUNCH_CHECK();
+  return CMBWS_OK;
+}
+
 // x = V-cycle approximation of G_k^-1 b (basic V-cycle of Sec. 4.4)
 int vcycle(MaskMG& mg, int k, const double* b, double* x, cudaStream_t s) {
   MgLevel& h = mg.lv[k];
-  if (h.nb > 0) {  // bottom: dense pseudo-inverse on the mask pixels
-    ProfScope ps(PROF_HARM, s, 1);
-    CMBWS_CUDA(cudaMemsetAsync(x, 0, h.npix * 8, s));
-    k_gather<<<nblk(h.nb), 256, 0, s>>>(b, h.idx.as<int>(), h.nb, h.vb.as<double>());
-    k_dense_mv<<<nblk(h.nb, 8), 256, 0, s>>>(h.Gp.as<double>(), h.nb, h.vb.as<double>(),
-                                            h.vb2.as<double>());
-    k_scatter<<<nblk(h.nb), 256, 0, s>>>(h.vb2.as<double>(), h.idx.as<int>(), h.nb, x);
-    CMBWS_LAUNCH_CHECK();
-    return CMBWS_OK;
-  }
+  if (h.nb > 0) return bottom_solve(h, b, x, s);
   MgLevel& H = mg.lv[k + 1];
   double* t = h.t.as<double>();
   double* y = h.y.as<double>();
@@ -223,16 +241,75 @@ int vcycle(MaskMG& mg, int k, const double* b, double* x, cudaStream_t s) {
   return lincomb(h, x, 1.0, x, h.smooth, t, s);
 }
 
+// The optimized V-cycle (Sec. 4.4, Fig. code:mg): I_h^H = Y_H R_H Y_h^T W_h and
+// G_h = P Y_h D_h Y_h^T P inserted so that restriction and interpolation share transforms
+// with G_h, and J = Y_h^T W_h P Y_h approximated by I as in the paper: 6 SHTs per level
+// (Y_h^T at L_h, Y_h^T W_h at L_H, Y_H and Y_H^T, Y_h at L_H, Y_h at L_h).  b and x are
+// zero outside the mask.
+int vcycle_opt(MaskMG& mg, int k, const double* b, double* x, cudaStream_t s) {
+  MgLevel& h = mg.lv[k];
+  if (h.nb > 0) return bottom_solve(h, b, x, s);
+  MgLevel& H = mg.lv[k + 1];
+  double* t = h.t.as<double>();
+  double* y = h.y.as<double>();
+  double* u = h.a.as<double>();    // Y_h^T x, kept for the post-smoothing
+  double* aH = h.aH.as<double>();
+  CMBWS_TRY(lincomb(h, x, h.smooth, b, 0.0, nullptr, s));              // pre-smoothing
+  CMBWS_TRY(adjoint(mg, h, x, u, 0, s));                                // u = Y_h^T x
+  CMBWS_TRY(adjoint_on(mg, h.gH, b, aH, 1, s));                         // Y_h^T W_h b, l <= L_H
+  CMBWS_TRY(xfer(u, h.L, aH, H.L, h.dneg.as<double>(), 1, s));          //   - D_h u
+  CMBWS_TRY(xfer(aH, H.L, H.a.as<double>(), H.L, h.rH.as<double>(), 0, s));
+  CMBWS_TRY(synth(mg, H, H.a.as<double>(), H.b.as<double>(), s));       // r_H = P Y_H R_H r~
+  CMBWS_TRY(lincomb(H, H.b.as<double>(), 1.0, H.b.as<double>(), 0.0, nullptr, s));
+  CMBWS_TRY(vcycle_opt(mg, k + 1, H.b.as<double>(), H.x.as<double>(), s));
+  CMBWS_TRY(adjoint(mg, H, H.x.as<double>(), H.a.as<double>(), 0, s));  // c~ = R_H Y_H^T c_H
+  CMBWS_TRY(xfer(H.a.as<double>(), H.L, aH, H.L, h.rH.as<double>(), 0, s));
+  CMBWS_TRY(synth_on(mg, h.gH, aH, t, s));                              // x += P W_h Y_h c~
+  CMBWS_TRY(lincomb(h, x, 1.0, x, h.w, t, s));
+  CMBWS_TRY(xfer(aH, H.L, u, h.L, h.ones.as<double>(), 1, s));          // u + J c~, J ~ I
+  CMBWS_TRY(xfer(u, h.L, u, h.L, h.d.as<double>(), 0, s));
+  CMBWS_TRY(synth(mg, h, u, y, s));                                     // G_h x
+  CMBWS_TRY(lincomb(h, t, 1.0, b, -1.0, y, s));                         // post-smoothing
+  return lincomb(h, x, 1.0, x, h.smooth, t, s);
+}
+
+// plan the fine grids at the coarse band-limits and the factors of the optimized cycle
+int prepare_opt(MaskMG& mg) {
+  for (size_t k = 0; k + 1 < mg.lv.size(); ++k) {
+    MgLevel& h = mg.lv[k];
+    if (h.nb > 0 || h.gH) continue;
+    const int LH = mg.lv[k + 1].L;
+    cmbws_grid g = nullptr;
+    CMBWS_TRY(cmbws_plan_grid(CMBWS_GRID_HEALPIX, h.nside, LH, &g));
+    std::vector<double> ones(LH + 1, 1.0), dneg(LH + 1);
+    for (int l = 0; l <= LH; ++l) dneg[l] = -h.d_h[l];
+    CMBWS_TRY(h.ones.upload(ones.data(), ones.size() * 8));
+    CMBWS_TRY(h.dneg.upload(dneg.data(), dneg.size() * 8));
+    CMBWS_TRY(h.aH.alloc((size_t)(LH + 1) * (LH + 1) * 8));
+    h.gH = reinterpret_cast<Grid*>(g);
+  }
+  return CMBWS_OK;
+}
+
 }  // namespace
 
 // z += M_mask r on the preconditioner's component (stacked vectors)
-int mask_mg_apply(MaskMG& mg, const Model& M, const double* r, double* z, cudaStream_t s) {
+int mask_mg_apply(MaskMG& mg, Model& M, const double* r, double* z, cudaStream_t s) {
+  if (M.vcycle == 1) CMBWS_TRY(prepare_opt(mg));
+  const long long n0 = mg.nsht;
+  struct Count {
+    MaskMG& mg;
+    Model& M;
+    long long n0;
+    ~Count() { M.n_sht += mg.nsht - n0; }
+  } count{mg, M, n0};
   MgLevel& h = mg.lv[0];
   const int64_t off = M.compOff[mg.comp];
   CMBWS_TRY(xfer(r + off, mg.Lk, h.a.as<double>(), mg.L0, mg.r0.as<double>(), 0, s));
   CMBWS_TRY(synth(mg, h, h.a.as<double>(), h.b.as<double>(), s));           // Z r
   CMBWS_TRY(lincomb(h, h.b.as<double>(), 1.0, h.b.as<double>(), 0.0, nullptr, s));
-  CMBWS_TRY(vcycle(mg, 0, h.b.as<double>(), h.x.as<double>(), s));
+  if (M.vcycle == 1) CMBWS_TRY(vcycle_opt(mg, 0, h.b.as<double>(), h.x.as<double>(), s));
+  else CMBWS_TRY(vcycle(mg, 0, h.b.as<double>(), h.x.as<double>(), s));
   CMBWS_TRY(adjoint(mg, h, h.x.as<double>(), h.a.as<double>(), 0, s));      // Z^T x
   return xfer(h.a.as<double>(), mg.L0, z + off, mg.Lk, mg.r0.as<double>(), 1, s);
 }
@@ -404,6 +481,17 @@ extern "C" int cmbws_model_add_mask_precond(cmbws_model mh, int comp, int nside,
   if (st != CMBWS_OK) return st;
   M->masks.push_back(mg);
   CMBWS_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  return CMBWS_OK;
+}
+
+extern "C" int cmbws_model_set_vcycle(cmbws_model mh, int kind) {
+  clear_error();
+  Model* M = reinterpret_cast<Model*>(mh);
+  if (!M || (kind != 0 && kind != 1)) {
+    set_error("cmbws_model_set_vcycle: invalid arguments (kind 0 = basic, 1 = optimized)");
+    return CMBWS_ERR_ARG;
+  }
+  M->vcycle = kind;
   return CMBWS_OK;
 }
 

@@ -135,6 +135,7 @@ struct Model {
 
   // mask-restricted preconditioners (Sec. 4), applied with M_PI when precond = 2
   std::vector<MaskMG*> masks;
+  int vcycle = 0;  // V-cycle of the mask preconditioners: 0 basic, 1 optimized (J ~ I)
   ~Model();
 
   HarmDev harm() const;
@@ -159,6 +160,6 @@ bool pinv_jacobi(const std::vector<double>& Uin, int nr, int nc, double rcond,
                  std::vector<double>& out);
 
 void mask_mg_destroy(MaskMG* p);
-int mask_mg_apply(MaskMG& mg, const Model& M, const double* r, double* z, cudaStream_t s);
+int mask_mg_apply(MaskMG& mg, Model& M, const double* r, double* z, cudaStream_t s);
 
 }  // namespace cmbws
