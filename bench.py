@@ -353,6 +353,24 @@ def batched_measure(nprob, tol, fmax=0.3, max_bottom=200):
     torch.cuda.synchronize()
     tseq = time.perf_counter() - t0
     print("[batched] timed solves done", file=sys.stderr, flush=True)
+    # the batched solves again with every operator apply replayed from a CUDA graph
+    x_eager = [x.clone() for x in xs]
+    for m in models:
+        cw.cmbws_model_set_graphs(m, True)
+    for x in xs:
+        x.zero_()
+    cw.cmbws_cg_solve_batched(models, bs, xs, check=False, **kw)   # captures the graphs
+    torch.cuda.synchronize()
+    for x in xs:
+        x.zero_()
+    t0 = time.perf_counter()
+    reps_g = cw.cmbws_cg_solve_batched(models, bs, xs, check=False, **kw)
+    torch.cuda.synchronize()
+    tbg = time.perf_counter() - t0
+    same = all(bool(torch.equal(a, c)) for a, c in zip(xs, x_eager))
+    for m in models:
+        cw.cmbws_model_set_graphs(m, False)
+    print("[batched] graph-replayed solves done", file=sys.stderr, flush=True)
     # the same masked problems with M_PI alone, on the three largest masks (budget-bounded)
     big = sorted(range(len(models)), key=lambda i: -masked[i])[:3]
     cmp = []
@@ -364,7 +382,11 @@ def batched_measure(nprob, tol, fmax=0.3, max_bottom=200):
                     "M_PI_certified": r1["status"] == 0, "iters_M_add": reps[i]["iters"]})
     its = [r["iters"] for r in reps]
     return {"nprob": nprob, "batched_s": round(tb, 3), "sequential_s": round(tseq, 3),
-            "speedup": round(tseq / tb, 2), "iters_min_median_max": [min(its), int(np.median(its)), max(its)],
+            "speedup": round(tseq / tb, 2),
+            "batched_graphs_s": round(tbg, 3), "speedup_graphs_vs_sequential": round(tseq / tbg, 2),
+            "graphs_bitwise_equal_to_eager": same,
+            "graphs_all_certified": all(r["status"] == 0 and r["rel_res"] <= tol for r in reps_g),
+            "iters_min_median_max": [min(its), int(np.median(its)), max(its)],
             "all_certified": all(r["status"] == 0 and r["rel_res"] <= tol for r in reps),
             "n_certified": sum(r["status"] == 0 and r["rel_res"] <= tol for r in reps),
             "setup_s": round(t_setup, 1), "M_PI_vs_M_add_largest_masks": cmp,
@@ -501,7 +523,21 @@ def tiny_measure(reps=5):
         x.zero_()
         r = cw.cmbws_cg_solve(m64, b, x, tol=1e-8, maxiter=1000)
     torch.cuda.synchronize()
-    return {"s": round((time.perf_counter() - t0) / reps, 5), "iters": r["iters"],
+    t_eager = (time.perf_counter() - t0) / reps
+    x_eager = x.clone()
+    cw.cmbws_model_set_graphs(m64, True)
+    x.zero_()
+    cw.cmbws_cg_solve(m64, b, x, tol=1e-8, maxiter=1000)   # captures the graphs
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        x.zero_()
+        rg = cw.cmbws_cg_solve(m64, b, x, tol=1e-8, maxiter=1000)
+    torch.cuda.synchronize()
+    t_graph = (time.perf_counter() - t0) / reps
+    cw.cmbws_model_set_graphs(m64, False)
+    return {"s": round(t_eager, 5), "s_graphs": round(t_graph, 5), "iters": r["iters"],
+            "iters_graphs": rg["iters"], "graphs_bitwise_equal": bool(torch.equal(x, x_eager)),
             "rel_res": r["rel_res"], "workload": work.name + ", FP64, M_PI, tol 1e-8"}
 
 

@@ -364,6 +364,19 @@ int cmbws_cg_solve(cmbws_model m, const double* b, double* x, const cmbws_cg_opt
                    cmbws_cg_report* report, void* stream);
 
 /*
+ * CUDA graphs for the operator applies inside the solvers (on = 1; default 0).  Each apply of
+ * A and of the preconditioner in PCG is tens to hundreds of kernel launches (per grid group:
+ * Legendre synthesis, ring FFT, Legendre adjoint; harmonic-space kernels; the multigrid
+ * levels of M_add); with graphs on, the second apply for a given operator, precision and
+ * pair of buffers is captured into a CUDA graph and later applies replay it with one launch.
+ * Results are bitwise those of the eager applies.  Graphs are not used while per-stage
+ * profiling is on, and are dropped when the model's preconditioners change
+ * (cmbws_model_add_mask_precond, cmbws_model_merge_precond, cmbws_model_set_vcycle) or when
+ * graphs are switched off.
+ */
+int cmbws_model_set_graphs(cmbws_model m, int on);
+
+/*
  * Solve nprob independent systems A_i x_i = b_i (each as cmbws_cg_solve) concurrently.
  *   models: [nprob] distinct models (each owns its workspace); b, x: host arrays [nprob] of
  *   device stacked vectors.  reports: [nprob] or NULL.

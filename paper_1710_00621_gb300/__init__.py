@@ -45,6 +45,7 @@ from .binding import (  # noqa: F401
     cmbws_model_destroy,
     cmbws_model_info,
     cmbws_model_merge_precond,
+    cmbws_model_set_graphs,
     cmbws_model_set_vcycle,
     cmbws_plan_grid,
     cmbws_powerlaw_mixing,

@@ -101,6 +101,7 @@ def load_library(path=None):
     lib.cmbws_apply_M_diag.argtypes = [vp, vp, vp, vp]
     lib.cmbws_model_merge_precond.argtypes = [vp, ctypes.POINTER(i), vp]
     lib.cmbws_model_set_vcycle.argtypes = [vp, i]
+    lib.cmbws_model_set_graphs.argtypes = [vp, i]
     u64 = ctypes.c_uint64
     lib.cmbws_draw.argtypes = [u64, u64, u64, ctypes.c_int64, ctypes.c_int64, i, vp, vp]
     lib.cmbws_cr_rhs.argtypes = [vp, ctypes.POINTER(vp), u64, u64, vp, vp]
@@ -347,6 +348,11 @@ def cmbws_rhs(model, d, b, omega1=None, omega2=None, stream=None):
     w2 = _dptr(omega2, model.nvec, "omega2") if omega2 is not None else ctypes.c_void_p()
     _check(load_library().cmbws_rhs(model.handle, dp, w1, w2, _dptr(b, model.nvec, "b"),
                                     _stream(stream)))
+
+
+def cmbws_model_set_graphs(model, on):
+    """Replay the solvers' operator applies from CUDA graphs (True) or launch them eagerly."""
+    _check(load_library().cmbws_model_set_graphs(model.handle, 1 if on else 0))
 
 
 CMBWS_VCYCLE_BASIC = 0

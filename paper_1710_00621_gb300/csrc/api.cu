@@ -1,5 +1,6 @@
 // Error state, device buffers and the SHT entry points of the C ABI
 // (synthesis Y, analysis Y^T W and adjoint synthesis Y^T; Sec. 2.1, Sec. 3.2).
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <mutex>
@@ -55,7 +56,7 @@ struct ProfRec {
   cudaEvent_t a, b;
 };
 std::mutex g_prof_mu;
-bool g_prof_on = false;
+std::atomic<bool> g_prof_on{false};
 std::vector<ProfRec> g_prof;
 std::vector<cudaEvent_t> g_pool;
 
@@ -74,8 +75,11 @@ cudaEvent_t pool_get() {
 }
 }  // namespace
 
+bool prof_enabled() { return g_prof_on.load(std::memory_order_relaxed); }
+
 ProfScope::ProfScope(int stage, cudaStream_t s_, int arith, double flops_)
     : slot(stage + PROF_N * arith), flops(flops_), s(s_) {
+  if (!g_prof_on.load(std::memory_order_relaxed)) return;  // no lock on the common path
   std::lock_guard<std::mutex> lk(g_prof_mu);
   if (!g_prof_on) return;
   a = pool_get();

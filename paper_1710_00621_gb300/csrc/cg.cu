@@ -167,6 +167,74 @@ static int precondition(Model& M, int use_M, int prec, const double* r, double* 
   return CMBWS_OK;
 }
 
+void Model::drop_graphs() {
+  for (OpGraph& g : graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  graphs.clear();
+}
+
+// One operator apply of PCG through a CUDA graph when the model asks for it: the launches of
+// an apply (tens to hundreds of kernels for small problems) are replayed with one graph
+// launch.  The first apply for a (operator, precision, in, out) runs eagerly (it performs any
+// lazy allocation or table build), the second is captured and instantiated, later ones
+// replay.  Capture is skipped while per-stage profiling is on (its events cannot be timed
+// inside a graph) and falls back to the eager apply whenever capture or instantiation fails.
+template <typename F>
+static int run_op(Model& M, int op, int prec, const double* in, double* out, cudaStream_t s,
+                  F&& eager) {
+  if (!M.use_graphs || prof_enabled()) return eager();
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return eager();
+  }
+  Model::OpGraph* g = nullptr;
+  for (Model::OpGraph& e : M.graphs)
+    if (e.op == op && e.prec == prec && e.in == in && e.out == out) g = &e;
+  if (!g) {
+    M.graphs.emplace_back();
+    g = &M.graphs.back();
+    g->op = op;
+    g->prec = prec;
+    g->in = in;
+    g->out = out;
+  }
+  if (g->failed) return eager();
+  if (g->exec) {
+    CMBWS_CUDA(cudaGraphLaunch(g->exec, s));
+    M.n_sht += g->nsht;
+    return CMBWS_OK;
+  }
+  if (g->calls++ == 0) return eager();
+  const long long n0 = M.n_sht;
+  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    g->failed = true;
+    return eager();
+  }
+  const int st = eager();
+  cudaGraph_t graph = nullptr;
+  cudaError_t ce = cudaStreamEndCapture(s, &graph);
+  const long long dn = M.n_sht - n0;
+  M.n_sht = n0;  // the captured launches have not run
+  cudaGraphExec_t ex = nullptr;
+  if (st == CMBWS_OK && ce == cudaSuccess && graph) ce = cudaGraphInstantiate(&ex, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (st != CMBWS_OK || ce != cudaSuccess || !ex) {
+    cudaGetLastError();
+    clear_error();
+    g->failed = true;
+    return eager();
+  }
+  g->exec = ex;
+  g->nsht = dn;
+  CMBWS_CUDA(cudaGraphLaunch(ex, s));
+  M.n_sht += dn;
+  return CMBWS_OK;
+}
+
+enum { OP_APPLY_A = 0, OP_PRECOND = 1 };
+
 // PCG on A d = r0 (d starts at zero), operator precision `prec`; stops when
 // ||r|| <= stop_abs or after maxit iterations.  r0 is overwritten with the final residual.
 static int pcg_core(Solver& S, int prec, int use_M, double* d, double* r, double stop_abs, int maxit,
@@ -182,12 +250,17 @@ static int pcg_core(Solver& S, int prec, int use_M, double* d, double* r, double
   *rr_out = rr;
   *iters = 0;
   if (std::sqrt(rr) <= stop_abs) return CMBWS_OK;
-  CMBWS_TRY(precondition(M, use_M, prec, r, z, n, S.s));
+  auto precond = [&]() {
+    if (!use_M) return precondition(M, use_M, prec, r, z, n, S.s);
+    return run_op(M, OP_PRECOND + 16 * use_M, prec, r, z, S.s,
+                  [&]() { return precondition(M, use_M, prec, r, z, n, S.s); });
+  };
+  CMBWS_TRY(precond());
   CMBWS_CUDA(cudaMemcpyAsync(p, z, n * 8, cudaMemcpyDeviceToDevice, S.s));
   double rz;
   CMBWS_TRY(S.dot(r, z, &rz));
   for (int it = 0; it < maxit; ++it) {
-    CMBWS_TRY(M.apply_A(p, q, prec, S.s));
+    CMBWS_TRY(run_op(M, OP_APPLY_A, prec, p, q, S.s, [&]() { return M.apply_A(p, q, prec, S.s); }));
     double pq;
     CMBWS_TRY(S.dot(p, q, &pq));
     if (!(pq > 0.0) || !std::isfinite(pq) || !std::isfinite(rz)) {
@@ -212,7 +285,7 @@ static int pcg_core(Solver& S, int prec, int use_M, double* d, double* r, double
       set_error("CG: wall-clock budget of %g s exhausted", timeout);
       return CMBWS_ERR_TIMEOUT;
     }
-    CMBWS_TRY(precondition(M, use_M, prec, r, z, n, S.s));
+    CMBWS_TRY(precond());
     double rz_new;
     CMBWS_TRY(S.dot(r, z, &rz_new));
     const double beta = rz_new / rz;
@@ -347,6 +420,18 @@ extern "C" int cmbws_cg_solve(cmbws_model mh, const double* b, double* x, const 
   rep.status = st;
   if (report) *report = rep;
   return st;
+}
+
+extern "C" int cmbws_model_set_graphs(cmbws_model mh, int on) {
+  clear_error();
+  Model* M = reinterpret_cast<Model*>(mh);
+  if (!M) {
+    set_error("cmbws_model_set_graphs: invalid model");
+    return CMBWS_ERR_ARG;
+  }
+  if (!on) M->drop_graphs();
+  M->use_graphs = on != 0;
+  return CMBWS_OK;
 }
 
 extern "C" int cmbws_cg_solve_batched(const cmbws_model* models, int nprob, const double* const* b,

@@ -224,6 +224,7 @@ int legendre_adj_df_ck(const Grid& g, int nm, const void* F, void* eo, double* o
 // The limit only ever grows, so concurrent launches with different sizes (several host
 // threads, cmbws_cg_solve_batched) never see it lowered under them.
 int ensure_dyn_smem(const void* func, size_t bytes);
+bool prof_enabled();  // per-stage CUDA-event profiling switched on (cmbws_profile_enable)
 
 // ---- kernel timing (api.cu): CUDA events around launches while enabled ----
 // Stages; a record's slot is stage + PROF_N * arith, arith 0 = FP32, 1 = FP64,

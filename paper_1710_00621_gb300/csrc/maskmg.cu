@@ -158,6 +158,7 @@ struct MaskMG {
 void mask_mg_destroy(MaskMG* p) { delete p; }
 
 Model::~Model() {
+  drop_graphs();
   for (MaskMG* p : masks) mask_mg_destroy(p);
 }
 
@@ -479,6 +480,7 @@ extern "C" int cmbws_model_add_mask_precond(cmbws_model mh, int comp, int nside,
   MaskMG* mg = nullptr;
   const int st = mask_mg_build(*M, comp, nside, mask, max_bottom, (cudaStream_t)stream, &mg);
   if (st != CMBWS_OK) return st;
+  M->drop_graphs();
   M->masks.push_back(mg);
   CMBWS_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
   return CMBWS_OK;
@@ -491,6 +493,7 @@ extern "C" int cmbws_model_set_vcycle(cmbws_model mh, int kind) {
     set_error("cmbws_model_set_vcycle: invalid arguments (kind 0 = basic, 1 = optimized)");
     return CMBWS_ERR_ARG;
   }
+  if (M->vcycle != kind) M->drop_graphs();
   M->vcycle = kind;
   return CMBWS_OK;
 }

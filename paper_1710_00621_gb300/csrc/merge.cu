@@ -117,6 +117,7 @@ void sym_top_eig(std::vector<double> S, int n, double* lam, std::vector<double>&
 }  // namespace
 
 int Model::merge_precond(const int* group, cudaStream_t s) {
+  drop_graphs();  // M_PI's launches (and possibly the partial-sum buffer) change
   if (!group) {
     merged.reset();
     nsht_M = 2 * nobs;

@@ -133,6 +133,22 @@ struct Model {
   int merge_precond(const int* group, cudaStream_t s);
   int apply_precond_merged(const double* r, double* z, int prec, cudaStream_t s);
 
+  // CUDA graphs of the operator applies inside PCG (cg.cu), per (operator, precision,
+  // input, output): the first apply runs eagerly, the second is captured, later ones replay.
+  // Dropped whenever the model's internal buffers change.
+  struct OpGraph {
+    int op = 0, prec = 0;
+    const double* in = nullptr;
+    double* out = nullptr;
+    int calls = 0;
+    bool failed = false;
+    cudaGraphExec_t exec = nullptr;
+    long long nsht = 0;  // SHTs of one apply (the replay adds them to n_sht)
+  };
+  bool use_graphs = false;
+  std::vector<OpGraph> graphs;
+  void drop_graphs();
+
   // mask-restricted preconditioners (Sec. 4), applied with M_PI when precond = 2
   std::vector<MaskMG*> masks;
   int vcycle = 0;  // V-cycle of the mask preconditioners: 0 basic, 1 optimized (J ~ I)
