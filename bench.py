@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--with-batched", type=int, default=32, metavar="NPROB",
                     help="also time NPROB independent uneven masked problems (GL L 128..1024), "
                          "batched vs sequential, reported under 'batched'")
+    ap.add_argument("--autotune", type=int, default=2, choices=[0, 1, 2],
+                    help="synthesis tiles: 0 default, 1 heuristic, 2 measured on first use")
     ap.add_argument("--cert", default="fp32x2", choices=["fp32x2", "fp64"],
                     help="arithmetic of the FP64-accurate residual applies of the mixed solve")
     return ap.parse_args()
@@ -723,6 +725,7 @@ def main():
     import torch
     import paper_1710_00621_gb300 as cw
     INNER_TOL[0] = args.inner_tol
+    cw.cmbws_set_autotune(args.autotune)
     rank, world, local = dist_init(args.gpus)
     work = workload(args.scale)
     P = build_problem(work, args.prec, seed_offset=rank)
@@ -882,6 +885,7 @@ def main():
                                       f"certified by FP64-accurate ({cert}) applies"
                                       if args.prec == "fp32" else "FP64"),
                        "l2": "inputs larger than L2, no flush",
+                       "synthesis_tiles": ["default", "heuristic", "autotuned"][args.autotune],
                        "parallelism": f"replicas x{world}"},
             "solve": out, "fp64_plain": fp64, "batched": batched, "masked_cr": masked_cr,
             "tiny": extras.get("tiny"), "differentiable": extras.get("differentiable"),

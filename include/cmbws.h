@@ -314,6 +314,24 @@ int cmbws_grad_terms(cmbws_model m, const double* x, const double* lambda,
 int cmbws_project(cmbws_model m, const double* x, double* const* d, void* stream);
 
 /*
+ * Autotuner of the Legendre synthesis tiles (ring pairs per thread and threads per CTA).
+ *   mode 0 (default): every launch uses the default tile;
+ *   mode 1: a heuristic by the grid's ring-pair count (the smallest CTA holding every pair);
+ *   mode 2: on the first synthesis for a (grid, precision, maps) key, each tile variant is
+ *     launched and timed with CUDA events on the caller's stream (the first call is then
+ *     synchronous), and the fastest is kept for that key for the life of the grid.
+ * FP64 results do not depend on the tile; FP32 results can differ in rounding (warps that
+ * hold a ring pair near a pole switch to the difference form of the recurrence, and the
+ * tile decides which pairs share a warp).  Errors: CMBWS_ERR_ARG for another mode.
+ */
+int cmbws_set_autotune(int mode);
+
+/* The tuner's decision for synthesis on grid g at precision prec with nmaps maps per
+ * launch (1..4): variant index (-1 if none was measured), nvar variants, and their times in
+ * ms (ms: array of at least 8 floats, or NULL). */
+int cmbws_grid_tuning(cmbws_grid g, int prec, int nmaps, int* variant, float* ms, int* nvar);
+
+/*
  * Kernel timing.  While enabled, the library brackets each of its kernel launches with
  * CUDA events on the launching stream.  Records are kept per slot = stage + 6 * arith,
  * stages 0 Legendre synthesis, 1 Legendre adjoint, 2 adjoint partial-sum reduction,

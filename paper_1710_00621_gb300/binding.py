@@ -102,6 +102,9 @@ def load_library(path=None):
     lib.cmbws_model_merge_precond.argtypes = [vp, ctypes.POINTER(i), vp]
     lib.cmbws_model_set_vcycle.argtypes = [vp, i]
     lib.cmbws_model_set_graphs.argtypes = [vp, i]
+    lib.cmbws_set_autotune.argtypes = [i]
+    lib.cmbws_grid_tuning.argtypes = [vp, i, i, ctypes.POINTER(i), ctypes.POINTER(ctypes.c_float),
+                                      ctypes.POINTER(i)]
     u64 = ctypes.c_uint64
     lib.cmbws_draw.argtypes = [u64, u64, u64, ctypes.c_int64, ctypes.c_int64, i, vp, vp]
     lib.cmbws_cr_rhs.argtypes = [vp, ctypes.POINTER(vp), u64, u64, vp, vp]
@@ -348,6 +351,29 @@ def cmbws_rhs(model, d, b, omega1=None, omega2=None, stream=None):
     w2 = _dptr(omega2, model.nvec, "omega2") if omega2 is not None else ctypes.c_void_p()
     _check(load_library().cmbws_rhs(model.handle, dp, w1, w2, _dptr(b, model.nvec, "b"),
                                     _stream(stream)))
+
+
+CMBWS_TUNE_DEFAULT = 0
+CMBWS_TUNE_HEURISTIC = 1
+CMBWS_TUNE_MEASURED = 2
+SYNTH_TILES = [(2, 128), (1, 128), (1, 64), (4, 64)]   # (ring pairs per thread, threads per CTA)
+
+
+def cmbws_set_autotune(mode):
+    """Tile choice of the Legendre synthesis: CMBWS_TUNE_DEFAULT, _HEURISTIC or _MEASURED."""
+    _check(load_library().cmbws_set_autotune(int(mode)))
+
+
+def cmbws_grid_tuning(grid, prec, nmaps):
+    """The measured tile decision for synthesis on a grid: {"variant", "tile", "ms"} or None."""
+    v = ctypes.c_int()
+    n = ctypes.c_int()
+    ms = (ctypes.c_float * 8)()
+    _check(load_library().cmbws_grid_tuning(grid.handle, int(prec), int(nmaps), ctypes.byref(v),
+                                            ms, ctypes.byref(n)))
+    if v.value < 0:
+        return None
+    return {"variant": v.value, "tile": SYNTH_TILES[v.value], "ms": [ms[i] for i in range(n.value)]}
 
 
 def cmbws_model_set_graphs(model, on):

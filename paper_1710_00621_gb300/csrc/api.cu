@@ -77,6 +77,61 @@ cudaEvent_t pool_get() {
 
 bool prof_enabled() { return g_prof_on.load(std::memory_order_relaxed); }
 
+namespace {
+std::atomic<int> g_tune_mode{0};
+}
+
+int autotune_mode() { return g_tune_mode.load(std::memory_order_relaxed); }
+
+int autotune_pick(const Grid& g, int key, int nvar, int heuristic,
+                  const std::function<int(int)>& launch, cudaStream_t s, int* chosen) {
+  const int mode = autotune_mode();
+  *chosen = mode == 1 ? heuristic : 0;
+  if (mode != 2 || nvar < 2) return CMBWS_OK;
+  std::lock_guard<std::mutex> lk(g.tune_mu);
+  auto it = g.tuned.find(key);
+  if (it != g.tuned.end()) {
+    *chosen = it->second.variant;
+    return CMBWS_OK;
+  }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    *chosen = heuristic;
+    return CMBWS_OK;
+  }
+  cudaEvent_t a = nullptr, b = nullptr;
+  CMBWS_CUDA(cudaEventCreate(&a));
+  if (cudaEventCreate(&b) != cudaSuccess) {
+    cudaEventDestroy(a);
+    CMBWS_CUDA(cudaGetLastError());
+  }
+  Grid::Tuned t;
+  t.nvar = nvar < 8 ? nvar : 8;
+  int st = CMBWS_OK;
+  for (int v = 0; v < t.nvar && st == CMBWS_OK; ++v) {
+    st = launch(v);  // warm-up
+    if (st == CMBWS_OK) cudaEventRecord(a, s);
+    for (int r = 0; r < 2 && st == CMBWS_OK; ++r) st = launch(v);
+    if (st != CMBWS_OK) break;
+    cudaEventRecord(b, s);
+    if (cudaEventSynchronize(b) != cudaSuccess) {
+      st = CMBWS_ERR_CUDA;
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    t.ms[v] = 0.5f * ms;
+    if (t.ms[v] < t.ms[t.variant]) t.variant = v;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (st != CMBWS_OK) return st;
+  g.tuned[key] = t;
+  *chosen = t.variant;
+  return CMBWS_OK;
+}
+
 ProfScope::ProfScope(int stage, cudaStream_t s_, int arith, double flops_)
     : slot(stage + PROF_N * arith), flops(flops_), s(s_) {
   if (!g_prof_on.load(std::memory_order_relaxed)) return;  // no lock on the common path
@@ -140,6 +195,38 @@ using namespace cmbws;
 extern "C" const char* cmbws_last_error(void) { return t_err.c_str(); }
 
 extern "C" const char* cmbws_version(void) { return "cmbws 0.1 (sm_103a)"; }
+
+extern "C" int cmbws_set_autotune(int mode) {
+  clear_error();
+  if (mode < 0 || mode > 2) {
+    set_error("cmbws_set_autotune: mode must be 0 (defaults), 1 (heuristic) or 2 (measured)");
+    return CMBWS_ERR_ARG;
+  }
+  g_tune_mode = mode;
+  return CMBWS_OK;
+}
+
+extern "C" int cmbws_grid_tuning(cmbws_grid gh, int prec, int nmaps, int* variant, float* ms,
+                                 int* nvar) {
+  clear_error();
+  const Grid* g = reinterpret_cast<const Grid*>(gh);
+  if (!g || !variant || !nvar || nmaps < 1) {
+    set_error("cmbws_grid_tuning: invalid arguments");
+    return CMBWS_ERR_ARG;
+  }
+  std::lock_guard<std::mutex> lk(g->tune_mu);
+  auto it = g->tuned.find(synth_tune_key(prec, nmaps < 4 ? nmaps : 4));
+  if (it == g->tuned.end()) {
+    *variant = -1;
+    *nvar = 0;
+    return CMBWS_OK;
+  }
+  *variant = it->second.variant;
+  *nvar = it->second.nvar;
+  if (ms)
+    for (int v = 0; v < it->second.nvar; ++v) ms[v] = it->second.ms[v];
+  return CMBWS_OK;
+}
 
 extern "C" int cmbws_profile_enable(int on) {
   clear_error();

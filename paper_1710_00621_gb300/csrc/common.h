@@ -17,6 +17,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -155,6 +157,14 @@ struct Grid {
   mutable std::mutex ck64_mu;
   std::vector<double> fmm_h;  // sqrt((2m+1)/(2m)) (host, for rebuilding seeds)
 
+  // autotuner decisions for launches on this grid (legendre.cu), by kernel / precision / maps
+  struct Tuned {
+    int variant = 0, nvar = 0;
+    float ms[8] = {0};
+  };
+  mutable std::map<int, Tuned> tuned;
+  mutable std::mutex tune_mu;
+
   // ring FFT tables (device)
   std::vector<FftPlan> plans;
   DevMem plans_d;
@@ -225,6 +235,16 @@ int legendre_adj_df_ck(const Grid& g, int nm, const void* F, void* eo, double* o
 // threads, cmbws_cg_solve_batched) never see it lowered under them.
 int ensure_dyn_smem(const void* func, size_t bytes);
 bool prof_enabled();  // per-stage CUDA-event profiling switched on (cmbws_profile_enable)
+
+// Autotuner (api.cu): mode 0 = every launch uses its kernel's default tile, 1 = a heuristic by
+// problem shape, 2 = the fastest tile measured with CUDA events on the first launch for a
+// (grid, kernel, precision, maps) key.  autotune_pick returns the variant to launch; in mode 2
+// it times launch(v) for every v (each launch writes the same output) unless the stream is
+// being captured, and records the result in g.tuned[key].
+int autotune_mode();
+inline int synth_tune_key(int prec, int nmaps) { return 1000 + 10 * prec + nmaps; }
+int autotune_pick(const Grid& g, int key, int nvar, int heuristic,
+                  const std::function<int(int)>& launch, cudaStream_t s, int* chosen);
 
 // ---- kernel timing (api.cu): CUDA events around launches while enabled ----
 // Stages; a record's slot is stage + PROF_N * arith, arith 0 = FP32, 1 = FP64,

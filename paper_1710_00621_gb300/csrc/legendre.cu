@@ -82,6 +82,9 @@ k_leg_synth(const typename V2<T>::t* __restrict__ alm, int64_t alm_stride,
   __syncthreads();
   const int lo = s_lo;
   int nxt = mylo;  // next l at which one of this thread's pairs starts
+  // first l at which a pair of this warp starts: the warp skips every chunk before it (its
+  // recurrence values are zero there; warps without a valid pair skip all chunks)
+  const int wlo = __reduce_min_sync(kFull, mylo);
   // warps holding a polar ring pair run the difference form (FP32 only; warp-uniform)
   bool polar = false;
   if constexpr (kF32) {
@@ -110,11 +113,15 @@ k_leg_synth(const typename V2<T>::t* __restrict__ alm, int64_t alm_stride,
       }
     }
     __syncthreads();
+    // values of l in this chunk (the last chunk stops at L; an even count, the partner of
+    // an odd tail reads the zeros staged beyond L)
+    const int jn = min(CH, (L - c0 + 2) & ~1);
+    if (c0 + jn <= wlo) continue;
     if constexpr (kF32) {
       if (polar) {
         // mu2 holds e_{l-1} = mu_{l-1} - R_{l-1} mu_{l-2} in this form
 #pragma unroll 2
-        for (int j = 0; j < CH; j += 2) {
+        for (int j = 0; j < jn; j += 2) {
           const int l = c0 + j;
           const T A0 = sA[j], A1 = sA[j + 1];
           const float B0 = sBRS[0][j], B1 = sBRS[0][j + 1], R0 = sBRS[1][j], R1 = sBRS[1][j + 1];
@@ -159,7 +166,7 @@ k_leg_synth(const typename V2<T>::t* __restrict__ alm, int64_t alm_stride,
       }
     }
 #pragma unroll 2
-    for (int j = 0; j < CH; j += 2) {
+    for (int j = 0; j < jn; j += 2) {
       const int l = c0 + j;
       const T A0 = sA[j], A1 = sA[j + 1];
       T ma[R], mb[R];
@@ -560,22 +567,52 @@ constexpr size_t adj2_smem() {
   return sizeof(T) * ((size_t)NR * (C::ACH + 2) + (size_t)NR * 2 * P + (size_t)NSLICE * NJ * 2 * P);
 }
 
-template <typename T, int NM>
-int launch_synth(const Grid& g, const void* alm, int64_t alm_stride, void* F, int64_t F_stride,
-                 cudaStream_t s) {
+template <typename T, int NM, int R, int NT>
+int launch_synth_rn(const Grid& g, const void* alm, int64_t alm_stride, void* F, int64_t F_stride,
+                    cudaStream_t s) {
   using C = Cfg<T>;
   using T2 = typename V2<T>::t;
   const int L = g.lmax;
-  dim3 grd((g.npair + C::SNT * C::SR - 1) / (C::SNT * C::SR), L + 1);
+  dim3 grd((g.npair + NT * R - 1) / (NT * R), L + 1);
   const T* A = std::is_same<T, double>::value ? (const T*)g.A64.p : (const T*)g.A32.p;
   const T2* st = std::is_same<T, double>::value ? (const T2*)g.st64.p : (const T2*)g.st32.p;
   const T* yr = std::is_same<T, double>::value ? (const T*)g.y64.p : (const T*)g.y32.p;
   ProfScope ps(PROF_LEG_SYNTH, s, sizeof(T) == 8, 4.0 * g.npair * (double)nlm_of(L) * (NM + 1));
-  k_leg_synth<T, NM, C::SR, C::SNT, C::SCH><<<grd, C::SNT, 0, s>>>(
+  k_leg_synth<T, NM, R, NT, C::SCH><<<grd, NT, 0, s>>>(
       (const T2*)alm, alm_stride, A, g.BRS32.as<float>(), g.ls.as<int>(), st, yr,
       g.pair_ring.as<int2>(), (T2*)F, F_stride, L, g.npair, g.nring);
   CMBWS_LAUNCH_CHECK();
   return CMBWS_OK;
+}
+
+// Tile variants of the synthesis (ring pairs per thread R, threads per CTA NT): variant 0 is
+// the default for large grids; the others trade pairs per CTA (fewer idle lanes on grids
+// with few ring pairs) against coefficient reuse (R = 4: a shared-memory broadcast serves
+// four recurrences).  The autotuner picks one per (grid, precision, maps).
+constexpr int kSynthVariants = 4;
+
+template <typename T, int NM>
+int launch_synth_variant(int v, const Grid& g, const void* alm, int64_t as, void* F, int64_t fs,
+                         cudaStream_t s) {
+  switch (v) {
+    case 1: return launch_synth_rn<T, NM, 1, 128>(g, alm, as, F, fs, s);
+    case 2: return launch_synth_rn<T, NM, 1, 64>(g, alm, as, F, fs, s);
+    case 3: return launch_synth_rn<T, NM, 4, 64>(g, alm, as, F, fs, s);
+    default: return launch_synth_rn<T, NM, 2, 128>(g, alm, as, F, fs, s);
+  }
+}
+
+// heuristic: the smallest CTA (in ring pairs) that holds all pairs of the grid
+inline int synth_heuristic(const Grid& g) { return g.npair <= 64 ? 2 : g.npair <= 128 ? 1 : 0; }
+
+template <typename T, int NM>
+int launch_synth(const Grid& g, const void* alm, int64_t as, void* F, int64_t fs, cudaStream_t s) {
+  int v = 0;
+  const int prec = std::is_same<T, double>::value ? CMBWS_FP64 : CMBWS_FP32;
+  CMBWS_TRY(autotune_pick(g, synth_tune_key(prec, NM), kSynthVariants, synth_heuristic(g),
+                          [&](int vv) { return launch_synth_variant<T, NM>(vv, g, alm, as, F, fs, s); },
+                          s, &v));
+  return launch_synth_variant<T, NM>(v, g, alm, as, F, fs, s);
 }
 
 template <typename T>

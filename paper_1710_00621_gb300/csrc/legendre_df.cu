@@ -67,6 +67,7 @@ k_leg_synth_df(const double2* __restrict__ alm, int64_t alm_stride, const float2
   __syncthreads();
   const int lo = s_lo;
   int nxt = mylo;
+  const int wlo = __reduce_min_sync(0xffffffffu, mylo);  // first start of this warp's pairs
 
   for (int c0 = lo; c0 <= L; c0 += CH) {
     __syncthreads();
@@ -83,7 +84,10 @@ k_leg_synth_df(const double2* __restrict__ alm, int64_t alm_stride, const float2
       }
     }
     __syncthreads();
-    for (int j = 0; j < CH; j += 2) {
+    // the last chunk stops at L (even count); warps whose pairs start later skip the chunk
+    const int jn = min(CH, (L - c0 + 2) & ~1);
+    if (c0 + jn <= wlo) continue;
+    for (int j = 0; j < jn; j += 2) {
       const int l = c0 + j;
       const float2 a0 = sA[j], a1 = sA[j + 1];
       const df A0 = {a0.x, a0.y}, A1 = {a1.x, a1.y};
