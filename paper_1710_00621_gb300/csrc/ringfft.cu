@@ -167,8 +167,8 @@ __device__ void dft_inverse(T2* buf, const FftPlan& P, const T2* __restrict__ ta
   __syncthreads();
 }
 
-template <typename T, int MODE>
-__global__ void __launch_bounds__(256)
+template <typename T, int MODE, int NT>
+__global__ void __launch_bounds__(NT)
 k_ringfft(typename V2<T>::t* __restrict__ F, int64_t F_stride, double* __restrict__ map_out,
           const double* __restrict__ map_in, int64_t npix,
           const typename PixT<T>::t* __restrict__ ring_w, PixPtrs<typename PixT<T>::t> pix,
@@ -327,9 +327,16 @@ size_t smem_bytes(const Grid& g) {
   return (size_t)g.nmax2 * sizeof(typename V2<T>::t);  // the transform buffer
 }
 
+// Threads per CTA: a grid with large transforms (>= 2048 entries, e.g. the 4 Nside-point
+// equatorial rings from Nside 512 up) gets 512 threads, so that the butterfly passes of one
+// ring have twice the warps to hide shared-memory latency with the same buffer per CTA.
 template <typename T, int MODE>
 int launch(const Grid& g, int nmaps, void* F, double* map_out, const double* map_in, int weighted,
-           const void* const* pix, cudaStream_t s) {
+           const void* const* pix, cudaStream_t s);
+
+template <typename T, int MODE, int NT>
+int launch_nt(const Grid& g, int nmaps, void* F, double* map_out, const double* map_in,
+              int weighted, const void* const* pix, cudaStream_t s) {
   using T2 = typename V2<T>::t;
   const size_t sm = smem_bytes<T>(g);
   if (sm > 227 * 1024) {
@@ -337,7 +344,7 @@ int launch(const Grid& g, int nmaps, void* F, double* map_out, const double* map
               sm, g.max_n);
     return CMBWS_ERR_ARG;
   }
-  auto kern = k_ringfft<T, MODE>;
+  auto kern = k_ringfft<T, MODE, NT>;
   CMBWS_TRY(ensure_dyn_smem((const void*)kern, sm));
   using TP = typename PixT<T>::t;
   const int64_t fs = (int64_t)g.nring * (g.lmax + 1);
@@ -352,7 +359,7 @@ int launch(const Grid& g, int nmaps, void* F, double* map_out, const double* map
       for (int i = 0; i < nm; ++i) pp.p[i] = (const TP*)pix[k0 + i];
     dim3 grd(g.npair, nm);
     ProfScope ps(PROF_FFT, s, f32 ? 0 : f64 ? 1 : 2);
-    kern<<<grd, 256, sm, s>>>((T2*)F + k0 * fs, fs, map_out ? map_out + k0 * g.npix : nullptr,
+    kern<<<grd, NT, sm, s>>>((T2*)F + k0 * fs, fs, map_out ? map_out + k0 * g.npix : nullptr,
                               map_in ? map_in + k0 * g.npix : nullptr, g.npix, rw, pp,
                               g.plans_d.as<FftPlan>(), g.pair_plan.as<int>(),
                               g.pair_ring.as<int2>(), g.pair_phase.as<int>(), g.ring_off.as<int64_t>(),
@@ -360,6 +367,14 @@ int launch(const Grid& g, int nmaps, void* F, double* map_out, const double* map
     CMBWS_LAUNCH_CHECK();
   }
   return CMBWS_OK;
+}
+
+template <typename T, int MODE>
+int launch(const Grid& g, int nmaps, void* F, double* map_out, const double* map_in, int weighted,
+           const void* const* pix, cudaStream_t s) {
+  if (g.nmax2 >= 2048)
+    return launch_nt<T, MODE, 512>(g, nmaps, F, map_out, map_in, weighted, pix, s);
+  return launch_nt<T, MODE, 256>(g, nmaps, F, map_out, map_in, weighted, pix, s);
 }
 
 }  // namespace
