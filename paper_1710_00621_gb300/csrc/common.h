@@ -120,6 +120,8 @@ struct FftPlan {
   int64_t phase;  // offset of exp(i pi k / n), k < n (ring offset phi0 = pi / n)
 };
 
+constexpr int kTileMinPT = 16;  // ring pairs per tile of the FP32 checkpointed adjoint
+
 struct Grid {
   int device = 0;
   int kind = 0, n = 0, lmax = 0, nring = 0, npair = 0;
@@ -145,6 +147,7 @@ struct Grid {
   DevMem st64, st32;      // {mu_ls, mu_ls+1} [L+1][npair]
   DevMem ck32;            // FP32 {mu_l0, mu_l0+1} at every chunk start l0 = m + kChunk c
   DevMem ck_base;         // int64 [L+1]: offset of m's block [pair][chunk] in ck32
+  DevMem ls_tmin;         // int [L+1][ceil(npair / kTileMinPT)]: smallest ls of each tile of pairs
   // warp tasks of the checkpointed adjoints: int2 {m, first chunk} per 32 consecutive
   // chunks of one m, m ascending (FP32 chunking; the double-float list is built with ck64)
   DevMem wt32;

@@ -425,8 +425,9 @@ k_leg_adj_ck(const float* __restrict__ eo, const float* __restrict__ Acoef,
              const int* __restrict__ ls_tab, const float2* __restrict__ st,
              const float* __restrict__ yr, const float2* __restrict__ ck,
              const int64_t* __restrict__ ck_base, const int2* __restrict__ tasks, int ntask,
-             const double* __restrict__ c64, double2* __restrict__ out, int64_t nlm, int L,
-             int npair) {
+             const int* __restrict__ tmin, const double* __restrict__ c64,
+             double2* __restrict__ out, int64_t nlm, int L, int npair) {
+  static_assert(PT == kTileMinPT, "the tile-start table is built for kTileMinPT pairs per tile");
   constexpr int P = 2 * NM;
   constexpr int K = kChunk;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -454,11 +455,18 @@ k_leg_adj_ck(const float* __restrict__ eo, const float* __restrict__ Acoef,
   const float2* ckc = ck + ck_base[m] + c;  // + p * nck
   const float* eom = eo + (int64_t)m * npair * 2 * P;
   const int ntile = (npair + PT - 1) / PT;
-  // the first pair that has started by the warp's last chunk bounds nothing (pairs are
-  // not sorted by start), so every tile is visited; pairs not yet started are skipped
+  // Pairs are not sorted by start; a tile whose pairs all start after the warp's last l
+  // (tmin, the smallest start of the tile) adds nothing to this warp's outputs and is not
+  // staged.  Pairs of a visited tile that have not started are skipped one by one.
+  const int llast = min(L, m + K * (cw + 32) - 1);
+  const int* tm = tmin + (int64_t)m * ntile;
+  auto next_tile = [&](int t) {
+    while (t < ntile && tm[t] > llast) ++t;
+    return t;
+  };
 
-  auto stage = [&](int t) {
-    const int bf = t & 1, p0 = t * PT;
+  auto stage = [&](int t, int bf) {
+    const int p0 = t * PT;
     const int np = min(PT, npair - p0);
     const float* src = eom + (int64_t)p0 * 2 * P;
     for (int i = lane; i < np * NM; i += 32) cp_async16(&S.eo[bf][0][0] + 4 * i, src + 4 * i);
@@ -472,17 +480,19 @@ k_leg_adj_ck(const float* __restrict__ eo, const float* __restrict__ Acoef,
     cp_async_commit();
   };
 
-  stage(0);
-  for (int t = 0; t < ntile; ++t) {
-    if (t + 1 < ntile) {
-      stage(t + 1);
+  int t = next_tile(0);
+  if (t < ntile) stage(t, 0);
+  for (int k = 0; t < ntile; ++k) {
+    const int tn = next_tile(t + 1);
+    if (tn < ntile) {
+      stage(tn, (k + 1) & 1);
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
     }
     __syncwarp();
     if (valid) {
-      const int bf = t & 1;
+      const int bf = k & 1;
       const int np = min(PT, npair - t * PT);
       for (int i = 0; i < np; ++i) {
         const int lsp = S.ls[bf][i];
@@ -518,7 +528,8 @@ k_leg_adj_ck(const float* __restrict__ eo, const float* __restrict__ Acoef,
         }
       }
     }
-    __syncwarp();  // buffer t & 1 is restaged two iterations later
+    __syncwarp();  // buffer k & 1 is restaged two iterations later
+    t = tn;
   }
   if (!valid) return;
 #pragma unroll
@@ -642,8 +653,8 @@ int launch_adj_ck(const Grid& g, const void* F, int64_t F_stride, void* part, do
   ProfScope ps(PROF_LEG_ADJ, s, 0, 4.0 * g.npair * (double)nlm * (NM + 1));
   kern<<<grd, NT, sm, s>>>(eo, g.A32.as<float>(), g.ls.as<int>(), g.st32.as<float2>(),
                            g.y32.as<float>(), g.ck32.as<float2>(), g.ck_base.as<int64_t>(),
-                           g.wt32.as<int2>(), g.nwt32, g.c64.as<double>(), (double2*)out, nlm, L,
-                           g.npair);
+                           g.wt32.as<int2>(), g.nwt32, g.ls_tmin.as<int>(), g.c64.as<double>(),
+                           (double2*)out, nlm, L, g.npair);
   CMBWS_LAUNCH_CHECK();
   return CMBWS_OK;
 }

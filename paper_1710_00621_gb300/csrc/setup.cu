@@ -24,6 +24,7 @@
 // start of every chunk of kChunk = 8 values of l ([m][pair][chunk], FP32; about
 // npair (L+1)^2 / 16 x 8 bytes: 9.7 GB at Nside 1024, L = 3071), so that the adjoint can
 // restart the recurrence of any pair at any chunk without a serial walk along l.
+#include <climits>
 #include <cmath>
 #include <complex>
 #include <cstring>
@@ -220,6 +221,17 @@ __global__ void k_unpack(const double2* __restrict__ lmc, int L, double* __restr
   if (m > 0) dst[(L - m + 1) + (l - m)] = v.y;
 }
 
+// tmin[m][t] = min over the pairs p of tile t (kTileMinPT consecutive pairs) of ls[m][p]
+__global__ void k_tile_min(const int* __restrict__ ls, int npair, int ntile, int* __restrict__ tmin) {
+  const int m = blockIdx.y;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ntile) return;
+  int v = INT_MAX;
+  const int p1 = min(npair, (t + 1) * kTileMinPT);
+  for (int p = t * kTileMinPT; p < p1; ++p) v = min(v, ls[(int64_t)m * npair + p]);
+  tmin[(int64_t)m * ntile + t] = v;
+}
+
 }  // namespace
 
 int pack_alm(const Grid& g, int prec, int nmaps, const double* packed, void* alm, cudaStream_t s) {
@@ -360,6 +372,11 @@ int grid_build_tables(Grid& g) {
     k_start<<<grd, 128>>>(g.y64.as<double>(), g.A64.as<double>(), L, g.npair, d_sv.as<double>(),
                           d_sk.as<int>(), g.ls.as<int>(), g.st64.as<double2>(), g.st32.as<float2>(),
                           g.ck_base.as<int64_t>(), g.ck32.as<float2>(), nullptr, nullptr);
+    CMBWS_LAUNCH_CHECK();
+    const int ntile = (g.npair + kTileMinPT - 1) / kTileMinPT;
+    CMBWS_TRY(g.ls_tmin.alloc((size_t)(L + 1) * ntile * 4));
+    dim3 gt((ntile + 127) / 128, L + 1);
+    k_tile_min<<<gt, 128>>>(g.ls.as<int>(), g.npair, ntile, g.ls_tmin.as<int>());
     CMBWS_LAUNCH_CHECK();
     CMBWS_CUDA(cudaDeviceSynchronize());
   }
