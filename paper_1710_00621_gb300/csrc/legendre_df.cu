@@ -189,8 +189,9 @@ k_leg_adj_ck_df(const float2* __restrict__ eo, const float2* __restrict__ Acoef,
                 const int* __restrict__ ls_tab, const double2* __restrict__ st,
                 const float2* __restrict__ yr, const float4* __restrict__ ck,
                 const int64_t* __restrict__ ck_base, const int2* __restrict__ tasks, int ntask,
-                const double* __restrict__ c64, double2* __restrict__ out, int64_t nlm, int L,
-                int npair) {
+                const int* __restrict__ tmin, const double* __restrict__ c64,
+                double2* __restrict__ out, int64_t nlm, int L, int npair) {
+  static_assert(kTileMinPT % PT == 0, "a tile must lie inside one entry of the tile-start table");
   constexpr int P = 2 * NM;
   constexpr int K = kChunkDf;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -221,9 +222,17 @@ k_leg_adj_ck_df(const float2* __restrict__ eo, const float2* __restrict__ Acoef,
   const float4* ckc = ck + ck_base[m] + c;  // + p * nck
   const float2* eom = eo + (int64_t)m * npair * 2 * P;
   const int ntile = (npair + PT - 1) / PT;
+  // tiles whose pairs all start after the warp's last l add nothing and are not staged;
+  // tmin holds the smallest start of each kTileMinPT pairs, a lower bound for this tile's
+  const int llast = min(L, m + K * (cw + 32) - 1);
+  const int* tm = tmin + (int64_t)m * ((npair + kTileMinPT - 1) / kTileMinPT);
+  auto next_tile = [&](int t) {
+    while (t < ntile && tm[t * PT / kTileMinPT] > llast) ++t;
+    return t;
+  };
 
-  auto stage = [&](int t) {
-    const int bf = t & 1, p0 = t * PT;
+  auto stage = [&](int t, int bf) {
+    const int p0 = t * PT;
     const int np = min(PT, npair - p0);
     const float2* src = eom + (int64_t)p0 * 2 * P;
     for (int i = lane; i < np * P; i += 32) cp_async16(&S.eo[bf][0][0] + 2 * i, src + 2 * i);
@@ -237,17 +246,19 @@ k_leg_adj_ck_df(const float2* __restrict__ eo, const float2* __restrict__ Acoef,
     cp_async_commit();
   };
 
-  stage(0);
-  for (int t = 0; t < ntile; ++t) {
-    if (t + 1 < ntile) {
-      stage(t + 1);
+  int t = next_tile(0);
+  if (t < ntile) stage(t, 0);
+  for (int k = 0; t < ntile; ++k) {
+    const int tn = next_tile(t + 1);
+    if (tn < ntile) {
+      stage(tn, (k + 1) & 1);
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
     }
     __syncwarp();
     if (valid) {
-      const int bf = t & 1;
+      const int bf = k & 1;
       const int np = min(PT, npair - t * PT);
       for (int i = 0; i < np; ++i) {
         const int lsp = S.ls[bf][i];
@@ -283,7 +294,8 @@ k_leg_adj_ck_df(const float2* __restrict__ eo, const float2* __restrict__ Acoef,
         }
       }
     }
-    __syncwarp();  // buffer t & 1 is restaged two iterations later
+    __syncwarp();  // buffer k & 1 is restaged two iterations later
+    t = tn;
   }
   if (!valid) return;
 #pragma unroll
@@ -333,8 +345,8 @@ int launch_adj_ck_df(const Grid& g, const void* F, int64_t fs, void* eo_buf, dou
   ProfScope ps(PROF_LEG_ADJ, s, 2, 4.0 * g.npair * (double)nlm * (NM + 1));
   kern<<<grd, kANT, sm, s>>>(eo, g.A2f.as<float2>(), g.ls.as<int>(), g.st64.as<double2>(),
                              g.y2f.as<float2>(), g.ck64.as<float4>(), g.ck64_base.as<int64_t>(),
-                             g.wtdf.as<int2>(), g.nwtdf, g.c64.as<double>(), (double2*)out, nlm, L,
-                             g.npair);
+                             g.wtdf.as<int2>(), g.nwtdf, g.ls_tmin.as<int>(), g.c64.as<double>(),
+                             (double2*)out, nlm, L, g.npair);
   CMBWS_LAUNCH_CHECK();
   return CMBWS_OK;
 }
