@@ -630,10 +630,10 @@ FP32_FLOPS_PER_ELEM = {("legendre_synth", "fp32"): 16.0, ("legendre_adjoint", "f
 
 
 # DRAM bytes (read + write) per element from one ncu capture of the kernel as it stands,
-# on the Nside 512, L = 1535, 3-map case (profiles/k_leg_adj_ck_df_healpix512_l1535_3maps.md);
-# the checkpoint table dominates, so it scales with the elements.  Empty while no capture of
-# the current kernel exists (the roofline's traffic is then null).
-DRAM_BYTES_PER_ELEM = {}
+# on the Nside 512, L = 1535, 3-map case (profiles/k_leg_adj_ck_df_healpix512_l1535_3maps.md):
+# 4.083 GB / 1.209e9 elements; the checkpoint table dominates, so it scales with the
+# elements.  Emptied whenever the kernel changes until it is captured again.
+DRAM_BYTES_PER_ELEM = {("legendre_adjoint", "fp32x2"): 3.38}
 
 
 def roofline(prof):
