@@ -29,7 +29,10 @@ equatorial zone pixel boundaries are the lines t -/+ 3z/4 = const in (t = 2 phi 
 in the polar caps the lines t' N sqrt(3 (1 - |z|)) = const with t' = t mod 1).
 
 Parity: pinned (tests/test_oracle_maskmg.py) -- ang2pix of every pixel centre returns the
-pixel, every coarse pixel has exactly four children, the bottom solve is a
+pixel, every coarse pixel has exactly four children, the coarse mask equals a brute-force
+rule (a coarse pixel kept iff the four fine pixels nearest its centre, its children, are
+all masked), the filter of Eq. rl has the l^2 (l+1)^2 shape with r^2 = 0.05 at L/2 (beta
+recovered from a single value), the bottom solve is a
 pseudo-inverse of the dense G, the V-cycle operator is symmetric and accelerates CG on G,
 M_mask with an exact inner inverse equals the dense Eq. M_mask, and M_add reduces the
 PCG iteration count of a masked problem against M_PI (the paper's masked benchmark).  The

@@ -198,3 +198,57 @@ def test_M_add_with_optimized_vcycle_converges_like_basic():
         assert np.linalg.norm(x - inp["x_true"]) < 1e-4 * np.linalg.norm(inp["x_true"])
         its[cyc] = rep["iters"]
     assert its["optimized"] <= 1.5 * its["basic"] + 2, its
+
+
+def _unit_vectors(g):
+    th, ph = g.pixel_angles()
+    return np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)], 1)
+
+
+@pytest.mark.parametrize("nside", [2, 4, 8, 16, 32])
+def test_coarse_mask_keeps_a_pixel_only_when_its_four_children_are_masked(nside):
+    """Sec. 4.4: a coarse pixel belongs to the coarse mask only if it is 100 % masked.
+
+    Brute force, independent of ang2pix: the centre of a coarse pixel is the vertex its four
+    children share (the subdivision halves the pixel along both face directions), so the
+    children are the four fine pixels whose centres lie nearest to it; the fifth nearest
+    lies clearly farther out.  A coarse pixel is kept exactly when all four are masked."""
+    from scipy.spatial import cKDTree
+    f, c = og.healpix(nside), og.healpix(nside // 2)
+    dist, near = cKDTree(_unit_vectors(f)).query(_unit_vectors(c), k=5)
+    assert np.all(dist[:, 4] > 1.01 * dist[:, 3])
+    children = near[:, :4]
+    # the oracle's parent map agrees with the brute-force children
+    par = mg.coarse_parent(nside)
+    np.testing.assert_array_equal(par[children], np.repeat(np.arange(c.npix)[:, None], 4, 1))
+    rng = np.random.default_rng(nside)
+    kept = dropped = 0
+    for frac in (0.3, 0.7, 0.95):
+        mask = rng.uniform(size=f.npix) < frac
+        mask |= _band_mask(nside, 0.2)            # whole masked blocks as well as random pixels
+        want = mask[children].all(axis=1)
+        got = mg.coarse_mask(nside, mask)
+        np.testing.assert_array_equal(got, want)
+        kept += int(want.sum())
+        dropped += int((~want & mask[children].any(axis=1)).sum())
+    assert kept > 0 and dropped > 0               # both outcomes occur
+
+
+@pytest.mark.parametrize("L", [2, 7, 40, 191, 1535])
+def test_rl_filter_matches_eq_rl(L):
+    """Eq. rl: r_l = exp(-beta l^2 (l+1)^2), beta fixed by r^2 = 0.05 at l = L/2.
+
+    beta is recovered from one value, r at lr = ceil(L/2) (where r is well below 1, so its
+    logarithm is well conditioned); every other r_l must follow the l^2 (l+1)^2 shape with
+    that beta, and the squared filter at L/2 (an integer or a half-integer l) must equal 0.05."""
+    r = mg.rl_filter(L, 2 * L)
+    assert r[0] == 1.0 and np.all(np.diff(r) < 0)
+    lr = max(1, (L + 1) // 2)
+    beta = -np.log(r[lr]) / (lr * lr * (lr + 1.0) ** 2)
+    l = np.arange(2 * L + 1, dtype=np.float64)
+    np.testing.assert_allclose(np.log(r[1:]), -beta * (l * l * (l + 1) ** 2)[1:], rtol=1e-10,
+                               atol=1e-15)
+    h = 0.5 * L
+    assert abs(np.exp(-2.0 * beta * h * h * (h + 1) ** 2) - 0.05) < 1e-13
+    if L % 2 == 0:
+        assert abs(r[L // 2] ** 2 - 0.05) < 1e-13
