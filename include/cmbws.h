@@ -52,7 +52,8 @@ enum {
   CMBWS_ERR_SINGULAR = -4,      /* a U block has a column with zero norm */
   CMBWS_ERR_BREAKDOWN = -5,     /* CG: p.Ap <= 0 or a non-finite scalar */
   CMBWS_ERR_NOT_CONVERGED = -6, /* CG: iteration cap reached (x holds the last iterate) */
-  CMBWS_ERR_TIMEOUT = -7        /* wall-clock budget of a solve exhausted */
+  CMBWS_ERR_TIMEOUT = -7        /* wall-clock budget of a solve exhausted, or a bounded
+                                   device-side wait ran out (cmbws_device_status) */
 };
 
 typedef enum { CMBWS_GRID_GL = 0, CMBWS_GRID_HEALPIX = 1 } cmbws_grid_kind;
@@ -450,6 +451,28 @@ int cmbws_cr_sample(cmbws_model m, const double* const* d, uint64_t seed, uint64
  */
 int cmbws_powerlaw_mixing(double nu_ratio, const double* beta, const double* mask, int64_t n,
                           double* q, void* stream);
+
+/*
+ * Device-side status.  Kernels that wait on an asynchronous event inside the GPU (the
+ * tensor-core Legendre synthesis waits on mbarriers for its MMAs) bound every wait; when a
+ * wait runs out the kernel stops issuing work, writes NaN into its outputs, records the
+ * event in a per-device status word and returns, so the context stays usable.  This call
+ * synchronises `stream`, then returns CMBWS_ERR_TIMEOUT if such an event was recorded on the
+ * current device since the last call (and clears the record), else CMBWS_OK.  The solvers
+ * check the record themselves when a non-finite scalar appears and return CMBWS_ERR_TIMEOUT
+ * instead of CMBWS_ERR_BREAKDOWN.
+ */
+int cmbws_device_status(void* stream);
+
+/*
+ * Test support for the bounded waits (no counterpart in the paper).  wait_cycles > 0 makes
+ * every CTA of the tensor-core Legendre synthesis (CMBWS_TF32, CMBWS_3XTF32) on the current
+ * device first wait at most wait_cycles SM clocks on an mbarrier phase that nothing ever
+ * completes: the wait runs out, and the CTA takes the failure path described at
+ * cmbws_device_status.  0 (the default) switches it off.  Errors: CMBWS_ERR_ARG outside
+ * [0, 2^32].
+ */
+int cmbws_testing_stall_waits(long long wait_cycles);
 
 #ifdef __cplusplus
 }

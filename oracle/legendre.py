@@ -104,3 +104,34 @@ def lambda_lm_table(lmax, theta):
     for l, lam in lambda_all(lmax, theta):
         out[l, : l + 1] = lam
     return out
+
+
+def lambda_m(m, lmax, theta):
+    """lambda_lm(theta) for one m and l = m..lmax, shape [lmax - m + 1, nring].
+
+    The same seeds, recurrence and exponent handling as lambda_all, walked along l for a
+    single m (used to check transforms at full size on a sample of m)."""
+    theta = np.asarray(theta, dtype=np.float64)
+    x = np.cos(theta)
+    sv, sk = seeds(m, theta)
+    out = np.zeros((lmax - m + 1, theta.size))
+    if lmax < m:
+        return out
+    cur, k = sv[m].copy(), sk[m].copy()
+    out[0] = np.where(k == 0, cur, 0.0)
+    prev = np.zeros_like(cur)
+    for l in range(m + 1, lmax + 1):
+        if l == m + 1:
+            nxt = np.sqrt(2.0 * m + 3.0) * x * cur
+        else:
+            a_l = np.sqrt((4.0 * l * l - 1.0) / (l * l - m * m))
+            a_lm1 = np.sqrt((4.0 * (l - 1) ** 2 - 1.0) / ((l - 1) ** 2 - m * m))
+            nxt = a_l * (x * cur - prev / a_lm1)
+        grow = (k > 0) & (np.abs(nxt) > _GROW)
+        if grow.any():
+            nxt = np.where(grow, nxt / _BIG, nxt)
+            cur = np.where(grow, cur / _BIG, cur)
+            k = k - grow
+        prev, cur = cur, nxt
+        out[l - m] = np.where(k == 0, cur, 0.0)
+    return out

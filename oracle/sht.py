@@ -25,7 +25,7 @@ adjoint identity <Y a, f> = <a, Y^T f>.
 import numpy as np
 
 from . import alm as _alm
-from .legendre import lambda_all, lambda_lm_table
+from .legendre import lambda_all, lambda_lm_table, lambda_m
 
 _SQRT2 = np.sqrt(2.0)
 
@@ -90,6 +90,48 @@ def adjoint(grid, lmax, fmap, weighted=False):
         X[l, lmax + ms] = (lam * Gc[: l + 1]).sum(axis=1)
         X[l, lmax - ms[1:]] = (lam[1:] * Gs[1: l + 1]).sum(axis=1)
     return _alm.from_2d(X, lmax)
+
+
+def adjoint_m(grid, lmax, fmap, ms, weighted=False):
+    """Y^T f (or Y^T W f) restricted to the orders m in ``ms``: {m: (cos part, sin part)},
+    each of length lmax - m + 1 (l = m..lmax; the sin part of m = 0 is zero).
+
+    The Legendre stage is independent per m, so this equals the matching entries of
+    ``adjoint`` while touching only the requested columns: the full azimuthal transform of
+    every ring, then the per-m recurrence over all rings."""
+    f = np.asarray(fmap, dtype=np.float64)
+    if weighted:
+        f = f * grid.pixel_weights()
+    ms = [int(m) for m in ms]
+    marr = np.asarray(ms)
+    Gc = np.zeros((len(ms), grid.nring))
+    Gs = np.zeros((len(ms), grid.nring))
+    for r in range(grid.nring):
+        n = int(grid.nphi[r])
+        H = np.fft.fft(f[grid.offset[r]: grid.offset[r + 1]])
+        G = H[marr % n] * np.exp(-1j * marr * grid.phi0[r])
+        Gc[:, r] = G.real
+        Gs[:, r] = -G.imag
+    out = {}
+    for i, m in enumerate(ms):
+        lam = lambda_m(m, lmax, grid.theta)            # [l - m, ring]
+        c = lam @ Gc[i]
+        s = lam @ Gs[i]
+        if m > 0:
+            c, s = _SQRT2 * c, _SQRT2 * s
+        else:
+            s = np.zeros_like(s)
+        out[m] = (c, s)
+    return out
+
+
+def packed_m(packed, lmax, m):
+    """The (cos part, sin part) of order m of a packed coefficient vector (l = m..lmax)."""
+    n = lmax - m + 1
+    if m == 0:
+        return np.asarray(packed[:n]), np.zeros(n)
+    o = (lmax + 1) + (m - 1) * (2 * lmax + 2 - m)
+    return np.asarray(packed[o: o + n]), np.asarray(packed[o + n: o + 2 * n])
 
 
 def analysis(grid, lmax, fmap):

@@ -112,6 +112,8 @@ def load_library(path=None):
                                     ctypes.POINTER(CgReport), vp]
     lib.cmbws_powerlaw_mixing.argtypes = [d, vp, vp, ctypes.c_int64, vp, vp]
     lib.cmbws_profile_enable.argtypes = [i]
+    lib.cmbws_device_status.argtypes = [vp]
+    lib.cmbws_testing_stall_waits.argtypes = [ctypes.c_longlong]
     lib.cmbws_profile_read.argtypes = [ctypes.POINTER(d), ctypes.POINTER(ctypes.c_int64),
                                        ctypes.POINTER(d), i]
     lib.cmbws_cg_solve.argtypes = [vp, vp, vp, ctypes.POINTER(CgOpts), ctypes.POINTER(CgReport), vp]
@@ -504,6 +506,18 @@ def cmbws_project(model, x, d, stream=None):
 
 PROFILE_STAGES = ("legendre_synth", "legendre_adjoint", "adjoint_reduce", "ring_fft", "harmonic",
                   "cg_vector")
+
+
+def cmbws_device_status(stream=None):
+    """Synchronise the stream and raise CmbwsError (CMBWS_ERR_TIMEOUT) if a bounded
+    device-side wait of a library kernel ran out since the last check."""
+    _check(load_library().cmbws_device_status(_stream(stream)))
+
+
+def cmbws_testing_stall_waits(wait_cycles):
+    """Test support: make the tensor-core synthesis CTAs wait up to wait_cycles SM clocks on an
+    mbarrier phase that never completes (0 switches it off)."""
+    _check(load_library().cmbws_testing_stall_waits(int(wait_cycles)))
 
 
 def cmbws_profile_enable(on=True):

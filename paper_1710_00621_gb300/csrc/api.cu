@@ -5,11 +5,33 @@
 #include <cstdio>
 #include <mutex>
 #include <string>
+#include <unordered_set>
 #include <vector>
 
 #include "common.h"
 
 namespace cmbws {
+
+namespace {
+std::mutex g_live_mu;
+std::unordered_set<const void*> g_live[2];
+}  // namespace
+
+void handle_add(int kind, const void* p) {
+  std::lock_guard<std::mutex> lk(g_live_mu);
+  g_live[kind].insert(p);
+}
+
+bool handle_del(int kind, const void* p) {
+  std::lock_guard<std::mutex> lk(g_live_mu);
+  return p && g_live[kind].erase(p) == 1;
+}
+
+bool handle_live(int kind, const void* p) {
+  if (!p) return false;
+  std::lock_guard<std::mutex> lk(g_live_mu);
+  return g_live[kind].count(p) != 0;
+}
 
 static thread_local std::string t_err;
 
@@ -209,7 +231,7 @@ extern "C" int cmbws_set_autotune(int mode) {
 extern "C" int cmbws_grid_tuning(cmbws_grid gh, int prec, int nmaps, int* variant, float* ms,
                                  int* nvar) {
   clear_error();
-  const Grid* g = reinterpret_cast<const Grid*>(gh);
+  const Grid* g = as_grid(gh);
   if (!g || !variant || !nvar || nmaps < 1) {
     set_error("cmbws_grid_tuning: invalid arguments");
     return CMBWS_ERR_ARG;
@@ -266,7 +288,7 @@ extern "C" int cmbws_profile_read(double* ms, int64_t* launches, double* flops, 
 extern "C" int cmbws_sht_synth(cmbws_grid gh, cmbws_prec prec, const double* alm, double* map,
                                int nmaps, void* stream) {
   clear_error();
-  Grid* g = reinterpret_cast<Grid*>(gh);
+  Grid* g = as_grid(gh);
   if (!g || !alm || !map || nmaps < 1 || !valid_prec(prec)) {
     set_error("cmbws_sht_synth: invalid arguments");
     return CMBWS_ERR_ARG;
@@ -290,7 +312,7 @@ extern "C" int cmbws_sht_synth(cmbws_grid gh, cmbws_prec prec, const double* alm
 extern "C" int cmbws_sht_analysis(cmbws_grid gh, cmbws_prec prec, const double* map, double* alm,
                                   int nmaps, int weighted, void* stream) {
   clear_error();
-  Grid* g = reinterpret_cast<Grid*>(gh);
+  Grid* g = as_grid(gh);
   if (!g || !alm || !map || nmaps < 1 || !valid_prec(prec)) {
     set_error("cmbws_sht_analysis: invalid arguments");
     return CMBWS_ERR_ARG;

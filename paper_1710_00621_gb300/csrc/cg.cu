@@ -264,6 +264,12 @@ static int pcg_core(Solver& S, int prec, int use_M, double* d, double* r, double
     double pq;
     CMBWS_TRY(S.dot(p, q, &pq));
     if (!(pq > 0.0) || !std::isfinite(pq) || !std::isfinite(rz)) {
+      // a bounded device-side wait that ran out leaves NaN in the operator's output
+      bool timed_out = false;
+      if (tc_status_take(&timed_out) == CMBWS_OK && timed_out) {
+        set_error("CG: a bounded device-side wait ran out in the operator apply (iteration %d)", it);
+        return CMBWS_ERR_TIMEOUT;
+      }
       set_error("CG breakdown: p.Ap = %g, r.z = %g at iteration %d", pq, rz, it);
       return CMBWS_ERR_BREAKDOWN;
     }
@@ -404,7 +410,7 @@ using namespace cmbws;
 extern "C" int cmbws_cg_solve(cmbws_model mh, const double* b, double* x, const cmbws_cg_opts* opts,
                               cmbws_cg_report* report, void* stream) {
   clear_error();
-  Model* M = reinterpret_cast<Model*>(mh);
+  Model* M = as_model(mh);
   if (!M || !b || !x || !opts || b == x || !(opts->tol > 0.0) || opts->maxiter < 1 ||
       opts->precond < 0 || opts->precond > 3) {
     set_error("cmbws_cg_solve: invalid arguments");
@@ -424,7 +430,7 @@ extern "C" int cmbws_cg_solve(cmbws_model mh, const double* b, double* x, const 
 
 extern "C" int cmbws_model_set_graphs(cmbws_model mh, int on) {
   clear_error();
-  Model* M = reinterpret_cast<Model*>(mh);
+  Model* M = as_model(mh);
   if (!M) {
     set_error("cmbws_model_set_graphs: invalid model");
     return CMBWS_ERR_ARG;
@@ -444,7 +450,7 @@ extern "C" int cmbws_cg_solve_batched(const cmbws_model* models, int nprob, cons
     return CMBWS_ERR_ARG;
   }
   for (int i = 0; i < nprob; ++i) {
-    if (!models[i] || !b[i] || !x[i] || b[i] == x[i]) {
+    if (!as_model(models[i]) || !b[i] || !x[i] || b[i] == x[i]) {
       set_error("cmbws_cg_solve_batched: invalid arguments for problem %d", i);
       return CMBWS_ERR_ARG;
     }

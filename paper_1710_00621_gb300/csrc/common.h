@@ -30,6 +30,14 @@ namespace cmbws {
 void set_error(const char* fmt, ...);
 void clear_error();
 
+// Registry of live handles (api.cu): every grid and model the library hands out is recorded
+// until it is destroyed, so calls with a destroyed, foreign or corrupted handle fail with
+// CMBWS_ERR_ARG instead of dereferencing it.
+enum { HANDLE_GRID = 0, HANDLE_MODEL = 1 };
+void handle_add(int kind, const void* p);
+bool handle_del(int kind, const void* p);  // false if p was not live
+bool handle_live(int kind, const void* p);
+
 #define CMBWS_CUDA(expr)                                                                     \
   do {                                                                                       \
     cudaError_t e_ = (expr);                                                                 \
@@ -181,6 +189,11 @@ struct Grid {
   DevMem ws_alm, ws_F, ws_part, ws_out;
 };
 
+// the grid behind a handle, or nullptr if the handle is not a live grid
+inline Grid* as_grid(const void* h) {
+  return handle_live(HANDLE_GRID, h) ? const_cast<Grid*>(static_cast<const Grid*>(h)) : nullptr;
+}
+
 // ---- launchers (legendre.cu) ----
 // alm: [nmaps][nlm] complex coefficients multiplied by c_lm; F: [nmaps][nring][L+1]
 int legendre_synth(const Grid& g, int prec, int nmaps, const void* alm, void* F, cudaStream_t s);
@@ -229,6 +242,9 @@ inline bool valid_prec(int prec) {
 int legendre_synth_df(const Grid& g, int nmaps, const void* alm, void* F, cudaStream_t s);
 // ---- tensor-core Legendre synthesis (legendre_tc.cu), prec CMBWS_TF32 / CMBWS_3XTF32 ----
 int legendre_synth_tc(const Grid& g, int prec, int nmaps, const void* alm, void* F, cudaStream_t s);
+// reads and clears the device-side status of the tensor-core kernels of the current device
+// (synchronous): *timed_out is true if a bounded mbarrier wait ran out since the last read
+int tc_status_take(bool* timed_out);
 // double-float adjoint from chunk checkpoints: F (FP64 ring spectra of nm maps) ->
 // out (FP64 coefficients); eo is a scratch of legendre_adjoint_part_bytes bytes
 int legendre_adj_df_ck(const Grid& g, int nm, const void* F, void* eo, double* out, cudaStream_t s);

@@ -198,7 +198,7 @@ extern "C" int cmbws_grad_terms(cmbws_model mh, const double* x, const double* l
                                 const double* const* d, const double* const* omega1,
                                 const double* omega2, double* out, void* stream) {
   clear_error();
-  Model* M = reinterpret_cast<Model*>(mh);
+  Model* M = as_model(mh);
   if (!M || !x || !lambda || !d || !out) {
     set_error("cmbws_grad_terms: invalid arguments");
     return CMBWS_ERR_ARG;

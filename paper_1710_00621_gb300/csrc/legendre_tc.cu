@@ -58,8 +58,19 @@ __device__ __forceinline__ void mma_tf32(uint32_t d, uint32_t a, uint64_t bdesc,
       "r"(a), "l"(bdesc), "r"(kIdesc), "r"(acc));
 }
 
-// Wait for the completion of phase `parity` of an mbarrier; false after the limit.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Device-side status of this file's kernels (one word per device): bit 0 is set when a
+// bounded mbarrier wait ran out; cmbws_device_status reads and clears it.
+__device__ unsigned int g_tc_status = 0;
+// Test support (cmbws_testing_stall_waits): when > 0, every CTA first waits at most this many
+// SM clocks on an mbarrier phase that nothing completes, so the wait runs out.
+__device__ long long g_tc_stall_cycles = 0;
+
+constexpr long long kWaitCycles = 1ll << 32;  // about two seconds at 2 GHz
+
+// Wait for the completion of phase `parity` of an mbarrier; false after `limit` SM clocks (or
+// 2^26 polls).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
+                                          long long limit = kWaitCycles) {
   const uint32_t a = smem_addr(bar);
   const long long t0 = clock64();
   for (int it = 0; it < (1 << 26); ++it) {
@@ -71,7 +82,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
         : "r"(a), "r"(parity)
         : "memory");
     if (done) return true;
-    if (clock64() - t0 > (1ll << 32)) break;  // about two seconds
+    if (clock64() - t0 > limit) break;
   }
   return false;
 }
@@ -91,8 +102,8 @@ struct TcLayout {
   static constexpr int kBStage = 4 * 512;                         // one 16 x 32 TF32 tile
   static constexpr int kStage = (SPLIT ? 2 : 1) * kBStage;        // hi (+ lo) per stage
   static constexpr int kOffA = 2 * kStage;                        // float sAc[2][4][32]: A, B, R, S
-  static constexpr int kOffBar = kOffA + 2 * 4 * kTcKB * 4;       // uint64_t mbar[2]
-  static constexpr int kOffT = kOffBar + 16;                      // uint32_t tmem base, bad flag
+  static constexpr int kOffBar = kOffA + 2 * 4 * kTcKB * 4;       // uint64_t mbar[3]
+  static constexpr int kOffT = kOffBar + 24;                      // uint32_t tmem base, bad flag
   static constexpr int kUsed = kOffT + 16;
   // Shared memory requested per CTA: caps residency so that the CTAs of an SM never ask
   // for more than its 512 tensor-memory columns (4 x 128 or 2 x 256).
@@ -163,7 +174,12 @@ k_leg_synth_tc(const float2* __restrict__ alm, int64_t alm_stride, const float* 
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&mbar[0])));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&mbar[1])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&mbar[2])));
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
+    // test support: a wait on mbar[2], which no thread or copy ever arrives at, runs out;
+    // the CTA then issues no MMA and writes NaN, as after a failed wait on a stage
+    const long long stall = g_tc_stall_cycles;
+    if (stall > 0 && !mbar_wait(&mbar[2], 0, stall)) *s_bad = 1;
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
   __syncthreads();
@@ -325,6 +341,7 @@ k_leg_synth_tc(const float2* __restrict__ alm, int64_t alm_stride, const float* 
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
   __syncthreads();
   const bool failed = *s_bad != 0;
+  if (failed && tid == 0) atomicOr(&g_tc_status, 1u);
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tb), "r"(LY::kCols));
   if (!valid) return;
   const int2 rr = pring[p];
@@ -385,4 +402,40 @@ int legendre_synth_tc(const Grid& g, int prec, int nmaps, const void* alm, void*
   return CMBWS_OK;
 }
 
+int tc_status_take(bool* timed_out) {
+  unsigned int v = 0;
+  CMBWS_CUDA(cudaMemcpyFromSymbol(&v, g_tc_status, sizeof(v)));
+  *timed_out = (v & 1u) != 0;
+  if (v) {
+    const unsigned int zero = 0;
+    CMBWS_CUDA(cudaMemcpyToSymbol(g_tc_status, &zero, sizeof(zero)));
+  }
+  return CMBWS_OK;
+}
+
 }  // namespace cmbws
+
+using namespace cmbws;
+
+extern "C" int cmbws_device_status(void* stream) {
+  clear_error();
+  CMBWS_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  bool to = false;
+  CMBWS_TRY(tc_status_take(&to));
+  if (to) {
+    set_error("a bounded device-side wait ran out in a tensor-core Legendre kernel; its outputs "
+              "hold NaN");
+    return CMBWS_ERR_TIMEOUT;
+  }
+  return CMBWS_OK;
+}
+
+extern "C" int cmbws_testing_stall_waits(long long wait_cycles) {
+  clear_error();
+  if (wait_cycles < 0 || wait_cycles > kWaitCycles) {
+    set_error("cmbws_testing_stall_waits: wait_cycles must be in [0, 2^32]");
+    return CMBWS_ERR_ARG;
+  }
+  CMBWS_CUDA(cudaMemcpyToSymbol(g_tc_stall_cycles, &wait_cycles, sizeof(wait_cycles)));
+  return CMBWS_OK;
+}

@@ -471,7 +471,7 @@ using namespace cmbws;
 extern "C" int cmbws_model_add_mask_precond(cmbws_model mh, int comp, int nside, const double* mask,
                                             int max_bottom, void* stream) {
   clear_error();
-  Model* M = reinterpret_cast<Model*>(mh);
+  Model* M = as_model(mh);
   if (!M || !mask || comp < 0 || comp >= M->ncomp || nside < 1 || max_bottom < 1 ||
       max_bottom > 4096) {
     set_error("cmbws_model_add_mask_precond: invalid arguments");
@@ -488,7 +488,7 @@ extern "C" int cmbws_model_add_mask_precond(cmbws_model mh, int comp, int nside,
 
 extern "C" int cmbws_model_set_vcycle(cmbws_model mh, int kind) {
   clear_error();
-  Model* M = reinterpret_cast<Model*>(mh);
+  Model* M = as_model(mh);
   if (!M || (kind != 0 && kind != 1)) {
     set_error("cmbws_model_set_vcycle: invalid arguments (kind 0 = basic, 1 = optimized)");
     return CMBWS_ERR_ARG;
@@ -500,7 +500,7 @@ extern "C" int cmbws_model_set_vcycle(cmbws_model mh, int kind) {
 
 extern "C" int cmbws_apply_M_add(cmbws_model mh, const double* r, double* z, void* stream) {
   clear_error();
-  Model* M = reinterpret_cast<Model*>(mh);
+  Model* M = as_model(mh);
   if (!M || !r || !z || r == z) {
     set_error("cmbws_apply_M_add: invalid arguments");
     return CMBWS_ERR_ARG;

@@ -259,7 +259,7 @@ using namespace cmbws;
 
 extern "C" int cmbws_model_merge_precond(cmbws_model mh, const int* group, void* stream) {
   clear_error();
-  Model* M = reinterpret_cast<Model*>(mh);
+  Model* M = as_model(mh);
   if (!M) {
     set_error("cmbws_model_merge_precond: invalid model");
     return CMBWS_ERR_ARG;

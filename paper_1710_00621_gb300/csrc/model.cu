@@ -708,7 +708,7 @@ int model_create(const cmbws_model_desc* desc, int prec, cudaStream_t s, Model**
   M->band_group.resize(no);
   M->band_slot.resize(no);
   for (int nu = 0; nu < no; ++nu) {
-    Grid* g = reinterpret_cast<Grid*>(desc->band_grid[nu]);
+    Grid* g = as_grid(desc->band_grid[nu]);
     if (!g || g->device != dev) {
       set_error("cmbws_model_create: band %d has no grid on the current device", nu);
       return CMBWS_ERR_ARG;
@@ -819,7 +819,7 @@ int model_create(const cmbws_model_desc* desc, int prec, cudaStream_t s, Model**
       for (int k = 0; k < nc; ++k) {
         const int id = nu * nc + k;
         if (!desc->mix_map[id]) continue;
-        Grid* g = reinterpret_cast<Grid*>(desc->mix_grid[id]);
+        Grid* g = as_grid(desc->mix_grid[id]);
         if (!g || g->device != dev) {
           set_error("cmbws_model_create: mixing pair (%d, %d) has no grid on this device", nu, k);
           return CMBWS_ERR_ARG;
@@ -962,19 +962,25 @@ extern "C" int cmbws_model_create(const cmbws_model_desc* desc, cmbws_prec prec,
   Model* M = nullptr;
   int st = model_create(desc, (int)prec, (cudaStream_t)stream, &M);
   if (st != CMBWS_OK) return st;
+  handle_add(HANDLE_MODEL, M);
   *out = reinterpret_cast<cmbws_model>(M);
   return CMBWS_OK;
 }
 
 extern "C" int cmbws_model_destroy(cmbws_model mh) {
   clear_error();
+  if (!mh) return CMBWS_OK;
+  if (!handle_del(HANDLE_MODEL, mh)) {
+    set_error("cmbws_model_destroy: not a live model handle (destroyed twice?)");
+    return CMBWS_ERR_ARG;
+  }
   delete reinterpret_cast<Model*>(mh);
   return CMBWS_OK;
 }
 
 extern "C" int cmbws_model_info(cmbws_model mh, int64_t* nvec, int* nsht_A, int* nsht_M) {
   clear_error();
-  Model* M = reinterpret_cast<Model*>(mh);
+  Model* M = as_model(mh);
   if (!M) {
     set_error("cmbws_model_info: null model");
     return CMBWS_ERR_ARG;
@@ -987,7 +993,7 @@ extern "C" int cmbws_model_info(cmbws_model mh, int64_t* nvec, int* nsht_A, int*
 
 extern "C" int cmbws_apply_A(cmbws_model mh, const double* x, double* y, void* stream) {
   clear_error();
-  Model* M = reinterpret_cast<Model*>(mh);
+  Model* M = as_model(mh);
   if (!M || !x || !y || x == y) {
     set_error("cmbws_apply_A: invalid arguments (x and y must be distinct device buffers)");
     return CMBWS_ERR_ARG;
@@ -997,7 +1003,7 @@ extern "C" int cmbws_apply_A(cmbws_model mh, const double* x, double* y, void* s
 
 extern "C" int cmbws_apply_precond(cmbws_model mh, const double* r, double* z, void* stream) {
   clear_error();
-  Model* M = reinterpret_cast<Model*>(mh);
+  Model* M = as_model(mh);
   if (!M || !r || !z || r == z) {
     set_error("cmbws_apply_precond: invalid arguments (r and z must be distinct device buffers)");
     return CMBWS_ERR_ARG;
@@ -1007,7 +1013,7 @@ extern "C" int cmbws_apply_precond(cmbws_model mh, const double* r, double* z, v
 
 extern "C" int cmbws_project(cmbws_model mh, const double* x, double* const* d, void* stream) {
   clear_error();
-  Model* M = reinterpret_cast<Model*>(mh);
+  Model* M = as_model(mh);
   if (!M || !x || !d) {
     set_error("cmbws_project: invalid arguments");
     return CMBWS_ERR_ARG;
@@ -1023,7 +1029,7 @@ extern "C" int cmbws_project(cmbws_model mh, const double* x, double* const* d, 
 extern "C" int cmbws_rhs(cmbws_model mh, const double* const* d, const double* const* omega1,
                          const double* omega2, double* b, void* stream) {
   clear_error();
-  Model* M = reinterpret_cast<Model*>(mh);
+  Model* M = as_model(mh);
   if (!M || !d || !b) {
     set_error("cmbws_rhs: invalid arguments");
     return CMBWS_ERR_ARG;

@@ -170,6 +170,11 @@ struct Model {
 
 int model_create(const cmbws_model_desc* desc, int prec, cudaStream_t s, Model** out);
 
+// the model behind a handle, or nullptr if the handle is not a live model
+inline Model* as_model(const void* h) {
+  return handle_live(HANDLE_MODEL, h) ? const_cast<Model*>(static_cast<const Model*>(h)) : nullptr;
+}
+
 // One-sided Jacobi SVD pseudo-inverse of an (nr x nc) row-major matrix, out (nc x nr);
 // singular values below rcond * max are dropped.  false if a column is zero.
 bool pinv_jacobi(const std::vector<double>& Uin, int nr, int nc, double rcond,

@@ -65,7 +65,7 @@ using namespace cmbws;
 extern "C" int cmbws_sht_analysis_noalloc(cmbws_grid gh, cmbws_prec prec, const double* map,
                                           double* alm, int nmaps, int weighted, void* stream) {
   clear_error();
-  Grid* g = reinterpret_cast<Grid*>(gh);
+  Grid* g = as_grid(gh);
   if (!g || !alm || !map || nmaps < 1 || (prec != CMBWS_FP64 && prec != CMBWS_FP32)) {
     set_error("cmbws_sht_analysis_noalloc: invalid arguments");
     return CMBWS_ERR_ARG;

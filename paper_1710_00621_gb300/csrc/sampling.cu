@@ -140,7 +140,7 @@ extern "C" int cmbws_cr_sample(cmbws_model mh, const double* const* d, uint64_t 
                                uint64_t sample, double* x, const cmbws_cg_opts* opts,
                                cmbws_cg_report* report, void* stream) {
   clear_error();
-  Model* M = reinterpret_cast<Model*>(mh);
+  Model* M = as_model(mh);
   if (!M || !d || !x || !opts) {
     set_error("cmbws_cr_sample: invalid arguments");
     return CMBWS_ERR_ARG;
@@ -159,7 +159,7 @@ extern "C" int cmbws_cr_sample(cmbws_model mh, const double* const* d, uint64_t 
 extern "C" int cmbws_cr_rhs(cmbws_model mh, const double* const* d, uint64_t seed,
                             uint64_t sample, double* b, void* stream) {
   clear_error();
-  Model* M = reinterpret_cast<Model*>(mh);
+  Model* M = as_model(mh);
   if (!M || !d || !b) {
     set_error("cmbws_cr_rhs: invalid arguments");
     return CMBWS_ERR_ARG;

@@ -594,6 +594,7 @@ extern "C" int cmbws_plan_grid(cmbws_grid_kind kind, int n, int lmax, cmbws_grid
     delete g;
     return s;
   }
+  handle_add(HANDLE_GRID, g);
   *out = reinterpret_cast<cmbws_grid>(g);
   return CMBWS_OK;
 }
@@ -601,7 +602,7 @@ extern "C" int cmbws_plan_grid(cmbws_grid_kind kind, int n, int lmax, cmbws_grid
 extern "C" int cmbws_grid_info(cmbws_grid gh, int64_t* npix, int* nring, const double** theta,
                                const double** weight) {
   clear_error();
-  Grid* g = reinterpret_cast<Grid*>(gh);
+  Grid* g = as_grid(gh);
   if (!g) {
     set_error("cmbws_grid_info: null grid");
     return CMBWS_ERR_ARG;
@@ -616,7 +617,7 @@ extern "C" int cmbws_grid_info(cmbws_grid gh, int64_t* npix, int* nring, const d
 extern "C" int cmbws_grid_rings(cmbws_grid gh, const double** phi0, const int** nphi,
                                 const int64_t** offset, int* lmax) {
   clear_error();
-  Grid* g = reinterpret_cast<Grid*>(gh);
+  Grid* g = as_grid(gh);
   if (!g) {
     set_error("cmbws_grid_rings: null grid");
     return CMBWS_ERR_ARG;
@@ -630,6 +631,11 @@ extern "C" int cmbws_grid_rings(cmbws_grid gh, const double** phi0, const int** 
 
 extern "C" int cmbws_grid_destroy(cmbws_grid gh) {
   clear_error();
+  if (!gh) return CMBWS_OK;
+  if (!handle_del(HANDLE_GRID, gh)) {
+    set_error("cmbws_grid_destroy: not a live grid handle (destroyed twice?)");
+    return CMBWS_ERR_ARG;
+  }
   delete reinterpret_cast<Grid*>(gh);
   return CMBWS_OK;
 }

@@ -206,3 +206,49 @@ def test_full_size_sampled_rings_nside1024(prec):
         # accumulations of L terms in different orders (the FP32 bound)
         bound = tol(cw.CMBWS_TF32, L) if prec == cw.CMBWS_TF32 else tol(cw.CMBWS_FP32, L)
         assert rel_err(gsub, g32) < bound, rel_err(gsub, g32)
+
+
+SAMPLED_M = [0, 1, 2, 700, 1535, 3000, 3071]
+
+
+def full_size_adjoint_tol(prec):
+    """Bound on the sampled-m adjoint at HEALPix Nside 1024, L = 3071 (see FULL_SIZE_TOL)."""
+    return FULL_SIZE_TOL[prec]
+
+
+# Parity bounds at the full band size (relative to the largest sampled output):
+# FP64 and double-float restart their recurrences from FP64-accurate values (the synthesis at
+# every pair's start, the double-float adjoint every 4 values of l) and accumulate up to 2048
+# ring pairs; FP32 restarts every 8 values of l from checkpoints but rounds every product and
+# partial sum to 24 bits.
+FULL_SIZE_TOL = {cw.CMBWS_FP64: 1e-11, cw.CMBWS_FP32X2: 1e-11, cw.CMBWS_FP32: 1e-4}
+
+
+@pytest.fixture(scope="module")
+def nside1024():
+    g = cw.cmbws_plan_grid(cw.CMBWS_GRID_HEALPIX, 1024, 3071)
+    return g, og.healpix(1024)
+
+
+@pytest.mark.parametrize("weighted", [0, 1])
+@pytest.mark.parametrize("prec", [cw.CMBWS_FP64, cw.CMBWS_FP32X2, cw.CMBWS_FP32])
+def test_full_size_adjoint_sampled_orders_nside1024(nside1024, prec, weighted):
+    """Adjoint synthesis / analysis of three maps at HEALPix Nside 1024, L = 3071 (the
+    bench's largest band grid, three bands per launch as in its solves) against the oracle on
+    every l of a sample of orders m, from m = 0 to m = L: the Legendre stage is independent
+    per m, so the oracle evaluates those columns exactly."""
+    g, o = nside1024
+    L, nmaps = 3071, 3
+    rng = np.random.default_rng(31 + weighted)
+    maps = rng.standard_normal((nmaps, g.npix))
+    out = to_dev(np.zeros((nmaps, (L + 1) ** 2)))
+    cw.cmbws_sht_analysis(g, prec, to_dev(maps), out, nmaps, weighted)
+    got = to_host(out)
+    errs = []
+    for k in range(nmaps):
+        ref = osht.adjoint_m(o, L, maps[k], SAMPLED_M, weighted=bool(weighted))
+        gv = np.concatenate([np.concatenate(osht.packed_m(got[k], L, m)) for m in SAMPLED_M])
+        rv = np.concatenate([np.concatenate(ref[m]) for m in SAMPLED_M])
+        errs.append(rel_err(gv, rv))
+    print(f"full-size adjoint prec={prec} weighted={weighted}: max rel err {max(errs):.3e}")
+    assert max(errs) < full_size_adjoint_tol(prec), errs

@@ -130,6 +130,25 @@ def test_wiener_solve_fp64_and_fp32_refined(models, name):
         assert rel_err(to_host(x), xo) < 1e-4, (prec, rep)
 
 
+def test_multires_fp64_solve_matches_oracle_solution_to_1e6(models):
+    """FP64 mode: the multi-resolution model at 1/16 of the benchmark's resolution (HEALPix
+    Nside 16/32/64 bands, L_nu up to 191, three components) solved to a residual of 1e-10 lies
+    within 1e-6 of the oracle's own solution (its FP64 PCG run to 1e-12)."""
+    work, m, inp = models["multires16"]
+    d = [mp + n for mp, n in zip(om.project(m, inp["x_true"]), inp["noise"])]
+    b = om.rhs(m, d)
+    xo, _ = pcg(lambda v: om.apply_A(m, v), b, lambda v: opc.apply_precond(m, v), tol=1e-12,
+                maxiter=2000)
+    g, _ = gpu_model(work, inp, cw.CMBWS_FP64)
+    x = to_dev(np.zeros(m.nvec()))
+    rep = cw.cmbws_cg_solve(g, to_dev(b), x, tol=1e-10, maxiter=2000)
+    assert rep["rel_res"] <= 1e-10
+    err = float(np.linalg.norm(to_host(x) - xo) / np.linalg.norm(xo))
+    print(f"multires FP64 solve: {rep['iters']} iterations, |x - x_oracle| / |x_oracle| = {err:.2e}")
+    assert err <= 1e-6
+    assert rel_err(to_host(x), xo) <= 1e-6
+
+
 def test_invalid_calls_return_error_codes(models):
     work, m, inp = models["tiny15"]
     g, grids = gpu_model(work, inp)

@@ -45,3 +45,15 @@ def test_invalid_arguments_are_rejected_without_a_gpu(lib):
     assert b"invalid" in lib.cmbws_last_error()
     assert lib.cmbws_apply_A(None, None, None, None) == -1
     assert lib.cmbws_cg_solve(None, None, None, None, None, None) == -1
+
+
+def test_handles_that_were_never_issued_are_rejected_without_a_gpu(lib):
+    # a pointer that the library never handed out is not dereferenced
+    fake = ctypes.c_void_p(0x1234560)
+    buf = ctypes.c_void_p(0x1000)
+    assert lib.cmbws_apply_A(fake, buf, ctypes.c_void_p(0x2000), None) == -1
+    assert lib.cmbws_model_destroy(fake) == -1
+    assert lib.cmbws_grid_destroy(fake) == -1
+    assert lib.cmbws_sht_synth(fake, 0, buf, buf, 1, None) == -1
+    n = ctypes.c_int64()
+    assert lib.cmbws_model_info(fake, ctypes.byref(n), None, None) == -1

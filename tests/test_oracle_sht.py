@@ -4,6 +4,7 @@ import pytest
 from scipy.special import sph_harm_y
 
 from oracle import alm, grids, sht
+from oracle.legendre import lambda_all, lambda_m
 
 
 def _real_Y_scipy(grid, lmax):
@@ -91,3 +92,29 @@ def test_adjoint_identity(grid, lmax):
     lhs = sht.synthesis(grid, lmax, a) @ f
     rhs = a @ sht.adjoint(grid, lmax, f)
     assert abs(lhs - rhs) <= 1e-12 * abs(lhs) * 100 + 1e-10
+
+
+@pytest.mark.parametrize("kind,n,lmax", [("gl", 31, 31), ("hp", 16, 47), ("hp", 8, 40)])
+@pytest.mark.parametrize("weighted", [False, True])
+def test_adjoint_of_sampled_orders_equals_full_adjoint(kind, n, lmax, weighted):
+    # the per-m form (used for full-size checks on a sample of m) against the full adjoint,
+    # itself pinned by the dense Y and the adjoint identity
+    g = grids.gauss_legendre(lmax) if kind == "gl" else grids.healpix(n)
+    f = np.random.default_rng(lmax + n).standard_normal(g.npix)
+    full = sht.adjoint(g, lmax, f, weighted=weighted)
+    ms = [0, 1, 2, lmax // 2, lmax - 1, lmax]
+    got = sht.adjoint_m(g, lmax, f, ms, weighted=weighted)
+    scale = np.abs(full).max()
+    for m in ms:
+        c, s = sht.packed_m(full, lmax, m)
+        np.testing.assert_allclose(got[m][0], c, atol=1e-13 * scale, rtol=0)
+        np.testing.assert_allclose(got[m][1], s, atol=1e-13 * scale, rtol=0)
+
+
+def test_lambda_of_one_order_equals_the_triangle_walk():
+    theta = grids.healpix(64).theta
+    tab = {l: lam for l, lam in lambda_all(300, theta)}
+    for m in (0, 3, 150, 299, 300):
+        lm = lambda_m(m, 300, theta)
+        ref = np.stack([tab[l][m] for l in range(m, 301)])
+        np.testing.assert_allclose(lm, ref, rtol=0, atol=1e-14 * max(np.abs(ref).max(), 1e-300))
