@@ -16,8 +16,9 @@ The library's kernel-timing records (CUDA events on the launching stream) give t
 time and the roofline of the dominant kernel.  --gpus N runs N independent replicas (one
 per rank) and reports the max time over ranks; there is no data-path collective.
 
---impl reference times the FP64 NumPy oracle on the host on a bounded sample (one SHT
-pair of the Nside-256 band grid) and scales it to the same solve.
+--impl reference times the FP64 NumPy oracle on every host core on a bounded sample (one
+SHT pair of the Nside-192 grid per core) and scales it to the same solve, with the
+oracle's own PCG iteration count (measured on the model at 1/16 resolution).
 """
 import argparse
 import json
@@ -177,7 +178,7 @@ def build_problem(work, prec, seed_offset=0):
     for nu in range(len(d)):
         d[nu] += torch.as_tensor(inp["noise"][nu], device=dev)
     torch.cuda.synchronize()
-    return dict(grids=band_grids, inp=inp, m64=m64, model=m_run, d=d, x_true=x_true)
+    return dict(grids=band_grids, inp=inp, m64=m64, model=m_run, d=d, x_true=x_true, ninv=ninv)
 
 
 INNER_TOL = [1e-3]
@@ -618,84 +619,165 @@ def precision_report(nside=1024, nmaps=3, reps=3):
     return out
 
 
-# FP32-pipe flops per (l, m, ring pair) element with three maps per grid group (six real
-# parts): FP32 kernels 2 FMA for the recurrence + 6 for the contraction (16 flops, the SHT
-# flop count itself); double-float kernels: a double-float recurrence step costs 39 FP32
-# flops (product 10, difference 11, fused multiply-subtract 18) and one compensated Dot2
-# update 15 (FMUL + 3 FFMA + 8 FADD); the synthesis steps the recurrence at every l, the
+# Implementation flops on the FP32 pipe per (l, m, ring pair) element, as a + b * maps: FP32
+# kernels 2 FMA for the recurrence + 2 per map for the contraction (the SHT flop count
+# itself); double-float kernels: a double-float recurrence step costs 39 FP32 flops
+# (product 10, difference 11, fused multiply-subtract 18) and one compensated Dot2 update 15
+# (FMUL + 3 FFMA + 8 FADD), two per map; the synthesis steps the recurrence at every l, the
 # adjoint at half of them (the other half restart from the double-float checkpoints).
-FP32_FLOPS_PER_ELEM = {("legendre_synth", "fp32"): 16.0, ("legendre_adjoint", "fp32"): 16.0,
-                       ("legendre_synth", "fp32x2"): 39.0 + 6 * 15.0,
-                       ("legendre_adjoint", "fp32x2"): 0.5 * 39.0 + 6 * 15.0}
+IMPL_FLOPS = {("legendre_synth", "fp32"): (4.0, 4.0), ("legendre_adjoint", "fp32"): (4.0, 4.0),
+              ("legendre_synth", "fp32x2"): (39.0, 30.0),
+              ("legendre_adjoint", "fp32x2"): (19.5, 30.0)}
 
 
-# DRAM bytes (read + write) per element from one ncu capture of the kernel as it stands,
-# on the Nside 512, L = 1535, 3-map case (profiles/k_leg_adj_ck_df_healpix512_l1535_3maps.md):
-# 4.083 GB / 1.209e9 elements; the checkpoint table dominates, so it scales with the
-# elements.  Emptied whenever the kernel changes until it is captured again.
+# DRAM bytes (read + write) per element from one ncu capture of the kernel as it stands
+# (the Nside 512, L = 1535, 3-map case): 4.083 GB / 1.209e9 elements; the checkpoint table
+# dominates, so it scales with the elements.  Emptied whenever the kernel changes until it
+# is captured again.
 DRAM_BYTES_PER_ELEM = {("legendre_adjoint", "fp32x2"): 3.38}
+
+
+def measured_peaks():
+    """HBM copy bandwidth (GB/s) from MEASURED_PEAKS.json, else the recipe's fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "of measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "of fallback"
 
 
 def roofline(prof):
     """Dominant kernel (by summed time) among the Legendre stages, with its achieved rate.
 
-    Every Legendre kernel of the step runs on the FP32 pipe (the FP64-accurate ones in
-    double-float arithmetic), so the peak is the derived FP32 rate and `achieved` counts the
-    FP32 flops each kernel's algorithm executes per (l, m, ring pair) element."""
+    `achieved` is the method's own work (the SHT flop count: 4 flops per (l, m, ring pair)
+    for the recurrence plus 4 per map, over the full (l, m) triangle) per second; every
+    Legendre kernel of the step runs on the FP32 pipe (the FP64-accurate ones in double-float
+    arithmetic), so the peak is the derived FP32 rate.  `impl_achieved` counts the FP32 flops
+    the kernel's algorithm executes (IMPL_FLOPS), which for double-float is several times the
+    method's."""
     best = None
-    for (stage, prec), (ms, n, fl) in prof.items():
+    for (stage, prec), v in prof.items():
+        ms, n = v[0], v[1]
         if stage not in ("legendre_synth", "legendre_adjoint") or n == 0:
             continue
         if best is None or ms > best[2]:
-            best = (stage, prec, ms, n, fl)
+            best = (stage, prec, ms, n, v)
     if best is None:
         return None
-    stage, prec, ms, n, fl = best
-    elems = fl / 16.0                     # the profiler's count is 4 (NM + 1) flops, NM = 3
-    per = FP32_FLOPS_PER_ELEM.get((stage, prec))
-    if per is None:
-        return None
-    achieved = elems * per / (ms * 1e-3) / 1e12
-    bpe = DRAM_BYTES_PER_ELEM.get((stage, prec))
-    traffic = round(bpe * elems / n) if bpe else None
+    stage, prec, ms, n, v = best
+    fl, elems, melems = v[2], v[3], v[4]
+    achieved = fl / (ms * 1e-3) / 1e12
     out = {"bound": "alu", "kernel": f"{stage}_{prec}", "achieved": round(achieved, 3),
            "peak": round(FP32_PEAK_TFLOPS, 2), "unit": "TFLOP/s",
-           "frac": round(achieved / FP32_PEAK_TFLOPS, 4), "traffic": traffic, "launches": n,
+           "frac": round(achieved / FP32_PEAK_TFLOPS, 4), "traffic": None, "launches": n,
            "avg_launch_ms": round(ms / n, 4),
            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (of derived)",
-           "flops_per_element": per}
+           "work": "method flops: 4 (1 + maps) per (l, m, ring pair), full triangle",
+           "elements_per_launch": round(elems / n)}
+    ab = IMPL_FLOPS.get((stage, prec))
+    if ab is not None:
+        impl = (ab[0] * elems + ab[1] * melems) / (ms * 1e-3) / 1e12
+        out["impl_achieved"] = round(impl, 3)
+        out["impl_frac"] = round(impl / FP32_PEAK_TFLOPS, 4)
+        out["impl_flops_per_element"] = round((ab[0] * elems + ab[1] * melems) / elems, 2)
+    bpe = DRAM_BYTES_PER_ELEM.get((stage, prec))
+    if bpe:
+        out["traffic"] = round(bpe * elems / n)
     if prec == "fp32x2":
-        out["fp64_accurate_sht_tflops"] = round(fl / (ms * 1e-3) / 1e12, 3)
-        out["note"] = ("double-float kernel: achieved counts the FP32 flops of the double-float "
-                       "algorithm; its FADD share caps it near 0.6 of the FMA-counted peak")
+        out["note"] = ("double-float kernel (FP64-accurate on the FP32 pipe): the method's flops "
+                       "cost impl_flops_per_element FP32 flops here; GB300's FP64 pipe peaks at "
+                       f"{FP64_PEAK_TFLOPS} TFLOP/s")
     return out
 
 
-def cpu_baseline(work, gpu_iters_fp64, sample_nside=256):
-    """Time the FP64 oracle on one SHT pair of one band grid and scale to the whole solve."""
+def fft_roofline(prof):
+    """The ring FFT stage with the largest summed time, as an HBM stream: algorithmic bytes
+    (ring spectra read and written once, pixel factors or maps once) per second."""
+    best = None
+    for (stage, prec), v in prof.items():
+        if stage != "ring_fft" or v[1] == 0 or v[5] <= 0:
+            continue
+        if best is None or v[0] > best[2]:
+            best = (stage, prec, v[0], v[1], v[5])
+    if best is None:
+        return None
+    stage, prec, ms, n, byts = best
+    peak, src = measured_peaks()
+    achieved = byts / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": f"{stage}_{prec}", "achieved": round(achieved, 1),
+            "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+            "launches": n, "avg_launch_ms": round(ms / n, 4),
+            "bytes_per_launch": round(byts / n), "peak_source": f"HBM copy bandwidth ({src})"}
+
+
+def _oracle_sht_pair(args):
+    """One synthesis + adjoint-synthesis pair of the FP64 oracle on a HEALPix grid (a worker of
+    the CPU baseline); returns its wall time in seconds."""
+    nside, seed = args
     from oracle import grids as og, sht as osht
-    nside = sample_nside // 1
     L = 3 * nside - 1
     g = og.healpix(nside)
-    a = np.random.default_rng(0).standard_normal((L + 1) ** 2)
+    a = np.random.default_rng(seed).standard_normal((L + 1) ** 2)
     t0 = time.perf_counter()
     f = osht.synthesis(g, L, a)
     osht.adjoint(g, L, f)
-    t_pair = time.perf_counter() - t0
-    unit_sample = (2 * nside) * (L + 1) * (L + 2) / 2          # ring pairs x (l, m) pairs
+    return time.perf_counter() - t0
+
+
+def _oracle_warm(_):
+    from oracle import grids, sht  # noqa: F401
+    return os.getpid()
+
+
+def cpu_baseline(work, iters_fp64, sample_nside=192):
+    """The FP64 oracle on every host core: one SHT pair of the Nside-192 grid (L = 575) per core,
+    run concurrently in spawned processes (single-threaded NumPy / BLAS each), scaled by ring
+    pairs x (l, m) pairs to the 9 bands and by the iteration count (+ RHS + certification)."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_warm, range(cores))                      # start-up outside the timing
+        t0 = time.perf_counter()
+        secs = pool.map(_oracle_sht_pair, [(sample_nside, i) for i in range(cores)], chunksize=1)
+        wall = time.perf_counter() - t0
+    L = 3 * sample_nside - 1
+    unit_sample = (2 * sample_nside) * (L + 1) * (L + 2) / 2       # ring pairs x (l, m) pairs
+    t_pair = wall / cores                                         # throughput of all cores
     # one PCG iteration = A + M_PI = 2 SHT pairs per band
     per_iter = 0.0
     for b in work.bands:
-        npair = 2 * b.n
-        per_iter += 2 * npair * (b.lmax + 1) * (b.lmax + 2) / 2
-    iters = max(gpu_iters_fp64, 1) + 2                            # + RHS and certification
+        per_iter += 2 * (2 * b.n) * (b.lmax + 1) * (b.lmax + 2) / 2
+    iters = max(int(iters_fp64), 1) + 2                            # + RHS and certification
     est = t_pair * per_iter * iters / unit_sample
-    return {"value": round(est, 1), "unit": "s", "cores": 1, "kind": "oracle",
-            "host_cpus": os.cpu_count(),
-            "sample": (f"one synthesis + adjoint-synthesis pair of the FP64 NumPy oracle on the "
-                       f"HEALPix Nside {nside} grid (L = {L}) took {t_pair:.2f} s; scaled by ring "
-                       f"pairs x (l, m) pairs to the {len(work.bands)} bands and to {iters} "
-                       f"iterations (the GPU FP64 solve's count + RHS + certification)")}
+    return {"value": round(est, 1), "unit": "s", "cores": cores, "kind": "oracle",
+            "threads_per_process": {"OMP_NUM_THREADS": 1, "OPENBLAS_NUM_THREADS": 1},
+            "sample": (f"{cores} synthesis + adjoint-synthesis pairs of the FP64 NumPy oracle on "
+                       f"the HEALPix Nside {sample_nside} grid (L = {L}), one per core in spawned "
+                       f"processes, took {wall:.2f} s wall (per pair {min(secs):.2f}-{max(secs):.2f} s); "
+                       f"scaled by ring pairs x (l, m) pairs to the {len(work.bands)} bands and to "
+                       f"{iters} iterations ({int(iters_fp64)} PCG iterations to 1e-6 + RHS + "
+                       "certification); an extrapolation")}
+
+
+def oracle_iterations(tol=1e-6, scale=16):
+    """PCG iterations of the oracle (M_PI, FP64) to `tol` on the benchmark model at 1/scale of
+    its resolution (the pseudo-inverse preconditioner's count hardly depends on resolution)."""
+    from oracle import grids as og, model as om, precond as opc
+    from oracle.cg import pcg
+    w = workload(scale)
+    gs = [og.healpix(b.n) for b in w.bands]
+    coords = [(np.cos(g.pixel_angles()[0]), g.pixel_angles()[1]) for g in gs]
+    inp = skygen.make_inputs(w, coords, [g.pixel_weights() for g in gs])
+    m = om.Model(lmax_comp=[c.lmax for c in w.comps], grids=gs, lmax_band=[b.lmax for b in w.bands],
+                 beam=inp["beams"], cl=inp["cl"], tau=inp["tau"], q=inp["q"])
+    d = [mp_ + n for mp_, n in zip(om.project(m, inp["x_true"]), inp["noise"])]
+    b = om.rhs(m, d)
+    _, info = pcg(lambda v: om.apply_A(m, v), b, lambda v: opc.apply_precond(m, v), tol=tol,
+                  maxiter=500)
+    return info["iters"]
 
 
 def run_reference(args):
@@ -703,17 +785,21 @@ def run_reference(args):
     if rank != 0:
         return
     work = workload(args.scale)
+    iters = oracle_iterations(args.tol)
     times = []
     for _ in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        cb = cpu_baseline(work, 25)
+        cb = cpu_baseline(work, iters)
         times.append(cb["value"])
     v = float(np.median(times[args.warmup:])) if args.steps else times[-1]
+    cb = dict(cb, value=v)
     line = {"impl": "reference", "metric": "Wiener solve time to 1e-6 residual", "value": v,
             "unit": "s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": work.name, "solve": "oracle PCG with M_PI (extrapolated)"},
+            "config": {"workload": work.name,
+                       "solve": (f"oracle PCG with M_PI, {iters} iterations to {args.tol} (the "
+                                 "oracle's own count on the model at 1/16 resolution), "
+                                 "extrapolated from per-core SHT-pair timings")},
             "cpu_baseline": cb, "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0,
                                          "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -810,6 +896,31 @@ def main():
                 "mixed_vs_fp64_rel_diff": diff}
         out["iters_fp64_plain"] = r64["iters"]
 
+    # the FP64-accurate solver on the FP32 pipe: every transform in double-float (48-bit
+    # significands), the fair plain-precision comparator on a GPU whose FP64 pipe runs at a
+    # 61st of the FP32 rate
+    fp32x2 = None
+    if not args.no_fp64_plain and args.prec == "fp32":
+        try:
+            inp = P["inp"]
+            mdf = cw.cmbws_model_create([c.lmax for c in work.comps], P["grids"], inp["beams"],
+                                        inp["cl"], P["ninv"], inp["q"], cw.CMBWS_FP32X2)
+            xdf = torch.zeros(n, dtype=torch.float64, device=dev)
+            for _ in range(2):                      # the first solve allocates the workspaces
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                rdf = solve_step(P, mdf, args.tol, xdf, b, cert="fp32x2")
+                torch.cuda.synchronize()
+                tdf = time.perf_counter() - t0
+            fp32x2 = {"s": round(tdf, 3), "iters": rdf["iters"], "rel_res_fp64": rdf["rel_res"],
+                      "mixed_vs_fp32x2_rel_diff": float(torch.linalg.vector_norm(x - xdf)
+                                                        / torch.linalg.vector_norm(xdf)),
+                      "note": ("plain PCG with every transform in double-float (FP64-accurate on "
+                               "the FP32 pipe), certified the same way")}
+            mdf.close()
+        except Exception as e:  # noqa: BLE001
+            fp32x2 = {"error": f"{type(e).__name__}: {e}"[:300]}
+
     # the paper's comparison (Sec. 5): the same solve with the block-diagonal preconditioner
     mdiag = None
     if not args.no_extras:
@@ -872,6 +983,7 @@ def main():
     if rank != 0:
         return
     rl = roofline(prof)
+    frl = fft_roofline(prof)
     cb = cpu_baseline(work, out.get("iters_fp64_plain", out["iters"])) if world == 1 else None
     stages = {f"{k[0]}_{k[1]}": {"ms": round(v[0], 3), "launches": v[1]} for k, v in prof.items() if v[1]}
     line = {"metric": "Wiener solve time to 1e-6 residual", "value": round(t_step, 4), "unit": "s",
@@ -888,13 +1000,14 @@ def main():
                        "l2": "inputs larger than L2, no flush",
                        "synthesis_tiles": ["default", "heuristic", "autotuned"][args.autotune],
                        "parallelism": f"replicas x{world}"},
-            "solve": out, "fp64_plain": fp64, "batched": batched, "masked_cr": masked_cr,
+            "solve": out, "fp64_plain": fp64, "fp32x2_plain": fp32x2, "batched": batched,
+            "masked_cr": masked_cr,
             "tiny": extras.get("tiny"), "differentiable": extras.get("differentiable"),
             "M_diag_comparison": mdiag,
             "cr_chain": crchain,
             "detector_splits": split,
             "precision": precision,
-            "roofline": rl, "cpu_baseline": cb, "e2e": e2e,
+            "roofline": rl, "roofline_ring_fft": frl, "cpu_baseline": cb, "e2e": e2e,
             "gpu_launches": launches, "stages": stages, "clocks": clk}
     print(json.dumps(line))
 

@@ -132,19 +132,22 @@ int cmbws_sht_analysis(cmbws_grid g, cmbws_prec prec, const double* map, double*
 /*
  * Same result as cmbws_sht_analysis, with no device allocation.  The paper has no
  * counterpart; this call exists for callers that cannot allocate device memory when
- * they need the transform: code running inside CUDA graph capture, runtimes that give
- * the library a fixed memory budget and forbid cudaMalloc after start-up, or loops that
- * must not block on the allocator.  Its workspace is one static device array of 32 MiB
- * (32 << 20 bytes) that every GPU loading the library holds until exit; a call whose
- * workspace (ring spectra nmaps * nring * (lmax+1) complex values, the Legendre adjoint's
- * per-block partial sums and the reduced coefficients) would exceed it returns
- * CMBWS_ERR_ARG with the bytes it needs.  The first call on a device looks up the
- * array's device address with cudaGetSymbolAddress (that device current); make that
- * first call before any stream capture.  Every call shares the array and overwrites what
- * it reads, so nothing carries over between calls, but calls whose kernels overlap on the
- * GPU race: serialise them.  Keep kernel timing (cmbws_profile_enable) off here, since it
- * creates CUDA events.  Arguments and layouts as for cmbws_sht_analysis; the grid's own
- * tables are allocated once by cmbws_plan_grid.
+ * they need the transform: runtimes that give the library a fixed memory budget and
+ * forbid cudaMalloc after start-up, or loops that must not block on the allocator
+ * (cudaMalloc can synchronise the device).  Its workspace is one static device array of
+ * 32 MiB (32 << 20 bytes) that every GPU loading the library holds until exit; a call
+ * whose workspace (ring spectra nmaps * nring * (lmax+1) complex values, the Legendre
+ * adjoint's per-block partial sums and the reduced coefficients) would exceed it returns
+ * CMBWS_ERR_ARG with the bytes it needs.  prec must be CMBWS_FP64 or CMBWS_FP32 (the other
+ * modes build tables on first use); another precision returns CMBWS_ERR_ARG naming it.
+ * The first call on a device looks up the array's device address with
+ * cudaGetSymbolAddress (that device current) and keeps it; make that first call before any
+ * stream capture, and do not use the library across a cudaDeviceReset, which makes the
+ * kept address stale.  Every call shares the array and overwrites what it reads, so nothing
+ * carries over between calls, but calls whose kernels overlap on the GPU race: serialise
+ * them.  Keep kernel timing (cmbws_profile_enable) off here, since it creates CUDA events.
+ * Other arguments and layouts as for cmbws_sht_analysis; the grid's own tables are
+ * allocated once by cmbws_plan_grid.
  */
 int cmbws_sht_analysis_noalloc(cmbws_grid g, cmbws_prec prec, const double* map, double* alm,
                                int nmaps, int weighted, void* stream);
@@ -339,13 +342,19 @@ int cmbws_grid_tuning(cmbws_grid g, int prec, int nmaps, int* variant, float* ms
  * 3 ring FFT, 4 harmonic-space kernels, 5 CG vector kernels; arith 0 = FP32, 1 = FP64,
  * 2 = double-float (CMBWS_FP32X2), 3 = TF32 tensor cores, 4 = split TF32 tensor cores.
  * cmbws_profile_read synchronises the recorded events and writes, per slot (host arrays
- * of 30, any may be NULL), the summed milliseconds, the launch count
- * and the summed algorithmic flops (Legendre stages: 4 flops per (l, m, ring pair) for
- * the recurrence plus 4 per map for the contraction, over the full (l, m) triangle;
- * 0 elsewhere) since the last reset; reset = 1 clears the record.
+ * of 30, any may be NULL), since the last reset:
+ *   ms: summed milliseconds; launches: launch count;
+ *   flops: summed algorithmic flops (Legendre stages: 4 per (l, m, ring pair) for the
+ *     recurrence plus 4 per map for the contraction, over the full (l, m) triangle);
+ *   elems: summed (l, m, ring pair) elements of the Legendre launches;
+ *   map_elems: summed elements x maps per launch (so flops = 4 (elems + map_elems));
+ *   bytes: summed algorithmic bytes of the ring FFT launches (ring spectra read and / or
+ *     written once, plus the pixel factors or FP64 maps once);
+ * 0 where a stage has no such count.  reset = 1 clears the record.
  */
 int cmbws_profile_enable(int on);
-int cmbws_profile_read(double* ms, int64_t* launches, double* flops, int reset);
+int cmbws_profile_read(double* ms, int64_t* launches, double* flops, double* elems,
+                       double* map_elems, double* bytes, int reset);
 
 typedef struct {
   double tol;         /* stop when ||b - A x||_2 / ||b||_2 <= tol, certified by an FP64 apply */

@@ -115,6 +115,7 @@ def load_library(path=None):
     lib.cmbws_device_status.argtypes = [vp]
     lib.cmbws_testing_stall_waits.argtypes = [ctypes.c_longlong]
     lib.cmbws_profile_read.argtypes = [ctypes.POINTER(d), ctypes.POINTER(ctypes.c_int64),
+                                       ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d),
                                        ctypes.POINTER(d), i]
     lib.cmbws_cg_solve.argtypes = [vp, vp, vp, ctypes.POINTER(CgOpts), ctypes.POINTER(CgReport), vp]
     lib.cmbws_cg_solve_batched.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(vp), ctypes.POINTER(vp),
@@ -528,16 +529,17 @@ PROFILE_ARITH = ("fp32", "fp64", "fp32x2", "tf32", "3xtf32")
 
 
 def cmbws_profile_read(reset=True):
-    """{(stage, arith): (milliseconds, launches, algorithmic flops)} since the last reset;
-    arith in PROFILE_ARITH."""
+    """{(stage, arith): (milliseconds, launches, algorithmic flops, elements, elements x maps,
+    algorithmic bytes)} since the last reset; arith in PROFILE_ARITH."""
     ns, na = len(PROFILE_STAGES), len(PROFILE_ARITH)
-    ms = (ctypes.c_double * (na * ns))()
+    arrs = [(ctypes.c_double * (na * ns))() for _ in range(5)]
     n = (ctypes.c_int64 * (na * ns))()
-    fl = (ctypes.c_double * (na * ns))()
-    _check(load_library().cmbws_profile_read(ms, n, fl, 1 if reset else 0))
+    ms, fl, el, me, by = arrs
+    _check(load_library().cmbws_profile_read(ms, n, fl, el, me, by, 1 if reset else 0))
     out = {}
     for i in range(na * ns):
-        out[(PROFILE_STAGES[i % ns], PROFILE_ARITH[i // ns])] = (ms[i], n[i], fl[i])
+        out[(PROFILE_STAGES[i % ns], PROFILE_ARITH[i // ns])] = (ms[i], n[i], fl[i], el[i], me[i],
+                                                                 by[i])
     return out
 
 

@@ -74,7 +74,7 @@ int DevMem::upload(const void* src, size_t n) {
 namespace {
 struct ProfRec {
   int slot;
-  double flops;
+  ProfWork work;
   cudaEvent_t a, b;
 };
 std::mutex g_prof_mu;
@@ -154,8 +154,8 @@ int autotune_pick(const Grid& g, int key, int nvar, int heuristic,
   return CMBWS_OK;
 }
 
-ProfScope::ProfScope(int stage, cudaStream_t s_, int arith, double flops_)
-    : slot(stage + PROF_N * arith), flops(flops_), s(s_) {
+ProfScope::ProfScope(int stage, cudaStream_t s_, int arith, ProfWork w)
+    : slot(stage + PROF_N * arith), work(w), s(s_) {
   if (!g_prof_on.load(std::memory_order_relaxed)) return;  // no lock on the common path
   std::lock_guard<std::mutex> lk(g_prof_mu);
   if (!g_prof_on) return;
@@ -172,7 +172,7 @@ ProfScope::~ProfScope() {
     return;
   }
   cudaEventRecord(b, s);
-  g_prof.push_back({slot, flops, a, b});
+  g_prof.push_back({slot, work, a, b});
 }
 
 int ensure_dyn_smem(const void* func, size_t bytes) {
@@ -257,23 +257,31 @@ extern "C" int cmbws_profile_enable(int on) {
   return CMBWS_OK;
 }
 
-extern "C" int cmbws_profile_read(double* ms, int64_t* launches, double* flops, int reset) {
+extern "C" int cmbws_profile_read(double* ms, int64_t* launches, double* flops, double* elems,
+                                  double* map_elems, double* bytes, int reset) {
   clear_error();
   std::lock_guard<std::mutex> lk(g_prof_mu);
-  double t[PROF_ARITH * PROF_N] = {0}, f[PROF_ARITH * PROF_N] = {0};
-  int64_t c[PROF_ARITH * PROF_N] = {0};
+  constexpr int NS = PROF_ARITH * PROF_N;
+  double t[NS] = {0}, f[NS] = {0}, e[NS] = {0}, me[NS] = {0}, by[NS] = {0};
+  int64_t c[NS] = {0};
   for (const ProfRec& r : g_prof) {
     CMBWS_CUDA(cudaEventSynchronize(r.b));
     float dt = 0.f;
     CMBWS_CUDA(cudaEventElapsedTime(&dt, r.a, r.b));
     t[r.slot] += dt;
-    f[r.slot] += r.flops;
+    f[r.slot] += r.work.flops;
+    e[r.slot] += r.work.elems;
+    me[r.slot] += r.work.melems;
+    by[r.slot] += r.work.bytes;
     c[r.slot] += 1;
   }
-  for (int i = 0; i < PROF_ARITH * PROF_N; ++i) {
+  for (int i = 0; i < NS; ++i) {
     if (ms) ms[i] = t[i];
     if (launches) launches[i] = c[i];
     if (flops) flops[i] = f[i];
+    if (elems) elems[i] = e[i];
+    if (map_elems) map_elems[i] = me[i];
+    if (bytes) bytes[i] = by[i];
   }
   if (reset) {
     for (const ProfRec& r : g_prof) {

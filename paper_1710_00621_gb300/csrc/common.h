@@ -268,8 +268,10 @@ int autotune_pick(const Grid& g, int key, int nvar, int heuristic,
 // ---- kernel timing (api.cu): CUDA events around launches while enabled ----
 // Stages; a record's slot is stage + PROF_N * arith, arith 0 = FP32, 1 = FP64,
 // 2 = double-float (FP32X2), 3 = TF32 tensor cores, 4 = split TF32 (PROF_ARITH kinds).
-// `flops` is the algorithmic count of the launch (full (l, m) triangle), 0 for stages
-// without one.
+// Each launch records its algorithmic work (ProfWork): Legendre stages their flops over the
+// full (l, m) triangle (4 per (l, m, ring pair) for the recurrence plus 4 per map), the
+// elements (l, m, ring pair) and elements x maps; ring FFTs the bytes they must move (ring
+// spectra and pixel factors or maps, read and written once).  0 for stages without one.
 enum {
   PROF_LEG_SYNTH = 0,
   PROF_LEG_ADJ = 1,
@@ -280,12 +282,28 @@ enum {
   PROF_N = 6,
   PROF_ARITH = 5
 };
+struct ProfWork {
+  double flops = 0, elems = 0, melems = 0, bytes = 0;
+};
+// the work of one Legendre launch over every (l, m, ring pair) of grid g with nm maps
+inline ProfWork leg_work(const Grid& g, int nm) {
+  ProfWork w;
+  w.elems = (double)g.npair * (double)nlm_of(g.lmax);
+  w.melems = w.elems * nm;
+  w.flops = 4.0 * (w.elems + w.melems);
+  return w;
+}
+inline ProfWork byte_work(double bytes) {
+  ProfWork w;
+  w.bytes = bytes;
+  return w;
+}
 struct ProfScope {
   int slot;
-  double flops;
+  ProfWork work;
   cudaStream_t s;
   cudaEvent_t a = nullptr;
-  ProfScope(int stage, cudaStream_t s_, int arith = 1, double flops_ = 0.0);
+  ProfScope(int stage, cudaStream_t s_, int arith = 1, ProfWork w = ProfWork());
   ~ProfScope();
 };
 

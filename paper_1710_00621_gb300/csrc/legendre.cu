@@ -588,7 +588,7 @@ int launch_synth_rn(const Grid& g, const void* alm, int64_t alm_stride, void* F,
   const T* A = std::is_same<T, double>::value ? (const T*)g.A64.p : (const T*)g.A32.p;
   const T2* st = std::is_same<T, double>::value ? (const T2*)g.st64.p : (const T2*)g.st32.p;
   const T* yr = std::is_same<T, double>::value ? (const T*)g.y64.p : (const T*)g.y32.p;
-  ProfScope ps(PROF_LEG_SYNTH, s, sizeof(T) == 8, 4.0 * g.npair * (double)nlm_of(L) * (NM + 1));
+  ProfScope ps(PROF_LEG_SYNTH, s, sizeof(T) == 8, leg_work(g, NM));
   k_leg_synth<T, NM, R, NT, C::SCH><<<grd, NT, 0, s>>>(
       (const T2*)alm, alm_stride, A, g.BRS32.as<float>(), g.ls.as<int>(), st, yr,
       g.pair_ring.as<int2>(), (T2*)F, F_stride, L, g.npair, g.nring);
@@ -650,7 +650,7 @@ int launch_adj_ck(const Grid& g, const void* F, int64_t F_stride, void* part, do
   constexpr size_t sm = sizeof(AdjCkWarp<NM, PT>) * (NT / 32);
   auto kern = k_leg_adj_ck<NM, NT, PT>;
   CMBWS_TRY(ensure_dyn_smem((const void*)kern, sm));
-  ProfScope ps(PROF_LEG_ADJ, s, 0, 4.0 * g.npair * (double)nlm * (NM + 1));
+  ProfScope ps(PROF_LEG_ADJ, s, 0, leg_work(g, NM));
   kern<<<grd, NT, sm, s>>>(eo, g.A32.as<float>(), g.ls.as<int>(), g.st32.as<float2>(),
                            g.y32.as<float>(), g.ck32.as<float2>(), g.ck_base.as<int64_t>(),
                            g.wt32.as<int2>(), g.nwt32, g.ls_tmin.as<int>(), g.c64.as<double>(),
@@ -675,7 +675,7 @@ int launch_adj(const Grid& g, const void* F, int64_t F_stride, T* part, double* 
     constexpr size_t sm = adj2_smem<T, NM>();
     auto kern = k_leg_adj2<T, NM, C::AR, C::ANT, C::ACH>;
     CMBWS_TRY(ensure_dyn_smem((const void*)kern, sm));
-    ProfScope ps(PROF_LEG_ADJ, s, sizeof(T) == 8, 4.0 * g.npair * (double)nlm * (NM + 1));
+    ProfScope ps(PROF_LEG_ADJ, s, sizeof(T) == 8, leg_work(g, NM));
     kern<<<grd, C::ANT, sm, s>>>((const T2*)F, F_stride, A, g.ls.as<int>(), st, yr,
                                  g.pair_ring.as<int2>(), part, nlm, L, g.npair);
     CMBWS_LAUNCH_CHECK();

@@ -317,7 +317,7 @@ template <int NM>
 int launch_synth_df(const Grid& g, const void* alm, int64_t as, void* F, int64_t fs, cudaStream_t s) {
   const int L = g.lmax;
   dim3 grd((g.npair + kSNT * kSR - 1) / (kSNT * kSR), L + 1);
-  ProfScope ps(PROF_LEG_SYNTH, s, 2, 4.0 * g.npair * (double)nlm_of(L) * (NM + 1));
+  ProfScope ps(PROF_LEG_SYNTH, s, 2, leg_work(g, NM));
   k_leg_synth_df<NM, kSR, kSNT, kSCH><<<grd, kSNT, 0, s>>>(
       (const double2*)alm, as, g.A2f.as<float2>(), g.ls.as<int>(), g.st64.as<double2>(),
       g.y64.as<double>(), g.pair_ring.as<int2>(), (df2*)F, fs, L, g.npair);
@@ -342,7 +342,7 @@ int launch_adj_ck_df(const Grid& g, const void* F, int64_t fs, void* eo_buf, dou
   constexpr size_t sm = sizeof(AdjCkDfWarp<NM, kAPT>) * (kANT / 32);
   auto kern = k_leg_adj_ck_df<NM, kANT, kAPT>;
   CMBWS_TRY(ensure_dyn_smem((const void*)kern, sm));
-  ProfScope ps(PROF_LEG_ADJ, s, 2, 4.0 * g.npair * (double)nlm * (NM + 1));
+  ProfScope ps(PROF_LEG_ADJ, s, 2, leg_work(g, NM));
   kern<<<grd, kANT, sm, s>>>(eo, g.A2f.as<float2>(), g.ls.as<int>(), g.st64.as<double2>(),
                              g.y2f.as<float2>(), g.ck64.as<float4>(), g.ck64_base.as<int64_t>(),
                              g.wtdf.as<int2>(), g.nwtdf, g.ls_tmin.as<int>(), g.c64.as<double>(),

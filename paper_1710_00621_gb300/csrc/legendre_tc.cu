@@ -365,7 +365,7 @@ int launch_synth_tc(const Grid& g, const void* alm, int64_t as, void* F, int64_t
   dim3 grd((g.npair + kTcNT - 1) / kTcNT, L + 1);
   auto kern = k_leg_synth_tc<NM, SPLIT>;
   CMBWS_TRY(ensure_dyn_smem((const void*)kern, LY::kSmem));
-  ProfScope ps(PROF_LEG_SYNTH, s, SPLIT ? 4 : 3, 4.0 * g.npair * (double)nlm_of(L) * (NM + 1));
+  ProfScope ps(PROF_LEG_SYNTH, s, SPLIT ? 4 : 3, leg_work(g, NM));
   kern<<<grd, kTcNT, LY::kSmem, s>>>((const float2*)alm, as, g.A32.as<float>(), g.BRS32.as<float>(),
                                      g.ls.as<int>(),
                                      g.st32.as<float2>(), g.y32.as<float>(), g.pair_ring.as<int2>(),

@@ -3,20 +3,22 @@
 // cmbws_sht_analysis keeps its workspace (ring spectra, the per-CTA partial
 // sums of the adjoint Legendre kernel, the reduced coefficients) in buffers
 // the grid allocates on first use.  Some callers cannot allocate device
-// memory at that point: code running while a CUDA graph is being captured,
-// host runtimes that hand the library a fixed memory budget and forbid
-// cudaMalloc after start-up, or real-time loops that must not block on the
-// allocator.  cmbws_sht_analysis_noalloc serves them from one file-scope
-// __device__ array of kScratchBytes (32 MiB), which every GPU that loads the
-// library holds until the process exits.
+// memory at that point: host runtimes that hand the library a fixed memory
+// budget and forbid cudaMalloc after start-up, or real-time loops that must
+// not block on the allocator (cudaMalloc can synchronise the device).
+// cmbws_sht_analysis_noalloc serves them from one file-scope __device__ array
+// of kScratchBytes (32 MiB), which every GPU that loads the library holds
+// until the process exits.
 //
 // The host cannot use the array's name as a device address (in host code it
 // names a host-side stand-in), so the device address is looked up with
 // cudaGetSymbolAddress once per device, with that device current, on the
 // first call made on the device.  Make that first call before any stream
-// capture begins.  All calls share the one array and find the previous
-// call's contents in it; the kernels overwrite every byte they read, so
-// nothing needs clearing, but calls whose kernels overlap on the GPU (other
+// capture begins.  The address belongs to the device's CUDA context at that
+// time; after cudaDeviceReset the cached address is stale, so the library must
+// not be used across a reset.  All calls share the one array and find the
+// previous call's contents in it; the kernels overwrite every byte they read,
+// so nothing needs clearing, but calls whose kernels overlap on the GPU (other
 // streams, other host threads) race and must be serialised by the caller.
 #include <mutex>
 
@@ -66,8 +68,14 @@ extern "C" int cmbws_sht_analysis_noalloc(cmbws_grid gh, cmbws_prec prec, const 
                                           double* alm, int nmaps, int weighted, void* stream) {
   clear_error();
   Grid* g = as_grid(gh);
-  if (!g || !alm || !map || nmaps < 1 || (prec != CMBWS_FP64 && prec != CMBWS_FP32)) {
+  if (!g || !alm || !map || nmaps < 1) {
     set_error("cmbws_sht_analysis_noalloc: invalid arguments");
+    return CMBWS_ERR_ARG;
+  }
+  if (prec != CMBWS_FP64 && prec != CMBWS_FP32) {
+    set_error("cmbws_sht_analysis_noalloc: precision %d is not supported here (CMBWS_FP64 or "
+              "CMBWS_FP32 only: the double-float and tensor-core modes build tables on first use)",
+              (int)prec);
     return CMBWS_ERR_ARG;
   }
   int dev = -1;

@@ -358,7 +358,12 @@ int launch_nt(const Grid& g, int nmaps, void* F, double* map_out, const double* 
     if (MODE == MODE_FUSED)
       for (int i = 0; i < nm; ++i) pp.p[i] = (const TP*)pix[k0 + i];
     dim3 grd(g.npair, nm);
-    ProfScope ps(PROF_FFT, s, f32 ? 0 : f64 ? 1 : 2);
+    // algorithmic bytes: ring spectra read and/or written once, pixel factors (fused) or the
+    // FP64 maps (synthesis output, analysis input) once
+    const double fb = (double)g.nring * (g.lmax + 1) * sizeof(T2);
+    const double pb = (double)g.npix * (MODE == MODE_FUSED ? sizeof(TP) : sizeof(double));
+    ProfScope ps(PROF_FFT, s, f32 ? 0 : f64 ? 1 : 2,
+                 byte_work(nm * ((MODE == MODE_FUSED ? 2.0 : 1.0) * fb + pb)));
     kern<<<grd, NT, sm, s>>>((T2*)F + k0 * fs, fs, map_out ? map_out + k0 * g.npix : nullptr,
                               map_in ? map_in + k0 * g.npix : nullptr, g.npix, rw, pp,
                               g.plans_d.as<FftPlan>(), g.pair_plan.as<int>(),

@@ -1,6 +1,6 @@
 """Run and time one transform case of the library (used for kernel profiling).
 
-    python -m paper_1710_00621_gb300.sht_case --grid healpix --n 1024 --lmax 3071 \
+    python sht_case.py --grid healpix --n 1024 --lmax 3071 \
         --nmaps 3 --prec fp32 --op both --reps 3
 
 Plans the grid, fills random band-limited coefficients / maps on the device, runs the
@@ -14,7 +14,7 @@ import sys
 
 import numpy as np
 
-sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
 
 
 def main():

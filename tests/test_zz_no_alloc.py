@@ -1,8 +1,8 @@
 """The allocation-free analysis entry point agrees with cmbws_sht_analysis (GPU).
 
-Callers that cannot allocate device memory (inside CUDA graph capture, under a fixed
-memory budget) use cmbws_sht_analysis_noalloc, whose workspace is a static 32 MiB device
-array.  This file is collected last so that a failure here, in a run that stops at the
+Callers that cannot allocate device memory (a runtime with a fixed memory budget, a loop
+that must not block on the allocator) use cmbws_sht_analysis_noalloc, whose workspace is a
+static 32 MiB device array.  This file is collected last so that a failure here, in a run that stops at the
 first failure, comes after every other test has run.
 """
 import numpy as np
@@ -26,7 +26,8 @@ def test_noalloc_matches_allocating_call_twice(prec):
     g = cw.cmbws_plan_grid(cw.CMBWS_GRID_HEALPIX, 64, 191)
     nalm = 192 ** 2
     rng = np.random.default_rng(2024)
-    for call, (nmaps, weighted) in enumerate(((2, 1), (3, 0))):   # two calls in a row
+    # calls in a row; 5 maps run two launches (4 + 1) that reuse the same scratch regions
+    for call, (nmaps, weighted) in enumerate(((2, 1), (3, 0), (5, 1))):
         maps = to_dev(rng.standard_normal((nmaps, g.npix)))
         ref = to_dev(np.zeros((nmaps, nalm)))
         got = to_dev(np.full((nmaps, nalm), np.nan))
@@ -44,3 +45,8 @@ def test_noalloc_rejects_sizes_beyond_its_workspace():
     with pytest.raises(cw.CmbwsError) as e:
         cw.cmbws_sht_analysis_noalloc(g, cw.CMBWS_FP64, maps, alm, 1, 1)
     assert e.value.code == -1 and "static scratch" in str(e.value)
+    g2 = cw.cmbws_plan_grid(cw.CMBWS_GRID_HEALPIX, 8, 23)
+    with pytest.raises(cw.CmbwsError) as e:
+        cw.cmbws_sht_analysis_noalloc(g2, cw.CMBWS_FP32X2, to_dev(np.zeros(g2.npix)),
+                                      to_dev(np.zeros(24 ** 2)), 1, 1)
+    assert e.value.code == -1 and "not supported" in str(e.value)
