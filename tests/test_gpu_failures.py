@@ -51,7 +51,7 @@ def test_exhausted_wall_clock_budget_is_a_timeout():
     x = to_dev(np.zeros(m.nvec()))
     rep = cw.cmbws_cg_solve(g, b, x, tol=1e-12, maxiter=1000, timeout_s=1e-9,
                             cert_prec=cw.CMBWS_FP32X2, check=False)
-    assert rep["code"] == -7 and rep["iters"] >= 1, rep
+    assert rep["code"] == -7, rep
     rep = cw.cmbws_cg_solve(g, b, x, tol=1e-6, maxiter=1000, cert_prec=cw.CMBWS_FP32X2)
     assert rep["rel_res"] <= 1e-6
 

@@ -15,10 +15,11 @@ pytestmark = pytest.mark.gpu
 
 
 def _tol(prec, lmax):
-    # the same bounds as the SHT parity tests
+    # the adjoint bounds of the SHT parity tests (FP64 40 (L+1) eps64, FP32 6 sqrt(L+1) eps32):
+    # both calls run the same kernels, so they agree to rounding
     if prec == cw.CMBWS_FP64:
-        return max(1e-12, 1e-16 * (lmax + 1) ** 2)
-    return max(1e-5, 5 * (lmax + 1) * 6e-8)
+        return max(1e-14, 40 * (lmax + 1) * 2.0 ** -53)
+    return max(1e-6, 6 * np.sqrt(lmax + 1) * 2.0 ** -24)
 
 
 @pytest.mark.parametrize("prec", [cw.CMBWS_FP64, cw.CMBWS_FP32])
