@@ -124,7 +124,8 @@ struct FftPlan {
   int bluestein;  // 1 if n is not a power of two
   int pad;
   int64_t chirp;  // offset (complex entries) of b_t = exp(i pi t^2 / n), t < n
-  int64_t filt;   // offset of the Bluestein filter spectrum (n2 entries, includes 1/n2)
+  int64_t filt;   // offset of the Bluestein filter spectrum (n2 entries, includes 1/n2,
+                  // bit-reversed order)
   int64_t phase;  // offset of exp(i pi k / n), k < n (ring offset phi0 = pi / n)
 };
 

@@ -409,8 +409,16 @@ int grid_build_tables(Grid& g) {
           if (t > 0) v[P.n2 - t] = tab[P.chirp + t];
         }
         host_fft(v, -1);
+        // stored in bit-reversed order: the ring FFT multiplies it into a spectrum that its
+        // decimation-in-frequency transform leaves bit-reversed
         P.filt = (int64_t)tab.size();
-        for (int j = 0; j < P.n2; ++j) tab.push_back(v[j] / (double)P.n2);
+        int lg2 = 0;
+        while ((1 << lg2) < P.n2) ++lg2;
+        for (int q = 0; q < P.n2; ++q) {
+          int j = 0;
+          for (int b = 0; b < lg2; ++b) j |= ((q >> b) & 1) << (lg2 - 1 - b);
+          tab.push_back(v[j] / (double)P.n2);
+        }
       } else {
         P.filt = 0;
       }

@@ -27,7 +27,9 @@ def main():
     ap.add_argument("--lmax", type=int, default=3071)
     ap.add_argument("--nmaps", type=int, default=3)
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "fp32x2", "tf32", "3xtf32"])
-    ap.add_argument("--op", default="both", choices=["synth", "analysis", "both"])
+    ap.add_argument("--op", default="both", choices=["synth", "analysis", "both", "apply"],
+                    help="apply: y = A x of a one-component model with nmaps bands on the grid "
+                         "(synthesis, fused ring FFT with the N^-1 multiply, adjoint)")
     ap.add_argument("--reps", type=int, default=3)
     a = ap.parse_args()
     kind = cw.CMBWS_GRID_HEALPIX if a.grid == "healpix" else cw.CMBWS_GRID_GL
@@ -41,12 +43,24 @@ def main():
     maps = torch.empty(a.nmaps * g.npix, dtype=torch.float64, device=dev)
     back = torch.empty_like(alm)
     cw.cmbws_sht_synth(g, prec, alm, maps, a.nmaps)
+    model = None
+    if a.op == "apply":
+        ninv = [1.0 + torch.rand(g.npix, dtype=torch.float64, device=dev, generator=gen)
+                for _ in range(a.nmaps)]
+        beams = [np.ones(a.lmax + 1)] * a.nmaps
+        model = cw.cmbws_model_create([a.lmax], [g] * a.nmaps, beams, [np.ones(a.lmax + 1)], ninv,
+                                      np.ones((a.nmaps, 1)), prec)
+        x = torch.randn(nalm, dtype=torch.float64, device=dev, generator=gen)
+        y = torch.empty_like(x)
+        cw.cmbws_apply_A(model, x, y)
     torch.cuda.synchronize()
     cw.cmbws_profile_read(reset=True)
     cw.cmbws_profile_enable(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(a.reps):
+        if a.op == "apply":
+            cw.cmbws_apply_A(model, x, y)
         if a.op in ("synth", "both"):
             cw.cmbws_sht_synth(g, prec, alm, maps, a.nmaps)
         if a.op in ("analysis", "both"):
@@ -57,7 +71,8 @@ def main():
     prof = cw.cmbws_profile_read(reset=True)
     out = {"case": vars(a), "ms_per_rep": e0.elapsed_time(e1) / a.reps,
            "stages": {f"{k[0]}_{k[1]}": {"ms": round(v[0], 3), "launches": v[1],
-                                          "tflops": round(v[2] / (v[0] * 1e-3) / 1e12, 3) if v[0] else 0}
+                                          "tflops": round(v[2] / (v[0] * 1e-3) / 1e12, 3) if v[0] else 0,
+                                          "gbs": round(v[5] / (v[0] * 1e-3) / 1e9, 1) if v[0] else 0}
                       for k, v in prof.items() if v[1]}}
     print(json.dumps(out))
 
