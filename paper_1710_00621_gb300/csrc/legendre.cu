@@ -495,14 +495,11 @@ k_leg_adj_ck(const float* __restrict__ eo, const float* __restrict__ Acoef,
       const int bf = k & 1;
       const int np = min(PT, npair - t * PT);
       for (int i = 0; i < np; ++i) {
-        const int lsp = S.ls[bf][i];
-        if (lsp > l0 + K - 1) continue;  // the pair starts after this chunk
+        const int jinj = S.ls[bf][i] - l0;  // where the pair starts, relative to the chunk
+        if (jinj > K - 1) continue;         // the pair starts after this chunk
         const float2 cv = S.ck[bf][i][lane];
-        float ma = cv.x, mb = cv.y;
-        if (lsp == l0) {
-          ma = S.st[bf][i].x;
-          mb = S.st[bf][i].y;
-        }
+        const float2 sv = S.st[bf][i];
+        float ma = jinj == 0 ? sv.x : cv.x, mb = jinj == 0 ? sv.y : cv.y;
         const float yv = S.y[bf][i];
         const float* e = S.eo[bf][i];
 #pragma unroll
@@ -514,9 +511,9 @@ k_leg_adj_ck(const float* __restrict__ eo, const float* __restrict__ Acoef,
         for (int j = 2; j < K; j += 2) {
           float na = fmaf(-Al[j], yv, Al[j]) * mb - ma;
           float nb = fmaf(-Al[j + 1], yv, Al[j + 1]) * na - mb;
-          if (l0 + j == lsp) {
-            na = S.st[bf][i].x;
-            nb = S.st[bf][i].y;
+          if (j == jinj) {
+            na = sv.x;
+            nb = sv.y;
           }
           ma = na;
           mb = nb;

@@ -183,8 +183,9 @@ struct AdjCkDfWarp {  // one warp's double-buffered tile
 // double-float checkpoints, and accumulates each output (l, m, part) with the
 // compensated dot product.  Each output has one owner and a fixed summation order, so
 // no cross-thread reduction or partial-sum buffer is needed.
+// four CTAs (16 warps) per SM: 128 registers per thread, measured 2.5 % faster than three
 template <int NM, int NT, int PT>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, 4)
 k_leg_adj_ck_df(const float2* __restrict__ eo, const float2* __restrict__ Acoef,
                 const int* __restrict__ ls_tab, const double2* __restrict__ st,
                 const float2* __restrict__ yr, const float4* __restrict__ ck,
@@ -261,8 +262,8 @@ k_leg_adj_ck_df(const float2* __restrict__ eo, const float2* __restrict__ Acoef,
       const int bf = k & 1;
       const int np = min(PT, npair - t * PT);
       for (int i = 0; i < np; ++i) {
-        const int lsp = S.ls[bf][i];
-        if (lsp > l0 + K - 1) continue;  // the pair starts after this chunk
+        const int jinj = S.ls[bf][i] - l0;  // where the pair starts, relative to the chunk
+        if (jinj > K - 1) continue;         // the pair starts after this chunk
         const float4 cv = S.ck[bf][i][lane];
         df ma = {cv.x, cv.y}, mb = {cv.z, cv.w};
         const float2 yy = S.y[bf][i];
@@ -278,7 +279,7 @@ k_leg_adj_ck_df(const float2* __restrict__ eo, const float2* __restrict__ Acoef,
         for (int j = 2; j < K; j += 2) {
           df na = df_recur(Al[j], yv, mb, ma);
           df nb = df_recur(Al[j + 1], yv, na, mb);
-          if (l0 + j == lsp) {
+          if (j == jinj) {
             const double2 sv = S.st[bf][i];
             na = df_from(sv.x);
             nb = df_from(sv.y);
