@@ -630,11 +630,11 @@ IMPL_FLOPS = {("legendre_synth", "fp32"): (4.0, 4.0), ("legendre_adjoint", "fp32
               ("legendre_adjoint", "fp32x2"): (19.5, 30.0)}
 
 
-# DRAM bytes (read + write) per element from one ncu capture of the kernel as it stands
-# (the Nside 512, L = 1535, 3-map case): 4.083 GB / 1.209e9 elements; the checkpoint table
-# dominates, so it scales with the elements.  Emptied whenever the kernel changes until it
-# is captured again.
-DRAM_BYTES_PER_ELEM = {("legendre_adjoint", "fp32x2"): 3.38}
+# DRAM bytes (read + write) per element from one ncu capture of the kernel as it stands (a
+# smaller case of the same kernel, scaled by the elements of a full-size launch: the
+# checkpoint table dominates, so the traffic grows with the elements).  Emptied whenever the
+# kernel changes until it is captured again.
+DRAM_BYTES_PER_ELEM = {}
 
 
 def measured_peaks():

@@ -392,6 +392,46 @@ int cmbws_cg_solve(cmbws_model m, const double* b, double* x, const cmbws_cg_opt
                    cmbws_cg_report* report, void* stream);
 
 /*
+ * Per-iteration record of the model's last solve (cmbws_cg_solve, cmbws_cg_resume, or one
+ * problem of cmbws_cg_solve_batched), the error-tracking method of Sec. 2.3 and Sec. 5:
+ *   rel_res[i] = ||r_i|| / ||b||, r_i the recursive residual after CG iteration i (over all
+ *     refinement passes; for FP32 models the residual of the correction equation, which
+ *     equals b - A x_i up to the FP32 operator's error);
+ *   rel_err[i] = ||x_i - x_true|| / ||x_true|| while a reference solution is set with
+ *     cmbws_cg_track_error (one extra dot product per iteration), else -1.
+ * Host arrays of at least cap entries (either may be NULL); *n receives the number of
+ * iterations recorded (entries beyond cap are not written).  Errors: CMBWS_ERR_ARG.
+ */
+int cmbws_cg_history(cmbws_model m, double* rel_res, double* rel_err, int cap, int* n);
+
+/* Reference solution for the error record of cmbws_cg_history (e.g. x_true with
+ * b = A x_true, Sec. 2.3): a device stacked vector, copied (synchronises `stream`); NULL
+ * stops the tracking. */
+int cmbws_cg_track_error(cmbws_model m, const double* x_true, void* stream);
+
+/*
+ * Checkpoint / resume of a PCG solve (models without FP32 transforms: CMBWS_FP64,
+ * CMBWS_FP32X2).  With checkpointing on, a solve that stops at its iteration cap
+ * (CMBWS_ERR_NOT_CONVERGED) keeps the state of its next iteration: the correction d
+ * (the solution is x0 + d), the residual r, the search direction p, and the scalars
+ * {iterations done, r.z, r.r}.  cmbws_cg_state_export copies it out (d, r, p: device stacked
+ * vectors; scalars: host array of 3), e.g. to storage; cmbws_cg_resume continues from such a
+ * state on a model built from the same description, with b and x holding the right-hand
+ * side and the initial guess x0 of the interrupted solve (x is overwritten with the
+ * solution).  opts.maxiter caps the iterations of both runs together, so an interrupted and
+ * resumed solve performs exactly the operations of an uninterrupted one and returns the
+ * bitwise same x.  Models with FP32 transforms (iterative refinement) resume by passing the
+ * returned x as the initial guess of a new solve instead: CMBWS_ERR_ARG here.
+ * Errors: CMBWS_ERR_ARG (no checkpoint, invalid scalars, FP32 models).
+ */
+int cmbws_cg_checkpointing(cmbws_model m, int on);
+int cmbws_cg_state_export(cmbws_model m, double* d, double* r, double* p, double* scalars,
+                          void* stream);
+int cmbws_cg_resume(cmbws_model m, const double* b, double* x, const double* d, const double* r,
+                    const double* p, const double* scalars, const cmbws_cg_opts* opts,
+                    cmbws_cg_report* report, void* stream);
+
+/*
  * CUDA graphs for the operator applies inside the solvers (on = 1; default 0).  Each apply of
  * A and of the preconditioner in PCG is tens to hundreds of kernel launches (per grid group:
  * Legendre synthesis, ring FFT, Legendre adjoint; harmonic-space kernels; the multigrid

@@ -112,3 +112,60 @@ def power_law_q(freqs, nu0, beta, fixed: List[bool]):
     q = (f / n0) ** beta[None, :]
     mask = torch.as_tensor(np.asarray(fixed, dtype=bool))[None, :]
     return torch.where(mask, torch.ones_like(q), q)
+
+
+class SHTSynthesis(torch.autograd.Function):
+    """map = Y alm (cmbws_sht_synth, Sec. 2.1) with its hand-written adjoint: the gradient of a
+    loss with respect to alm is Y^T (dL/dmap), the adjoint synthesis of the library
+    (cmbws_sht_analysis with weighted = 0, Sec. 3.2), the exact transpose of the synthesis.
+
+    alm: CUDA float64 [nmaps, (L+1)^2] (CMBWS_ALM order) or [(L+1)^2]; returns [nmaps, npix]
+    (or [npix])."""
+
+    @staticmethod
+    def forward(ctx, alm, grid, prec):
+        a = alm.detach().contiguous()
+        nmaps = 1 if a.dim() == 1 else a.shape[0]
+        out = torch.empty((nmaps, grid.npix) if a.dim() > 1 else (grid.npix,), dtype=torch.float64,
+                          device=a.device)
+        B.cmbws_sht_synth(grid, prec, a, out, nmaps)
+        ctx.grid, ctx.prec, ctx.nmaps, ctx.shape = grid, prec, nmaps, a.shape
+        return out
+
+    @staticmethod
+    def backward(ctx, g):
+        ga = torch.empty(ctx.shape, dtype=torch.float64, device=g.device)
+        B.cmbws_sht_analysis(ctx.grid, ctx.prec, g.contiguous(), ga, ctx.nmaps, 0)
+        return ga, None, None
+
+
+class SHTAdjoint(torch.autograd.Function):
+    """alm = Y^T map (adjoint synthesis, cmbws_sht_analysis with weighted = 0), whose own
+    adjoint is the synthesis Y: the gradient with respect to the map is Y (dL/dalm)."""
+
+    @staticmethod
+    def forward(ctx, m, grid, prec):
+        f = m.detach().contiguous()
+        nmaps = 1 if f.dim() == 1 else f.shape[0]
+        nalm = (grid.lmax + 1) ** 2
+        out = torch.empty((nmaps, nalm) if f.dim() > 1 else (nalm,), dtype=torch.float64,
+                          device=f.device)
+        B.cmbws_sht_analysis(grid, prec, f, out, nmaps, 0)
+        ctx.grid, ctx.prec, ctx.nmaps, ctx.shape = grid, prec, nmaps, f.shape
+        return out
+
+    @staticmethod
+    def backward(ctx, g):
+        gm = torch.empty(ctx.shape, dtype=torch.float64, device=g.device)
+        B.cmbws_sht_synth(ctx.grid, ctx.prec, g.contiguous(), gm, ctx.nmaps)
+        return gm, None, None
+
+
+def sht_synth(alm, grid, prec=B.CMBWS_FP64):
+    """Differentiable Y alm."""
+    return SHTSynthesis.apply(alm, grid, prec)
+
+
+def sht_adjoint(m, grid, prec=B.CMBWS_FP64):
+    """Differentiable Y^T map."""
+    return SHTAdjoint.apply(m, grid, prec)

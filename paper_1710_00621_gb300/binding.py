@@ -113,6 +113,13 @@ def load_library(path=None):
     lib.cmbws_powerlaw_mixing.argtypes = [d, vp, vp, ctypes.c_int64, vp, vp]
     lib.cmbws_profile_enable.argtypes = [i]
     lib.cmbws_device_status.argtypes = [vp]
+    lib.cmbws_cg_history.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(d), i,
+                                     ctypes.POINTER(i)]
+    lib.cmbws_cg_track_error.argtypes = [vp, vp, vp]
+    lib.cmbws_cg_checkpointing.argtypes = [vp, i]
+    lib.cmbws_cg_state_export.argtypes = [vp, vp, vp, vp, ctypes.POINTER(d), vp]
+    lib.cmbws_cg_resume.argtypes = [vp, vp, vp, vp, vp, vp, ctypes.POINTER(d),
+                                    ctypes.POINTER(CgOpts), ctypes.POINTER(CgReport), vp]
     lib.cmbws_testing_stall_waits.argtypes = [ctypes.c_longlong]
     lib.cmbws_profile_read.argtypes = [ctypes.POINTER(d), ctypes.POINTER(ctypes.c_int64),
                                        ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d),
@@ -552,6 +559,56 @@ def cmbws_cg_solve(model, b, x, tol=1e-6, maxiter=1000, precond=1, inner_tol=1e-
     code = load_library().cmbws_cg_solve(model.handle, _dptr(b, model.nvec, "b"),
                                          _dptr(x, model.nvec, "x"), ctypes.byref(opts),
                                          ctypes.byref(rep), _stream(stream))
+    if check:
+        _check(code)
+    out = rep.as_dict()
+    out["code"] = code
+    return out
+
+
+def cmbws_cg_history(model):
+    """(rel_res, rel_err) per CG iteration of the model's last solve (rel_err -1 when no
+    reference solution is tracked)."""
+    n = ctypes.c_int()
+    _check(load_library().cmbws_cg_history(model.handle, None, None, 0, ctypes.byref(n)))
+    res = (ctypes.c_double * max(n.value, 1))()
+    err = (ctypes.c_double * max(n.value, 1))()
+    _check(load_library().cmbws_cg_history(model.handle, res, err, n.value, ctypes.byref(n)))
+    return np.array(res[:n.value]), np.array(err[:n.value])
+
+
+def cmbws_cg_track_error(model, x_true=None, stream=None):
+    ptr = None if x_true is None else _dptr(x_true, model.nvec, "x_true")
+    _check(load_library().cmbws_cg_track_error(model.handle, ptr, _stream(stream)))
+
+
+def cmbws_cg_checkpointing(model, on=True):
+    _check(load_library().cmbws_cg_checkpointing(model.handle, 1 if on else 0))
+
+
+def cmbws_cg_state_export(model, d, r, p, stream=None):
+    """Copy the checkpointed PCG state into d, r, p (device vectors); returns the scalars
+    [iterations, r.z, r.r]."""
+    sc = (ctypes.c_double * 3)()
+    _check(load_library().cmbws_cg_state_export(model.handle, _dptr(d, model.nvec, "d"),
+                                                _dptr(r, model.nvec, "r"),
+                                                _dptr(p, model.nvec, "p"), sc, _stream(stream)))
+    return [sc[0], sc[1], sc[2]]
+
+
+def cmbws_cg_resume(model, b, x, d, r, p, scalars, tol=1e-6, maxiter=1000, precond=1,
+                    inner_tol=1e-3, max_outer=20, timeout_s=0.0, cert_prec=CMBWS_FP64, stream=None,
+                    check=True):
+    """Continue an exported PCG state (x: the interrupted solve's initial guess; overwritten with
+    the solution).  Returns the report as a dict."""
+    opts = CgOpts(float(tol), int(maxiter), int(precond), float(inner_tol), int(max_outer),
+                  float(timeout_s), int(cert_prec))
+    rep = CgReport()
+    sc = (ctypes.c_double * 3)(*[float(v) for v in scalars])
+    code = load_library().cmbws_cg_resume(model.handle, _dptr(b, model.nvec, "b"),
+                                          _dptr(x, model.nvec, "x"), _dptr(d, model.nvec, "d"),
+                                          _dptr(r, model.nvec, "r"), _dptr(p, model.nvec, "p"), sc,
+                                          ctypes.byref(opts), ctypes.byref(rep), _stream(stream))
     if check:
         _check(code)
     out = rep.as_dict()

@@ -96,6 +96,20 @@ __global__ void k_axpy1(const double* __restrict__ x, double* __restrict__ y, in
     y[i] += x[i];
 }
 
+// partial sums of |x + d - t|^2 (distance of the current iterate to a reference solution)
+__global__ void k_err_partial(const double* __restrict__ x, const double* __restrict__ d,
+                              const double* __restrict__ t, int64_t n, double* __restrict__ partial) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double e = x[i] + d[i] - t[i];
+    s += e * e;
+  }
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
 __global__ void k_finish(const double* __restrict__ partial, int nb, double* __restrict__ out) {
   __shared__ double sh[32];
   double s = 0.0;
@@ -235,31 +249,73 @@ static int run_op(Model& M, int op, int prec, const double* in, double* out, cud
 
 enum { OP_APPLY_A = 0, OP_PRECOND = 1 };
 
-// PCG on A d = r0 (d starts at zero), operator precision `prec`; stops when
-// ||r|| <= stop_abs or after maxit iterations.  r0 is overwritten with the final residual.
+// Where a PCG run starts: from d = 0 (a fresh pass), or from an exported state (the correction
+// d, residual r and direction p already in the model's workspaces, with the iteration count
+// and the scalars r.z and r.r of the next iteration).
+struct PcgStart {
+  bool resume = false;
+  int it0 = 0;
+  double rz = 0.0, rr = 0.0;
+};
+
+// Record of one iteration: ||r|| / ||b|| and, when tracked, ||x + d - x_true|| / ||x_true||.
+struct PcgRecord {
+  const double* x = nullptr;  // outer iterate (the current solution is x + d)
+  double bnorm = 1.0, tnorm = 1.0;
+};
+
+static int record_iteration(Solver& S, const PcgRecord& rec, const double* d, double rr) {
+  Model& M = S.M;
+  M.hist_res.push_back(std::sqrt(rr) / rec.bnorm);
+  if (!M.track_err) return CMBWS_OK;
+  {
+    ProfScope ps_(PROF_CG, S.s);
+    k_err_partial<<<kRedBlocks, kRedThreads, 0, S.s>>>(rec.x, d, M.cg_xtrue.as<double>(), S.n, S.red);
+    CMBWS_LAUNCH_CHECK();
+  }
+  double ee;
+  CMBWS_TRY(S.finish(&ee));
+  M.hist_err.push_back(std::sqrt(ee) / rec.tnorm);
+  return CMBWS_OK;
+}
+
+// PCG on A d = r0 (d starts at zero unless resuming), operator precision `prec`; stops when
+// ||r|| <= stop_abs or after maxit iterations in all (counting a resumed run's earlier ones).
+// r0 is overwritten with the final residual; *rz_out is r.z of the next iteration.
 static int pcg_core(Solver& S, int prec, int use_M, double* d, double* r, double stop_abs, int maxit,
-                    int* iters, double* rr_out, const Clock& clk, double timeout) {
+                    int* iters, double* rr_out, const Clock& clk, double timeout,
+                    const PcgStart& start, const PcgRecord& rec, double* rz_out) {
   Model& M = S.M;
   double* z = M.cg_z.as<double>();
   double* p = M.cg_p.as<double>();
   double* q = M.cg_q.as<double>();
   const int64_t n = S.n;
-  CMBWS_CUDA(cudaMemsetAsync(d, 0, n * 8, S.s));
-  double rr;
-  CMBWS_TRY(S.dot(r, r, &rr));
-  *rr_out = rr;
-  *iters = 0;
-  if (std::sqrt(rr) <= stop_abs) return CMBWS_OK;
   auto precond = [&]() {
     if (!use_M) return precondition(M, use_M, prec, r, z, n, S.s);
     return run_op(M, OP_PRECOND + 16 * use_M, prec, r, z, S.s,
                   [&]() { return precondition(M, use_M, prec, r, z, n, S.s); });
   };
-  CMBWS_TRY(precond());
-  CMBWS_CUDA(cudaMemcpyAsync(p, z, n * 8, cudaMemcpyDeviceToDevice, S.s));
-  double rz;
-  CMBWS_TRY(S.dot(r, z, &rz));
-  for (int it = 0; it < maxit; ++it) {
+  double rr, rz;
+  if (start.resume) {
+    rr = start.rr;
+    rz = start.rz;
+    *rr_out = rr;
+    *rz_out = rz;
+    *iters = start.it0;
+    if (std::sqrt(rr) <= stop_abs) return CMBWS_OK;
+  } else {
+    CMBWS_CUDA(cudaMemsetAsync(d, 0, n * 8, S.s));
+    CMBWS_TRY(S.dot(r, r, &rr));
+    *rr_out = rr;
+    *iters = 0;
+    *rz_out = 0.0;
+    if (std::sqrt(rr) <= stop_abs) return CMBWS_OK;
+    CMBWS_TRY(precond());
+    CMBWS_CUDA(cudaMemcpyAsync(p, z, n * 8, cudaMemcpyDeviceToDevice, S.s));
+    CMBWS_TRY(S.dot(r, z, &rz));
+    *rz_out = rz;
+  }
+  for (int it = start.resume ? start.it0 : 0; it < maxit; ++it) {
     CMBWS_TRY(run_op(M, OP_APPLY_A, prec, p, q, S.s, [&]() { return M.apply_A(p, q, prec, S.s); }));
     double pq;
     CMBWS_TRY(S.dot(p, q, &pq));
@@ -286,6 +342,7 @@ static int pcg_core(Solver& S, int prec, int use_M, double* d, double* r, double
       set_error("CG breakdown: non-finite residual at iteration %d", it);
       return CMBWS_ERR_BREAKDOWN;
     }
+    CMBWS_TRY(record_iteration(S, rec, d, rr));
     if (std::sqrt(rr) <= stop_abs) return CMBWS_OK;
     if (timeout > 0 && clk.s() > timeout) {
       set_error("CG: wall-clock budget of %g s exhausted", timeout);
@@ -296,6 +353,7 @@ static int pcg_core(Solver& S, int prec, int use_M, double* d, double* r, double
     CMBWS_TRY(S.dot(r, z, &rz_new));
     const double beta = rz_new / rz;
     rz = rz_new;
+    *rz_out = rz;
     {
       ProfScope ps_(PROF_CG, S.s);
       k_xpby<<<kRedBlocks, kRedThreads, 0, S.s>>>(z, p, beta, n);
@@ -305,8 +363,11 @@ static int pcg_core(Solver& S, int prec, int use_M, double* d, double* r, double
   return CMBWS_ERR_NOT_CONVERGED;
 }
 
+// One solve.  resume = nullptr: a fresh solve from the initial guess in x.  Otherwise (models
+// without FP32 transforms) the run continues the exported PCG state that the caller placed in
+// cg_d, cg_r and cg_p, with x holding the same initial guess as the interrupted solve.
 static int cg_solve_impl(Model& M, const double* b, double* x, const cmbws_cg_opts& o,
-                         cmbws_cg_report& rep, cudaStream_t s) {
+                         cmbws_cg_report& rep, cudaStream_t s, const PcgStart* resume = nullptr) {
   const Clock clk;
   const int64_t n = M.nvec;
   CMBWS_TRY(M.cg_r.ensure(n * 8));
@@ -325,6 +386,9 @@ static int cg_solve_impl(Model& M, const double* b, double* x, const cmbws_cg_op
   Solver S{M, s, n, M.cg_red.as<double>(), hscal};
   S.cert = o.cert_prec == CMBWS_FP32X2 ? CMBWS_FP32X2 : CMBWS_FP64;
   const long long sht0 = M.n_sht;
+  M.hist_res.clear();
+  M.hist_err.clear();
+  if (!resume) M.ck_valid = false;
 
   double bb;
   CMBWS_TRY(S.dot(b, b, &bb));
@@ -337,20 +401,35 @@ static int cg_solve_impl(Model& M, const double* b, double* x, const cmbws_cg_op
     rep.rel_res = 0.0;
     return CMBWS_OK;
   }
-  double rr, xx;
-  CMBWS_TRY(S.dot(x, x, &xx));
-  if (xx == 0.0) {
-    // x0 = 0: r = b without an apply of A
-    CMBWS_CUDA(cudaMemcpyAsync(r, b, n * 8, cudaMemcpyDeviceToDevice, s));
-    rr = bb;
+  PcgRecord rec;
+  rec.x = x;
+  rec.bnorm = bnorm;
+  if (M.track_err) {
+    double tt;
+    CMBWS_TRY(S.dot(M.cg_xtrue.as<double>(), M.cg_xtrue.as<double>(), &tt));
+    rec.tnorm = tt > 0.0 ? std::sqrt(tt) : 1.0;
+  }
+  double rr;
+  if (resume) {
+    rr = resume->rr;
   } else {
-    CMBWS_TRY(S.true_residual(b, x, r, tmp, &rr));
+    double xx;
+    CMBWS_TRY(S.dot(x, x, &xx));
+    if (xx == 0.0) {
+      // x0 = 0: r = b without an apply of A
+      CMBWS_CUDA(cudaMemcpyAsync(r, b, n * 8, cudaMemcpyDeviceToDevice, s));
+      rr = bb;
+    } else {
+      CMBWS_TRY(S.true_residual(b, x, r, tmp, &rr));
+    }
   }
   int status = CMBWS_ERR_NOT_CONVERGED;
-  int total = 0, outer = 0;
+  int total = resume ? resume->it0 : 0, outer = 0;
   const double target = o.tol * bnorm;
+  PcgStart start;
+  if (resume) start = *resume;
   while (true) {
-    if (std::sqrt(rr) <= target) {
+    if (!start.resume && std::sqrt(rr) <= target) {
       status = CMBWS_OK;
       break;
     }
@@ -375,14 +454,29 @@ static int cg_solve_impl(Model& M, const double* b, double* x, const cmbws_cg_op
     const double stop = !is_f32(M.prec) ? 0.5 * target
                                              : std::max(o.inner_tol * std::sqrt(rr), 0.5 * target);
     int it = 0;
-    double rr_in;
-    const int st = pcg_core(S, M.prec, o.precond, d, r, stop, o.maxiter - total, &it, &rr_in, clk,
-                            o.timeout_s);
-    total += it;
+    double rr_in, rz = 0.0;
+    // a resumed run counts its earlier iterations against the cap
+    const int cap = start.resume ? o.maxiter : o.maxiter - total;
+    const int st = pcg_core(S, M.prec, o.precond, d, r, stop, cap, &it, &rr_in, clk, o.timeout_s,
+                            start, rec, &rz);
+    total = (start.resume ? 0 : total) + it;
+    start = PcgStart();
     ++outer;
     if (st != CMBWS_OK && st != CMBWS_ERR_NOT_CONVERGED) {
       status = st;
       break;
+    }
+    if (st == CMBWS_ERR_NOT_CONVERGED && M.ck_on && !is_f32(M.prec)) {
+      // the state of the next iteration, before the certification overwrites r
+      CMBWS_TRY(M.cg_ck.ensure(3 * n * 8));
+      double* ck = M.cg_ck.as<double>();
+      CMBWS_CUDA(cudaMemcpyAsync(ck, d, n * 8, cudaMemcpyDeviceToDevice, s));
+      CMBWS_CUDA(cudaMemcpyAsync(ck + n, r, n * 8, cudaMemcpyDeviceToDevice, s));
+      CMBWS_CUDA(cudaMemcpyAsync(ck + 2 * n, M.cg_p.p, n * 8, cudaMemcpyDeviceToDevice, s));
+      M.ck_iters = total;
+      M.ck_rz = rz;
+      M.ck_rr = rr_in;
+      M.ck_valid = true;
     }
     {
       ProfScope ps_(PROF_CG, s);
@@ -506,4 +600,124 @@ extern "C" int cmbws_cg_solve_batched(const cmbws_model* models, int nprob, cons
     }
   }
   return status;
+}
+
+extern "C" int cmbws_cg_history(cmbws_model mh, double* rel_res, double* rel_err, int cap, int* n) {
+  clear_error();
+  Model* M = as_model(mh);
+  if (!M || !n || cap < 0) {
+    set_error("cmbws_cg_history: invalid arguments");
+    return CMBWS_ERR_ARG;
+  }
+  const int len = (int)M->hist_res.size();
+  *n = len;
+  for (int i = 0; i < len && i < cap; ++i) {
+    if (rel_res) rel_res[i] = M->hist_res[i];
+    if (rel_err) rel_err[i] = i < (int)M->hist_err.size() ? M->hist_err[i] : -1.0;
+  }
+  return CMBWS_OK;
+}
+
+extern "C" int cmbws_cg_track_error(cmbws_model mh, const double* x_true, void* stream) {
+  clear_error();
+  Model* M = as_model(mh);
+  if (!M) {
+    set_error("cmbws_cg_track_error: invalid model");
+    return CMBWS_ERR_ARG;
+  }
+  if (!x_true) {
+    M->track_err = false;
+    return CMBWS_OK;
+  }
+  CMBWS_TRY(M->cg_xtrue.ensure(M->nvec * 8));
+  CMBWS_CUDA(cudaMemcpyAsync(M->cg_xtrue.p, x_true, M->nvec * 8, cudaMemcpyDeviceToDevice,
+                             (cudaStream_t)stream));
+  CMBWS_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  M->track_err = true;
+  return CMBWS_OK;
+}
+
+extern "C" int cmbws_cg_checkpointing(cmbws_model mh, int on) {
+  clear_error();
+  Model* M = as_model(mh);
+  if (!M) {
+    set_error("cmbws_cg_checkpointing: invalid model");
+    return CMBWS_ERR_ARG;
+  }
+  if (on && is_f32(M->prec)) {
+    set_error("cmbws_cg_checkpointing: models with FP32 transforms restart from x (refinement)");
+    return CMBWS_ERR_ARG;
+  }
+  M->ck_on = on != 0;
+  if (!on) M->ck_valid = false;
+  return CMBWS_OK;
+}
+
+extern "C" int cmbws_cg_state_export(cmbws_model mh, double* d, double* r, double* p,
+                                     double* scalars, void* stream) {
+  clear_error();
+  Model* M = as_model(mh);
+  if (!M || !d || !r || !p || !scalars) {
+    set_error("cmbws_cg_state_export: invalid arguments");
+    return CMBWS_ERR_ARG;
+  }
+  if (!M->ck_valid) {
+    set_error("cmbws_cg_state_export: no checkpoint (checkpointing off, or the last solve did "
+              "not stop at its iteration cap)");
+    return CMBWS_ERR_ARG;
+  }
+  const int64_t n = M->nvec;
+  cudaStream_t s = (cudaStream_t)stream;
+  const double* ck = M->cg_ck.as<double>();
+  CMBWS_CUDA(cudaMemcpyAsync(d, ck, n * 8, cudaMemcpyDeviceToDevice, s));
+  CMBWS_CUDA(cudaMemcpyAsync(r, ck + n, n * 8, cudaMemcpyDeviceToDevice, s));
+  CMBWS_CUDA(cudaMemcpyAsync(p, ck + 2 * n, n * 8, cudaMemcpyDeviceToDevice, s));
+  scalars[0] = M->ck_iters;
+  scalars[1] = M->ck_rz;
+  scalars[2] = M->ck_rr;
+  return CMBWS_OK;
+}
+
+extern "C" int cmbws_cg_resume(cmbws_model mh, const double* b, double* x, const double* d,
+                               const double* r, const double* p, const double* scalars,
+                               const cmbws_cg_opts* opts, cmbws_cg_report* report, void* stream) {
+  clear_error();
+  Model* M = as_model(mh);
+  if (!M || !b || !x || !d || !r || !p || !scalars || !opts || b == x || !(opts->tol > 0.0) ||
+      opts->maxiter < 1 || opts->precond < 0 || opts->precond > 3) {
+    set_error("cmbws_cg_resume: invalid arguments");
+    return CMBWS_ERR_ARG;
+  }
+  if (is_f32(M->prec)) {
+    set_error("cmbws_cg_resume: models with FP32 transforms restart from x (refinement)");
+    return CMBWS_ERR_ARG;
+  }
+  const int it0 = (int)scalars[0];
+  if (it0 < 0 || (double)it0 != scalars[0] || !std::isfinite(scalars[1]) || !std::isfinite(scalars[2])) {
+    set_error("cmbws_cg_resume: invalid state scalars");
+    return CMBWS_ERR_ARG;
+  }
+  cmbws_cg_opts o = *opts;
+  if (!(o.inner_tol > 0.0 && o.inner_tol < 1.0)) o.inner_tol = 1e-3;
+  if (o.max_outer < 1) o.max_outer = 20;
+  const int64_t n = M->nvec;
+  cudaStream_t s = (cudaStream_t)stream;
+  CMBWS_TRY(M->cg_d.ensure(n * 8));
+  CMBWS_TRY(M->cg_r.ensure(n * 8));
+  CMBWS_TRY(M->cg_p.ensure(n * 8));
+  CMBWS_CUDA(cudaMemcpyAsync(M->cg_d.p, d, n * 8, cudaMemcpyDeviceToDevice, s));
+  CMBWS_CUDA(cudaMemcpyAsync(M->cg_r.p, r, n * 8, cudaMemcpyDeviceToDevice, s));
+  CMBWS_CUDA(cudaMemcpyAsync(M->cg_p.p, p, n * 8, cudaMemcpyDeviceToDevice, s));
+  PcgStart st;
+  st.resume = true;
+  st.it0 = it0;
+  st.rz = scalars[1];
+  st.rr = scalars[2];
+  cmbws_cg_report rep{};
+  const auto t0 = std::chrono::steady_clock::now();
+  const int code = cg_solve_impl(*M, b, x, o, rep, s, &st);
+  rep.ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  rep.status = code;
+  if (report) *report = rep;
+  return code;
 }

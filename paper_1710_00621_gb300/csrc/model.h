@@ -105,6 +105,17 @@ struct Model {
 
   // CG workspace (cg.cu)
   DevMem cg_r, cg_z, cg_p, cg_q, cg_d, cg_x, cg_red;
+  // per-iteration record of the last solve (cmbws_cg_history): ||r_i|| / ||b|| and, while a
+  // reference solution is set (cmbws_cg_track_error), ||x_i - x_true|| / ||x_true||
+  std::vector<double> hist_res, hist_err;
+  DevMem cg_xtrue;
+  bool track_err = false;
+  // checkpoint of an FP64 solve stopped by its iteration cap (cmbws_cg_checkpointing):
+  // the correction d, residual r and direction p, and the scalars of the next iteration
+  bool ck_on = false, ck_valid = false;
+  DevMem cg_ck;  // [3][nvec]
+  int ck_iters = 0;
+  double ck_rz = 0.0, ck_rr = 0.0;
 
   // spatially variable mixing (Eq. Q)
   int nmix = 0;

@@ -168,3 +168,48 @@ def test_gradient_full_size_l511_fp64_fd_and_fp32():
         if i < nc and w.comps[i].beta is None:
             continue
         assert abs(g32[i] - g64[i]) <= 1e-7 * abs(g64[i]), (i, g32[i], g64[i])
+
+
+@pytest.mark.parametrize("kind", ["gl", "healpix"])
+def test_sht_autograd_pair_gradients(kind):
+    """The synthesis / adjoint-synthesis autograd pair: gradients of a quadratic loss through
+    Y and through Y^T against the explicit transposes (the oracle's dense Y at L = 15) and
+    against central finite differences of the library's own transforms."""
+    import torch
+    import paper_1710_00621_gb300 as cw
+    from paper_1710_00621_gb300.autodiff import sht_adjoint, sht_synth
+    from oracle import grids as og, sht as osht
+    L = 15
+    if kind == "gl":
+        g = cw.cmbws_plan_grid(cw.CMBWS_GRID_GL, L + 1, L)
+        o = og.gauss_legendre(L)
+    else:
+        g = cw.cmbws_plan_grid(cw.CMBWS_GRID_HEALPIX, 8, L)
+        o = og.healpix(8)
+    Y = osht.dense_Y(o, L)
+    rng = np.random.default_rng(41)
+    a0 = rng.standard_normal((2, (L + 1) ** 2))
+    wm = rng.standard_normal((2, g.npix))
+    # L(a) = sum w * (Y a)^2  ->  dL/da = 2 Y^T (w * Y a)
+    a = torch.tensor(a0, device="cuda", requires_grad=True)
+    loss = (to_dev(wm) * sht_synth(a, g) ** 2).sum()
+    loss.backward()
+    ref = np.stack([2 * Y.T @ (wm[k] * (Y @ a0[k])) for k in range(2)])
+    assert rel_err(a.grad.cpu().numpy(), ref) < 1e-12
+    # L(f) = sum v * (Y^T f)^2  ->  dL/df = 2 Y (v * Y^T f)
+    f0 = rng.standard_normal((2, g.npix))
+    va = rng.standard_normal((2, (L + 1) ** 2))
+    f = torch.tensor(f0, device="cuda", requires_grad=True)
+    loss2 = (to_dev(va) * sht_adjoint(f, g) ** 2).sum()
+    loss2.backward()
+    ref2 = np.stack([2 * Y @ (va[k] * (Y.T @ f0[k])) for k in range(2)])
+    assert rel_err(f.grad.cpu().numpy(), ref2) < 1e-12
+    # central differences of the library's transforms along a random direction
+    dirn = rng.standard_normal((2, (L + 1) ** 2))
+    h = 1e-4
+
+    def lossf(av):
+        with torch.no_grad():
+            return float((to_dev(wm) * sht_synth(to_dev(av), g) ** 2).sum())
+    fd = (lossf(a0 + h * dirn) - lossf(a0 - h * dirn)) / (2 * h)
+    assert abs(fd - float((a.grad.cpu().numpy() * dirn).sum())) <= 1e-7 * abs(fd)
