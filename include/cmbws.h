@@ -52,8 +52,9 @@ enum {
   CMBWS_ERR_SINGULAR = -4,      /* a U block has a column with zero norm */
   CMBWS_ERR_BREAKDOWN = -5,     /* CG: p.Ap <= 0 or a non-finite scalar */
   CMBWS_ERR_NOT_CONVERGED = -6, /* CG: iteration cap reached (x holds the last iterate) */
-  CMBWS_ERR_TIMEOUT = -7        /* wall-clock budget of a solve exhausted, or a bounded
+  CMBWS_ERR_TIMEOUT = -7,       /* wall-clock budget of a solve exhausted, or a bounded
                                    device-side wait ran out (cmbws_device_status) */
+  CMBWS_ERR_COMM = -8           /* the all-reduce callback of a sharded solve failed */
 };
 
 typedef enum { CMBWS_GRID_GL = 0, CMBWS_GRID_HEALPIX = 1 } cmbws_grid_kind;
@@ -457,6 +458,42 @@ int cmbws_model_set_graphs(cmbws_model m, int on);
 int cmbws_cg_solve_batched(const cmbws_model* models, int nprob, const double* const* b,
                            double* const* x, const cmbws_cg_opts* opts, cmbws_cg_report* reports,
                            int nworkers, void* stream);
+
+/*
+ * Band sharding, for a solve spread over several GPUs (one process and one model per GPU).
+ * A is a sum over bands plus the prior (Eq. A), and M_PI = U^+ T^+ (U^+)^T is a sum over the
+ * rows of U: one term per band (its T^+_nu) and the prior rows (Sec. 3.3).  With a shard set,
+ * this model's cmbws_apply_A, cmbws_apply_precond and cmbws_rhs return only the terms of the
+ * bands it owns, plus the prior terms if prior = 1, and run the transforms of those bands
+ * only; the sum of the shards' outputs is the full result.  Every shard's model is built from
+ * the same full description (U^+ needs every band's alpha, beam and mixing).
+ *   owned: host array [nobs] of 0 / 1, or NULL to drop the shard (the full operators again).
+ * Other calls that apply or solve (cmbws_cg_solve, batched, resume, M_diag, M_add, mask
+ * preconditioners, merging, gradients, CR draws) refuse a sharded model with CMBWS_ERR_ARG.
+ * Errors: CMBWS_ERR_ARG (entries other than 0 / 1, merged rows or mask preconditioners set).
+ */
+int cmbws_model_set_shard(cmbws_model m, const int* owned, int prior);
+
+/*
+ * All-reduce callback of a sharded solve: replace the device vector v of n doubles by its sum
+ * over all shards, ordered after the work already queued on `stream` (the solve's stream,
+ * passed through), and return 0 (nonzero reports CMBWS_ERR_COMM).  Every shard must end up
+ * with the bitwise same sum (true of a ring all-reduce, or of a gather-and-add in a fixed order).
+ */
+typedef int (*cmbws_allreduce_fn)(double* v, int64_t n, void* stream, void* ctx);
+
+/*
+ * PCG (precond 0 or 1) over a band-sharded operator: every shard calls this with the same b,
+ * initial x and opts on its own model (cmbws_model_set_shard, the shards' bands together
+ * covering every band once and one shard owning the prior).  Each apply of A and of M_PI runs
+ * the shard's partial terms and one all-reduce of the stacked vector; the CG vectors stay
+ * replicated, so the scalars (dot products) are computed identically on every shard and need
+ * no collective.  Results as cmbws_cg_solve (up to the summation order of the all-reduce).
+ * Errors: as cmbws_cg_solve; CMBWS_ERR_COMM when the callback fails.
+ */
+int cmbws_cg_solve_sharded(cmbws_model m, const double* b, double* x, const cmbws_cg_opts* opts,
+                           cmbws_allreduce_fn allreduce, void* ctx, cmbws_cg_report* report,
+                           void* stream);
 
 /*
  * Variates of a counter-based stream, for constrained realizations (Sec. 2.3) drawn on the

@@ -24,7 +24,7 @@ CMBWS_3XTF32 = 4
 
 _ERRORS = {-1: "CMBWS_ERR_ARG", -2: "CMBWS_ERR_CUDA", -3: "CMBWS_ERR_NOMEM",
            -4: "CMBWS_ERR_SINGULAR", -5: "CMBWS_ERR_BREAKDOWN", -6: "CMBWS_ERR_NOT_CONVERGED",
-           -7: "CMBWS_ERR_TIMEOUT"}
+           -7: "CMBWS_ERR_TIMEOUT", -8: "CMBWS_ERR_COMM"}
 
 _lib = None
 
@@ -117,6 +117,9 @@ def load_library(path=None):
                                      ctypes.POINTER(i)]
     lib.cmbws_cg_track_error.argtypes = [vp, vp, vp]
     lib.cmbws_cg_checkpointing.argtypes = [vp, i]
+    lib.cmbws_model_set_shard.argtypes = [vp, ctypes.POINTER(i), i]
+    lib.cmbws_cg_solve_sharded.argtypes = [vp, vp, vp, ctypes.POINTER(CgOpts), vp, vp,
+                                           ctypes.POINTER(CgReport), vp]
     lib.cmbws_cg_state_export.argtypes = [vp, vp, vp, vp, ctypes.POINTER(d), vp]
     lib.cmbws_cg_resume.argtypes = [vp, vp, vp, vp, vp, vp, ctypes.POINTER(d),
                                     ctypes.POINTER(CgOpts), ctypes.POINTER(CgReport), vp]
@@ -609,6 +612,33 @@ def cmbws_cg_resume(model, b, x, d, r, p, scalars, tol=1e-6, maxiter=1000, preco
                                           _dptr(x, model.nvec, "x"), _dptr(d, model.nvec, "d"),
                                           _dptr(r, model.nvec, "r"), _dptr(p, model.nvec, "p"), sc,
                                           ctypes.byref(opts), ctypes.byref(rep), _stream(stream))
+    if check:
+        _check(code)
+    out = rep.as_dict()
+    out["code"] = code
+    return out
+
+
+def cmbws_model_set_shard(model, owned, prior=1):
+    """owned: [nobs] 0 / 1 flags (None drops the shard); prior: 1 if this shard adds the prior."""
+    if owned is None:
+        _check(load_library().cmbws_model_set_shard(model.handle, None, int(prior)))
+        return
+    arr = (ctypes.c_int * model.nobs)(*[int(v) for v in owned])
+    _check(load_library().cmbws_model_set_shard(model.handle, arr, int(prior)))
+
+
+def cmbws_cg_solve_sharded(model, b, x, allreduce, tol=1e-6, maxiter=1000, precond=1,
+                           inner_tol=1e-3, max_outer=20, timeout_s=0.0, cert_prec=CMBWS_FP64,
+                           stream=None, check=True):
+    """PCG over a band-sharded operator; allreduce: a ctypes callback (sharding.make_allreduce)."""
+    opts = CgOpts(float(tol), int(maxiter), int(precond), float(inner_tol), int(max_outer),
+                  float(timeout_s), int(cert_prec))
+    rep = CgReport()
+    fn = ctypes.cast(allreduce, ctypes.c_void_p)
+    code = load_library().cmbws_cg_solve_sharded(model.handle, _dptr(b, model.nvec, "b"),
+                                                 _dptr(x, model.nvec, "x"), ctypes.byref(opts), fn,
+                                                 None, ctypes.byref(rep), _stream(stream))
     if check:
         _check(code)
     out = rep.as_dict()

@@ -125,12 +125,31 @@ struct Clock {
   }
 };
 
+// The all-reduce of a band-sharded solve: called on each operator output so that every shard
+// holds the full A p, M r and A x (cmbws_cg_solve_sharded).
+struct Comm {
+  cmbws_allreduce_fn fn;
+  void* ctx;
+};
+
 struct Solver {
   Model& M;
   cudaStream_t s;
   int64_t n;
   double* red;     // [kRedBlocks + 1]
   double* hscal;   // pinned host scalar
+  const Comm* comm = nullptr;
+
+  // sum a device vector of n doubles over the shards (no-op for unsharded solves)
+  int reduce(double* v) {
+    if (!comm) return CMBWS_OK;
+    const int rc = comm->fn(v, n, (void*)s, comm->ctx);
+    if (rc != 0) {
+      set_error("sharded solve: the all-reduce callback returned %d", rc);
+      return CMBWS_ERR_COMM;
+    }
+    return CMBWS_OK;
+  }
 
   int finish(double* out) {
     {
@@ -155,6 +174,7 @@ struct Solver {
   // r = b - A x (FP64-accurate chain), returns ||r||^2
   int true_residual(const double* b, const double* x, double* r, double* tmp, double* rr) {
     CMBWS_TRY(M.apply_A(x, tmp, cert, s));
+    CMBWS_TRY(reduce(tmp));
     {
       ProfScope ps_(PROF_CG, s);
       k_resid<<<kRedBlocks, kRedThreads, 0, s>>>(b, tmp, r, n, red);
@@ -292,6 +312,10 @@ static int pcg_core(Solver& S, int prec, int use_M, double* d, double* r, double
   const int64_t n = S.n;
   auto precond = [&]() {
     if (!use_M) return precondition(M, use_M, prec, r, z, n, S.s);
+    if (S.comm) {  // sharded: the partial M r, summed over the shards (no graphs)
+      CMBWS_TRY(precondition(M, use_M, prec, r, z, n, S.s));
+      return S.reduce(z);
+    }
     return run_op(M, OP_PRECOND + 16 * use_M, prec, r, z, S.s,
                   [&]() { return precondition(M, use_M, prec, r, z, n, S.s); });
   };
@@ -316,7 +340,12 @@ static int pcg_core(Solver& S, int prec, int use_M, double* d, double* r, double
     *rz_out = rz;
   }
   for (int it = start.resume ? start.it0 : 0; it < maxit; ++it) {
-    CMBWS_TRY(run_op(M, OP_APPLY_A, prec, p, q, S.s, [&]() { return M.apply_A(p, q, prec, S.s); }));
+    if (S.comm) {  // sharded: the partial A p, summed over the shards (no graphs)
+      CMBWS_TRY(M.apply_A(p, q, prec, S.s));
+      CMBWS_TRY(S.reduce(q));
+    } else {
+      CMBWS_TRY(run_op(M, OP_APPLY_A, prec, p, q, S.s, [&]() { return M.apply_A(p, q, prec, S.s); }));
+    }
     double pq;
     CMBWS_TRY(S.dot(p, q, &pq));
     if (!(pq > 0.0) || !std::isfinite(pq) || !std::isfinite(rz)) {
@@ -367,7 +396,8 @@ static int pcg_core(Solver& S, int prec, int use_M, double* d, double* r, double
 // without FP32 transforms) the run continues the exported PCG state that the caller placed in
 // cg_d, cg_r and cg_p, with x holding the same initial guess as the interrupted solve.
 static int cg_solve_impl(Model& M, const double* b, double* x, const cmbws_cg_opts& o,
-                         cmbws_cg_report& rep, cudaStream_t s, const PcgStart* resume = nullptr) {
+                         cmbws_cg_report& rep, cudaStream_t s, const PcgStart* resume = nullptr,
+                         const Comm* comm = nullptr) {
   const Clock clk;
   const int64_t n = M.nvec;
   CMBWS_TRY(M.cg_r.ensure(n * 8));
@@ -385,6 +415,7 @@ static int cg_solve_impl(Model& M, const double* b, double* x, const cmbws_cg_op
   } fr{hscal};
   Solver S{M, s, n, M.cg_red.as<double>(), hscal};
   S.cert = o.cert_prec == CMBWS_FP32X2 ? CMBWS_FP32X2 : CMBWS_FP64;
+  S.comm = comm;
   const long long sht0 = M.n_sht;
   M.hist_res.clear();
   M.hist_err.clear();
@@ -505,6 +536,7 @@ extern "C" int cmbws_cg_solve(cmbws_model mh, const double* b, double* x, const 
                               cmbws_cg_report* report, void* stream) {
   clear_error();
   Model* M = as_model(mh);
+  if (refuse_sharded(M, "cmbws_cg_solve")) return CMBWS_ERR_ARG;
   if (!M || !b || !x || !opts || b == x || !(opts->tol > 0.0) || opts->maxiter < 1 ||
       opts->precond < 0 || opts->precond > 3) {
     set_error("cmbws_cg_solve: invalid arguments");
@@ -544,7 +576,8 @@ extern "C" int cmbws_cg_solve_batched(const cmbws_model* models, int nprob, cons
     return CMBWS_ERR_ARG;
   }
   for (int i = 0; i < nprob; ++i) {
-    if (!as_model(models[i]) || !b[i] || !x[i] || b[i] == x[i]) {
+    if (!as_model(models[i]) || !b[i] || !x[i] || b[i] == x[i] ||
+        refuse_sharded(as_model(models[i]), "cmbws_cg_solve_batched")) {
       set_error("cmbws_cg_solve_batched: invalid arguments for problem %d", i);
       return CMBWS_ERR_ARG;
     }
@@ -683,6 +716,7 @@ extern "C" int cmbws_cg_resume(cmbws_model mh, const double* b, double* x, const
                                const cmbws_cg_opts* opts, cmbws_cg_report* report, void* stream) {
   clear_error();
   Model* M = as_model(mh);
+  if (refuse_sharded(M, "cmbws_cg_resume")) return CMBWS_ERR_ARG;
   if (!M || !b || !x || !d || !r || !p || !scalars || !opts || b == x || !(opts->tol > 0.0) ||
       opts->maxiter < 1 || opts->precond < 0 || opts->precond > 3) {
     set_error("cmbws_cg_resume: invalid arguments");
@@ -720,4 +754,27 @@ extern "C" int cmbws_cg_resume(cmbws_model mh, const double* b, double* x, const
   rep.status = code;
   if (report) *report = rep;
   return code;
+}
+
+extern "C" int cmbws_cg_solve_sharded(cmbws_model mh, const double* b, double* x,
+                                      const cmbws_cg_opts* opts, cmbws_allreduce_fn allreduce,
+                                      void* ctx, cmbws_cg_report* report, void* stream) {
+  clear_error();
+  Model* M = as_model(mh);
+  if (!M || !b || !x || !opts || !allreduce || b == x || !(opts->tol > 0.0) ||
+      opts->maxiter < 1 || opts->precond < 0 || opts->precond > 1) {
+    set_error("cmbws_cg_solve_sharded: invalid arguments (precond must be 0 or 1)");
+    return CMBWS_ERR_ARG;
+  }
+  cmbws_cg_opts o = *opts;
+  if (!(o.inner_tol > 0.0 && o.inner_tol < 1.0)) o.inner_tol = 1e-3;
+  if (o.max_outer < 1) o.max_outer = 20;
+  const Comm comm{allreduce, ctx};
+  cmbws_cg_report rep{};
+  const auto t0 = std::chrono::steady_clock::now();
+  const int st = cg_solve_impl(*M, b, x, o, rep, (cudaStream_t)stream, nullptr, &comm);
+  rep.ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  rep.status = st;
+  if (report) *report = rep;
+  return st;
 }

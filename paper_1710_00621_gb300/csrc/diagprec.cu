@@ -279,6 +279,7 @@ using namespace cmbws;
 extern "C" int cmbws_apply_M_diag(cmbws_model mh, const double* r, double* z, void* stream) {
   clear_error();
   Model* M = as_model(mh);
+  if (refuse_sharded(M, "cmbws_apply_M_diag")) return CMBWS_ERR_ARG;
   if (!M || !r || !z || r == z) {
     set_error("cmbws_apply_M_diag: invalid arguments");
     return CMBWS_ERR_ARG;

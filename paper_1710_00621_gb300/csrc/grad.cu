@@ -199,6 +199,7 @@ extern "C" int cmbws_grad_terms(cmbws_model mh, const double* x, const double* l
                                 const double* omega2, double* out, void* stream) {
   clear_error();
   Model* M = as_model(mh);
+  if (refuse_sharded(M, "cmbws_grad_terms")) return CMBWS_ERR_ARG;
   if (!M || !x || !lambda || !d || !out) {
     set_error("cmbws_grad_terms: invalid arguments");
     return CMBWS_ERR_ARG;

@@ -472,6 +472,7 @@ extern "C" int cmbws_model_add_mask_precond(cmbws_model mh, int comp, int nside,
                                             int max_bottom, void* stream) {
   clear_error();
   Model* M = as_model(mh);
+  if (refuse_sharded(M, "cmbws_model_add_mask_precond")) return CMBWS_ERR_ARG;
   if (!M || !mask || comp < 0 || comp >= M->ncomp || nside < 1 || max_bottom < 1 ||
       max_bottom > 4096) {
     set_error("cmbws_model_add_mask_precond: invalid arguments");
@@ -501,6 +502,7 @@ extern "C" int cmbws_model_set_vcycle(cmbws_model mh, int kind) {
 extern "C" int cmbws_apply_M_add(cmbws_model mh, const double* r, double* z, void* stream) {
   clear_error();
   Model* M = as_model(mh);
+  if (refuse_sharded(M, "cmbws_apply_M_add")) return CMBWS_ERR_ARG;
   if (!M || !r || !z || r == z) {
     set_error("cmbws_apply_M_add: invalid arguments");
     return CMBWS_ERR_ARG;

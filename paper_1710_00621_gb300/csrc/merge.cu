@@ -260,6 +260,7 @@ using namespace cmbws;
 extern "C" int cmbws_model_merge_precond(cmbws_model mh, const int* group, void* stream) {
   clear_error();
   Model* M = as_model(mh);
+  if (refuse_sharded(M, "cmbws_model_merge_precond")) return CMBWS_ERR_ARG;
   if (!M) {
     set_error("cmbws_model_merge_precond: invalid model");
     return CMBWS_ERR_ARG;

@@ -83,6 +83,7 @@ __global__ void k_mix_adjoint(HarmDev h, BandDev bd, int k, const double* __rest
   if (l > Lk) return;
   double yr = 0.0, yi = 0.0;
   for (int nu = 0; nu < h.nobs; ++nu) {
+    if (!((h.own >> nu) & 1)) continue;  // another shard's band
     const PairDev& pd = h.pairs[nu * h.ncomp + k];
     if (pd.var) {
       // Q~^T B u_nu from the transposed mixing chain (covers l <= L_k)
@@ -99,11 +100,12 @@ __global__ void k_mix_adjoint(HarmDev h, BandDev bd, int k, const double* __rest
     yi += w * u.y;
   }
   const int64_t base = h.compOff[k] + packed_off(Lk, m);
-  const double ci = x ? h.cinv[h.clOff[k] + l] : 0.0;
-  y[base + (l - m)] = yr + (x ? ci * x[base + (l - m)] : 0.0);
+  const bool pr = x && h.prior_on;
+  const double ci = pr ? h.cinv[h.clOff[k] + l] : 0.0;
+  y[base + (l - m)] = yr + (pr ? ci * x[base + (l - m)] : 0.0);
   if (m > 0) {
     const int64_t is = base + (Lk - m + 1) + (l - m);
-    y[is] = yi + (x ? ci * x[is] : 0.0);
+    y[is] = yi + (pr ? ci * x[is] : 0.0);
   }
 }
 
@@ -256,7 +258,7 @@ __global__ void k_pinv(HarmDev h, BandDev bd, const double* __restrict__ tp, dou
   for (int c = 0; c < nc; ++c) zr[c] = zi[c] = 0.0;
   for (int nu = 0; nu < h.nobs; ++nu) {
     const int Ln = bd.L[nu];
-    if (l > Ln) continue;
+    if (l > Ln || !((h.own >> nu) & 1)) continue;
     const double2 u = bd.out[nu][lm_off(Ln, m) + (l - m)];
     for (int c = 0; c < nc; ++c) {
       const double w = U[c * nr + nu];
@@ -266,7 +268,7 @@ __global__ void k_pinv(HarmDev h, BandDev bd, const double* __restrict__ tp, dou
   }
   for (int k = 0; k < nc; ++k) {
     const int Lk = h.compL[k];
-    if (l > Lk) continue;
+    if (l > Lk || !h.prior_on) continue;
     const int64_t base = h.compOff[k] + packed_off(Lk, m);
     const double tr = tp[base + (l - m)];
     const double ti = m > 0 ? tp[base + (Lk - m + 1) + (l - m)] : 0.0;
@@ -344,7 +346,7 @@ __global__ void k_add_scaled_prior(HarmDev h, const double* __restrict__ w2, dou
   const int m = blockIdx.y;
   const int Lk = h.compL[k];
   const int l = m + blockIdx.x * blockDim.x + threadIdx.x;
-  if (l > Lk) return;
+  if (l > Lk || !h.prior_on) return;  // the prior terms belong to one shard
   const int64_t base = h.compOff[k] + packed_off(Lk, m);
   const double s = h.cisq[h.clOff[k] + l];
   b[base + (l - m)] += s * w2[base + (l - m)];
@@ -447,6 +449,8 @@ HarmDev Model::harm() const {
   h.Up = d_Up.as<double>();
   h.Lup = Lup;
   h.pairs = d_pairs.as<PairDev>();
+  h.own = shard_own;
+  h.prior_on = shard_prior ? 1 : 0;
   return h;
 }
 
@@ -560,6 +564,7 @@ int Model::apply_A(const double* x, double* y, int prec, cudaStream_t s) {
   const HarmDev h = harm();
   if (nmix) CMBWS_TRY(mixvar_forward(prec, x, s));
   for (Group& G : groups) {
+    if (!group_owned(G)) continue;  // another shard's bands
     CMBWS_TRY(mix_forward(G, prec, x, s));
     CMBWS_TRY(group_chain(G, prec, 0, s));
   }
@@ -627,7 +632,8 @@ int Model::apply_precond(const double* r, double* z, int prec, cudaStream_t s) {
     else k_pinv_T<float2><<<grd, 128, 0, s>>>(h, bd, r, tprior.as<double>(), Lall);
     CMBWS_LAUNCH_CHECK();
   }
-  for (Group& G : groups) CMBWS_TRY(group_chain(G, prec, 1, s));
+  for (Group& G : groups)
+    if (group_owned(G)) CMBWS_TRY(group_chain(G, prec, 1, s));
   {
     dim3 grd((Lcomp + 1 + 127) / 128, Lcomp + 1);
     ProfScope ps(PROF_HARM, s, is_f32(prec) ? 0 : 1);
@@ -644,6 +650,7 @@ int Model::rhs(const double* const* d, const double* const* w1, const double* w2
   const int ap = prec == CMBWS_FP64 ? CMBWS_FP64 : CMBWS_FP32X2;  // FP64-accurate either way
   // P^T applied to the pixel maps: per group, analysis FFT (unweighted) + Legendre adjoint
   for (Group& G : groups) {
+    if (!group_owned(G)) continue;  // another shard's bands
     const Grid& g = *G.grid;
     CMBWS_TRY(pixtmp.ensure((size_t)G.nmaps * g.npix * 8));
     for (int j = 0; j < G.nmaps; ++j) {
@@ -1040,4 +1047,37 @@ extern "C" int cmbws_rhs(cmbws_model mh, const double* const* d, const double* c
       return CMBWS_ERR_ARG;
     }
   return M->rhs(d, omega1, omega2, b, (cudaStream_t)stream);
+}
+
+extern "C" int cmbws_model_set_shard(cmbws_model mh, const int* owned, int prior) {
+  clear_error();
+  Model* M = as_model(mh);
+  if (!M) {
+    set_error("cmbws_model_set_shard: invalid model");
+    return CMBWS_ERR_ARG;
+  }
+  if (!owned) {
+    M->shard_on = false;
+    M->shard_own = ~0ull;
+    M->shard_prior = true;
+    M->drop_graphs();
+    return CMBWS_OK;
+  }
+  if (M->merged || !M->masks.empty()) {
+    set_error("cmbws_model_set_shard: not available with merged rows or mask preconditioners");
+    return CMBWS_ERR_ARG;
+  }
+  uint64_t own = 0;
+  for (int nu = 0; nu < M->nobs; ++nu) {
+    if (owned[nu] != 0 && owned[nu] != 1) {
+      set_error("cmbws_model_set_shard: owned[%d] must be 0 or 1", nu);
+      return CMBWS_ERR_ARG;
+    }
+    if (owned[nu]) own |= 1ull << nu;
+  }
+  M->shard_on = true;
+  M->shard_own = own;
+  M->shard_prior = prior != 0;
+  M->drop_graphs();
+  return CMBWS_OK;
 }

@@ -37,6 +37,8 @@ struct HarmDev {
   const int64_t* clOff;
   const double* Up;        // U^+ [Lup+1][ncomp][nobs+ncomp]
   const PairDev* pairs;    // [nobs * ncomp] variable-mixing pairs (var = 0: scalar q)
+  uint64_t own;            // bands whose terms this model adds (bit nu; all unless sharded)
+  int prior_on;            // 1 if this model adds the prior terms (always unless sharded)
 };
 
 struct GroupDev {
@@ -160,6 +162,17 @@ struct Model {
   std::vector<OpGraph> graphs;
   void drop_graphs();
 
+  // band sharding (cmbws_model_set_shard): the bands and the prior terms this model adds to
+  // apply_A, apply_precond and rhs; the sum over the shards of all models is the full operator
+  bool shard_on = false;
+  uint64_t shard_own = ~0ull;
+  bool shard_prior = true;
+  bool group_owned(const Group& G) const {
+    for (int j = 0; j < G.nmaps; ++j)
+      if ((shard_own >> G.bands[j]) & 1) return true;
+    return false;
+  }
+
   // mask-restricted preconditioners (Sec. 4), applied with M_PI when precond = 2
   std::vector<MaskMG*> masks;
   int vcycle = 0;  // V-cycle of the mask preconditioners: 0 basic, 1 optimized (J ~ I)
@@ -180,6 +193,16 @@ struct Model {
 };
 
 int model_create(const cmbws_model_desc* desc, int prec, cudaStream_t s, Model** out);
+
+// Calls other than cmbws_apply_A, cmbws_apply_precond, cmbws_rhs, cmbws_project and the
+// sharded solve refuse a sharded model (their results would be one shard's partial terms).
+inline bool refuse_sharded(const Model* M, const char* fn) {
+  if (M && M->shard_on) {
+    set_error("%s: the model is sharded (cmbws_model_set_shard); use cmbws_cg_solve_sharded", fn);
+    return true;
+  }
+  return false;
+}
 
 // the model behind a handle, or nullptr if the handle is not a live model
 inline Model* as_model(const void* h) {

@@ -141,6 +141,7 @@ extern "C" int cmbws_cr_sample(cmbws_model mh, const double* const* d, uint64_t 
                                cmbws_cg_report* report, void* stream) {
   clear_error();
   Model* M = as_model(mh);
+  if (refuse_sharded(M, "cmbws_cr_sample")) return CMBWS_ERR_ARG;
   if (!M || !d || !x || !opts) {
     set_error("cmbws_cr_sample: invalid arguments");
     return CMBWS_ERR_ARG;
@@ -160,6 +161,7 @@ extern "C" int cmbws_cr_rhs(cmbws_model mh, const double* const* d, uint64_t see
                             uint64_t sample, double* b, void* stream) {
   clear_error();
   Model* M = as_model(mh);
+  if (refuse_sharded(M, "cmbws_cr_rhs")) return CMBWS_ERR_ARG;
   if (!M || !d || !b) {
     set_error("cmbws_cr_rhs: invalid arguments");
     return CMBWS_ERR_ARG;
