@@ -337,7 +337,7 @@ extern "C" int cmbws_sht_analysis(cmbws_grid gh, cmbws_prec prec, const double* 
   const size_t pb = legendre_adjoint_part_bytes(*g, prec, nmaps);
   CMBWS_TRY(g->ws_part.ensure(pb));
   CMBWS_TRY(g->ws_out.ensure((size_t)nmaps * nlm * 16));
-  CMBWS_TRY(ringfft_analysis(*g, prec, nmaps, map, weighted, g->ws_F.p, s));
+  CMBWS_TRY(ringfft_analysis(*g, prec, nmaps, map, weighted, g->ws_F.p, g->ws_part.p, s));
   CMBWS_TRY(legendre_adjoint(*g, prec, nmaps, g->ws_F.p, g->ws_part.p, g->ws_part.bytes,
                              g->ws_out.as<double>(), s));
   CMBWS_TRY(unpack_alm(*g, nmaps, g->ws_out.as<double>(), alm, s));

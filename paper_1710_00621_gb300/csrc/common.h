@@ -198,19 +198,30 @@ inline Grid* as_grid(const void* h) {
 // ---- launchers (legendre.cu) ----
 // alm: [nmaps][nlm] complex coefficients multiplied by c_lm; F: [nmaps][nring][L+1]
 int legendre_synth(const Grid& g, int prec, int nmaps, const void* alm, void* F, cudaStream_t s);
-// F -> per-CTA partial sums -> out[nmaps][nlm] complex FP64 (final coefficients)
+// ring spectra -> out[nmaps][nlm] complex FP64 (final coefficients).  FP64 reads F (with
+// per-CTA partial sums in part); the other precisions read the eo layout, which the forward
+// ring FFT wrote into part.
 int legendre_adjoint(const Grid& g, int prec, int nmaps, const void* F, void* part, size_t part_bytes,
                      double* out, cudaStream_t s);
 size_t legendre_adjoint_part_bytes(const Grid& g, int prec, int nmaps);
 
 // ---- launchers (ringfft.cu) ----
+// Layout of the adjoint Legendre input ("eo") that the forward ring FFTs write for the
+// checkpointed adjoints (every precision but FP64): maps in chunks of eo_maps(prec) (the
+// adjoint's maps per launch); chunk c starts at scalar c * eo_maps * (L+1) * npair * 4 and,
+// for its NMc maps, holds eo[(m * npair + p) * 4 NMc + q]: q < 2 NMc the even-l parts
+// (north + south ring spectra, re / im per map), q >= 2 NMc the odd-l parts (north - south).
+// Scalars are float (FP32 modes) or double-float pairs (FP32X2).
+inline int eo_maps(int prec) { return prec == CMBWS_FP32X2 ? 3 : 4; }
 // F (ring spectra) -> pixel maps map[nmaps][npix] (FP64 out)
 int ringfft_synth(const Grid& g, int prec, int nmaps, const void* F, double* map, cudaStream_t s);
-// map[nmaps][npix] (FP64 in) -> F; weighted: multiply by quadrature weights
+// map[nmaps][npix] (FP64 in) -> ring spectra: F (FP64) or the adjoint input eo (other
+// precisions); weighted: multiply by quadrature weights
 int ringfft_analysis(const Grid& g, int prec, int nmaps, const double* map, int weighted, void* F,
-                     cudaStream_t s);
-// F -> pixels -> * pix[map] -> F, in place. pix: [nmaps] device pointers (prec type) of npix.
-int ringfft_fused(const Grid& g, int prec, int nmaps, void* F, const void* const* pix,
+                     void* eo, cudaStream_t s);
+// F -> pixels -> * pix[map] -> ring spectra, written to F in place (FP64) or to eo (other
+// precisions).  pix: [nmaps] device pointers (prec type) of npix.
+int ringfft_fused(const Grid& g, int prec, int nmaps, void* F, const void* const* pix, void* eo,
                   cudaStream_t s);
 int ringfft_smem_ok(const Grid& g, int prec);
 
@@ -246,9 +257,9 @@ int legendre_synth_tc(const Grid& g, int prec, int nmaps, const void* alm, void*
 // reads and clears the device-side status of the tensor-core kernels of the current device
 // (synchronous): *timed_out is true if a bounded mbarrier wait ran out since the last read
 int tc_status_take(bool* timed_out);
-// double-float adjoint from chunk checkpoints: F (FP64 ring spectra of nm maps) ->
-// out (FP64 coefficients); eo is a scratch of legendre_adjoint_part_bytes bytes
-int legendre_adj_df_ck(const Grid& g, int nm, const void* F, void* eo, double* out, cudaStream_t s);
+// double-float adjoint from chunk checkpoints: eo (double-float adjoint input of nm <= 3
+// maps) -> out (FP64 coefficients)
+int legendre_adj_df_ck(const Grid& g, int nm, const void* eo, double* out, cudaStream_t s);
 
 // Raise a kernel's dynamic shared-memory limit to at least `bytes` on the current device.
 // The limit only ever grows, so concurrent launches with different sizes (several host

@@ -161,7 +161,8 @@ static int grad_terms(Model& M, const double* x, const double* lam, const double
             M.pixA64[nu].as<double>(), M.tausq[nu].as<double>(), mp[nu], g.npix, pass == 0);
         CMBWS_LAUNCH_CHECK();
       }
-      CMBWS_TRY(ringfft_analysis(g, ap, G.nmaps, M.gradmaps.as<double>() + goff[gi], 0, G.F.p, s));
+      CMBWS_TRY(ringfft_analysis(g, ap, G.nmaps, M.gradmaps.as<double>() + goff[gi], 0, G.F.p,
+                                 M.part.p, s));
       CMBWS_TRY(legendre_adjoint(g, ap, G.nmaps, G.F.p, M.part.p, M.part.bytes, G.out.as<double>(), s));
     }
     M.n_sht += M.nobs;

@@ -384,32 +384,11 @@ k_leg_adj2(const typename V2<T>::t* __restrict__ F, int64_t F_stride, const T* _
 // values (setup.cu), so no thread needs another thread's sums: each output (l, m) is
 // owned by one thread and summed over the pairs in a fixed order.
 // Tiles of PT pairs are staged in shared memory with cp.async, double-buffered: the
-// per-pair even/odd parts E, O (prepared by k_adj_eo), y, the start index and values,
+// per-pair even/odd parts E, O (written by the forward ring FFT), y, the start index and values,
 // and each thread's own column of checkpoints, so the HBM reads of the next tile
 // overlap the arithmetic of the current one.
 // E/O parts of every (pair, m): eo[(m * npair + p) * 2P + q], q < P even-l parts (north +
 // south), q >= P odd-l parts (north - south), parts = (re, im) per map.
-template <int NM>
-__global__ void k_adj_eo(const float2* __restrict__ F, int64_t F_stride, const int2* __restrict__ pring,
-                         float* __restrict__ eo, int L, int npair) {
-  constexpr int P = 2 * NM;
-  const int m = blockIdx.y;
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= npair) return;
-  const int2 rr = pring[p];
-  float* e = eo + ((int64_t)m * npair + p) * 2 * P;
-#pragma unroll
-  for (int k = 0; k < NM; ++k) {
-    const float2 gn = F[k * F_stride + (int64_t)rr.x * (L + 1) + m];
-    float2 gs = make_float2(0.f, 0.f);
-    if (rr.y >= 0) gs = F[k * F_stride + (int64_t)rr.y * (L + 1) + m];
-    e[2 * k] = gn.x + gs.x;
-    e[2 * k + 1] = gn.y + gs.y;
-    e[P + 2 * k] = rr.y >= 0 ? gn.x - gs.x : gn.x;
-    e[P + 2 * k + 1] = rr.y >= 0 ? gn.y - gs.y : gn.y;
-  }
-}
-
 template <int NM, int PT>
 struct AdjCkWarp {  // one warp's double-buffered tile
   float eo[2][PT][4 * NM];
@@ -495,11 +474,14 @@ k_leg_adj_ck(const float* __restrict__ eo, const float* __restrict__ Acoef,
       const int bf = k & 1;
       const int np = min(PT, npair - t * PT);
       for (int i = 0; i < np; ++i) {
-        const int jinj = S.ls[bf][i] - l0;  // where the pair starts, relative to the chunk
-        if (jinj > K - 1) continue;         // the pair starts after this chunk
+        const int lsp = S.ls[bf][i];
+        if (lsp > l0 + K - 1) continue;  // the pair starts after this chunk
         const float2 cv = S.ck[bf][i][lane];
-        const float2 sv = S.st[bf][i];
-        float ma = jinj == 0 ? sv.x : cv.x, mb = jinj == 0 ? sv.y : cv.y;
+        float ma = cv.x, mb = cv.y;
+        if (lsp == l0) {
+          ma = S.st[bf][i].x;
+          mb = S.st[bf][i].y;
+        }
         const float yv = S.y[bf][i];
         const float* e = S.eo[bf][i];
 #pragma unroll
@@ -511,9 +493,9 @@ k_leg_adj_ck(const float* __restrict__ eo, const float* __restrict__ Acoef,
         for (int j = 2; j < K; j += 2) {
           float na = fmaf(-Al[j], yv, Al[j]) * mb - ma;
           float nb = fmaf(-Al[j + 1], yv, Al[j + 1]) * na - mb;
-          if (j == jinj) {
-            na = sv.x;
-            nb = sv.y;
+          if (l0 + j == lsp) {
+            na = S.st[bf][i].x;
+            nb = S.st[bf][i].y;
           }
           ma = na;
           mb = nb;
@@ -630,19 +612,10 @@ int adj_nblk(const Grid& g) {
 }
 
 template <int NM>
-int launch_adj_ck(const Grid& g, const void* F, int64_t F_stride, void* part, double* out,
-                  cudaStream_t s) {
+int launch_adj_ck(const Grid& g, const float* eo, double* out, cudaStream_t s) {
   constexpr int NT = 128, PT = 16;
   const int L = g.lmax;
   const int64_t nlm = nlm_of(L);
-  float* eo = (float*)part;  // [L+1][npair][2P] floats, sized by legendre_adjoint_part_bytes
-  {
-    dim3 grd((g.npair + 127) / 128, L + 1);
-    ProfScope ps(PROF_LEG_RED, s, 0);
-    k_adj_eo<NM><<<grd, 128, 0, s>>>((const float2*)F, F_stride, g.pair_ring.as<int2>(), eo, L,
-                                     g.npair);
-    CMBWS_LAUNCH_CHECK();
-  }
   dim3 grd((g.nwt32 + NT / 32 - 1) / (NT / 32));
   constexpr size_t sm = sizeof(AdjCkWarp<NM, PT>) * (NT / 32);
   auto kern = k_leg_adj_ck<NM, NT, PT>;
@@ -658,7 +631,6 @@ int launch_adj_ck(const Grid& g, const void* F, int64_t F_stride, void* part, do
 
 template <typename T, int NM>
 int launch_adj(const Grid& g, const void* F, int64_t F_stride, T* part, double* out, cudaStream_t s) {
-  if (std::is_same<T, float>::value) return launch_adj_ck<NM>(g, F, F_stride, part, out, s);
   using C = Cfg<T>;
   using T2 = typename V2<T>::t;
   const int L = g.lmax;
@@ -724,6 +696,25 @@ int adj_dispatch(const Grid& g, int nmaps, const void* F, void* part, double* ou
   return CMBWS_OK;
 }
 
+// FP32 adjoints from the adjoint input (eo layout, chunks of 4 maps) that the ring FFT wrote
+int adj_dispatch_ck(const Grid& g, int nmaps, const float* eo, double* out, cudaStream_t s) {
+  const int64_t nlm = nlm_of(g.lmax), cs = (int64_t)(g.lmax + 1) * g.npair * 4;
+  for (int k0 = 0; k0 < nmaps; k0 += 4) {
+    const int nm = nmaps - k0 < 4 ? nmaps - k0 : 4;
+    const float* e = eo + k0 * cs;
+    double* o = out + 2 * k0 * nlm;
+    int st = CMBWS_OK;
+    switch (nm) {
+      case 1: st = launch_adj_ck<1>(g, e, o, s); break;
+      case 2: st = launch_adj_ck<2>(g, e, o, s); break;
+      case 3: st = launch_adj_ck<3>(g, e, o, s); break;
+      default: st = launch_adj_ck<4>(g, e, o, s); break;
+    }
+    if (st != CMBWS_OK) return st;
+  }
+  return CMBWS_OK;
+}
+
 }  // namespace
 
 int legendre_synth(const Grid& g, int prec, int nmaps, const void* alm, void* F, cudaStream_t s) {
@@ -734,11 +725,11 @@ int legendre_synth(const Grid& g, int prec, int nmaps, const void* alm, void* F,
 }
 
 size_t legendre_adjoint_part_bytes(const Grid& g, int prec, int nmaps) {
-  const int nm = nmaps < 4 ? nmaps : 4;
-  if (is_f32(prec))  // E/O parts of the checkpointed FP32 adjoint
-    return (size_t)(g.lmax + 1) * g.npair * 4 * nm * sizeof(float);
-  if (prec == CMBWS_FP32X2)  // double-float E/O parts
-    return (size_t)(g.lmax + 1) * g.npair * 4 * nm * 2 * sizeof(float);
+  // the adjoint input (eo layout) of every map: (L+1) npair 4 scalars per map
+  const size_t eo = (size_t)nmaps * (g.lmax + 1) * g.npair * 4;
+  if (is_f32(prec)) return eo * sizeof(float);
+  if (prec == CMBWS_FP32X2) return eo * 2 * sizeof(float);
+  const int nm = nmaps < 4 ? nmaps : 4;  // FP64: per-CTA partial sums of one launch
   return (size_t)adj_nblk<double>(g) * 2 * nm * nlm_of(g.lmax) * sizeof(double);
 }
 
@@ -749,16 +740,16 @@ int legendre_adjoint(const Grid& g, int prec, int nmaps, const void* F, void* pa
     return CMBWS_ERR_ARG;
   }
   if (prec == CMBWS_FP32X2) {
-    const int64_t nlm = nlm_of(g.lmax), fs = (int64_t)g.nring * (g.lmax + 1);
+    const int64_t nlm = nlm_of(g.lmax), cs = (int64_t)(g.lmax + 1) * g.npair * 4;
     // at most 3 maps per launch: 4 maps' double-float accumulators exceed the register file
     for (int k0 = 0; k0 < nmaps; k0 += 3) {
       const int nm = nmaps - k0 < 3 ? nmaps - k0 : 3;
-      CMBWS_TRY(legendre_adj_df_ck(g, nm, (const double2*)F + k0 * fs, part, out + 2 * k0 * nlm, s));
+      CMBWS_TRY(legendre_adj_df_ck(g, nm, (const float2*)part + k0 * cs, out + 2 * k0 * nlm, s));
     }
     return CMBWS_OK;
   }
   if (prec == CMBWS_FP64) return adj_dispatch<double>(g, nmaps, F, part, out, s);
-  return adj_dispatch<float>(g, nmaps, F, part, out, s);
+  return adj_dispatch_ck(g, nmaps, (const float*)part, out, s);
 }
 
 }  // namespace cmbws

@@ -143,31 +143,6 @@ k_leg_synth_df(const double2* __restrict__ alm, int64_t alm_stride, const float2
   }
 }
 
-// E/O parts of every (pair, m) as double-float pairs: eo[(m * npair + p) * 2P + q],
-// q < P even-l parts (north + south), q >= P odd-l parts (north - south).
-template <int NM>
-__global__ void k_adj_eo_df(const df2* __restrict__ F, int64_t F_stride,
-                            const int2* __restrict__ pring, float2* __restrict__ eo, int L, int npair) {
-  constexpr int P = 2 * NM;
-  const int m = blockIdx.y;
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= npair) return;
-  const int2 rr = pring[p];
-  float2* e = eo + ((int64_t)m * npair + p) * 2 * P;
-#pragma unroll
-  for (int k = 0; k < NM; ++k) {
-    const df2 gn = F[k * F_stride + (int64_t)rr.x * (L + 1) + m];
-    df2 gs{df(0.f, 0.f), df(0.f, 0.f)};
-    if (rr.y >= 0) gs = F[k * F_stride + (int64_t)rr.y * (L + 1) + m];
-    const df er = gn.x + gs.x, ei = gn.y + gs.y;
-    const df orr = gn.x - gs.x, oi = gn.y - gs.y;
-    e[2 * k] = make_float2(er.h, er.l);
-    e[2 * k + 1] = make_float2(ei.h, ei.l);
-    e[P + 2 * k] = make_float2(orr.h, orr.l);
-    e[P + 2 * k + 1] = make_float2(oi.h, oi.l);
-  }
-}
-
 template <int NM, int PT>
 struct AdjCkDfWarp {  // one warp's double-buffered tile
   float2 eo[2][PT][4 * NM];
@@ -329,16 +304,9 @@ int launch_synth_df(const Grid& g, const void* alm, int64_t as, void* F, int64_t
 constexpr int kANT = 128, kAPT = 8;
 
 template <int NM>
-int launch_adj_ck_df(const Grid& g, const void* F, int64_t fs, void* eo_buf, double* out, cudaStream_t s) {
+int launch_adj_ck_df(const Grid& g, const float2* eo, double* out, cudaStream_t s) {
   const int L = g.lmax;
   const int64_t nlm = nlm_of(L);
-  float2* eo = (float2*)eo_buf;  // [L+1][npair][2P] double-float pairs
-  {
-    dim3 grd((g.npair + 127) / 128, L + 1);
-    ProfScope ps(PROF_LEG_RED, s, 2);
-    k_adj_eo_df<NM><<<grd, 128, 0, s>>>((const df2*)F, fs, g.pair_ring.as<int2>(), eo, L, g.npair);
-    CMBWS_LAUNCH_CHECK();
-  }
   dim3 grd((g.nwtdf + kANT / 32 - 1) / (kANT / 32));
   constexpr size_t sm = sizeof(AdjCkDfWarp<NM, kAPT>) * (kANT / 32);
   auto kern = k_leg_adj_ck_df<NM, kANT, kAPT>;
@@ -373,13 +341,13 @@ int legendre_synth_df(const Grid& g, int nmaps, const void* alm, void* F, cudaSt
   return CMBWS_OK;
 }
 
-int legendre_adj_df_ck(const Grid& g, int nm, const void* F, void* eo, double* out, cudaStream_t s) {
+int legendre_adj_df_ck(const Grid& g, int nm, const void* eo, double* out, cudaStream_t s) {
   CMBWS_TRY(grid_ensure_ck64(g));
-  const int64_t fs = (int64_t)g.nring * (g.lmax + 1);
+  const float2* e = (const float2*)eo;
   switch (nm) {
-    case 1: return launch_adj_ck_df<1>(g, F, fs, eo, out, s);
-    case 2: return launch_adj_ck_df<2>(g, F, fs, eo, out, s);
-    default: return launch_adj_ck_df<3>(g, F, fs, eo, out, s);
+    case 1: return launch_adj_ck_df<1>(g, e, out, s);
+    case 2: return launch_adj_ck_df<2>(g, e, out, s);
+    default: return launch_adj_ck_df<3>(g, e, out, s);
   }
 }
 

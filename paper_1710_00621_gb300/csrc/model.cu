@@ -429,7 +429,7 @@ int Model::group_chain(Group& G, int prec, int which, cudaStream_t s) {
                         : (!is_f32(prec) ? pixM64[nu].p : pixM32[nu].p);
   }
   CMBWS_TRY(legendre_synth(g, prec, G.nmaps, G.alm.p, G.F.p, s));
-  CMBWS_TRY(ringfft_fused(g, prec, G.nmaps, G.F.p, pix, s));
+  CMBWS_TRY(ringfft_fused(g, prec, G.nmaps, G.F.p, pix, part.p, s));
   CMBWS_TRY(legendre_adjoint(g, prec, G.nmaps, G.F.p, part.p, part.bytes, G.out.as<double>(), s));
   return CMBWS_OK;
 }
@@ -473,7 +473,7 @@ int Model::mix_chain(Group& G, int prec, cudaStream_t s) {
   const void* pix[kMaxMaps];
   for (int j = 0; j < G.nmaps; ++j) pix[j] = !is_f32(prec) ? pixQ64[G.bands[j]].p : pixQ32[G.bands[j]].p;
   CMBWS_TRY(legendre_synth(g, prec, G.nmaps, G.alm.p, G.F.p, s));
-  CMBWS_TRY(ringfft_fused(g, prec, G.nmaps, G.F.p, pix, s));
+  CMBWS_TRY(ringfft_fused(g, prec, G.nmaps, G.F.p, pix, part.p, s));
   CMBWS_TRY(legendre_adjoint(g, prec, G.nmaps, G.F.p, part.p, part.bytes, G.out.as<double>(), s));
   return CMBWS_OK;
 }
@@ -608,7 +608,7 @@ int Model::apply_precond_merged(const double* r, double* z, int prec, cudaStream
     for (int j = 0; j < G.nmaps; ++j)
       pix[j] = !is_f32(prec) ? P.pixM64[G.bands[j]].p : P.pixM32[G.bands[j]].p;
     CMBWS_TRY(legendre_synth(g, prec, G.nmaps, G.alm.p, G.F.p, s));
-    CMBWS_TRY(ringfft_fused(g, prec, G.nmaps, G.F.p, pix, s));
+    CMBWS_TRY(ringfft_fused(g, prec, G.nmaps, G.F.p, pix, part.p, s));
     CMBWS_TRY(legendre_adjoint(g, prec, G.nmaps, G.F.p, part.p, part.bytes, G.out.as<double>(), s));
   }
   {
@@ -662,7 +662,7 @@ int Model::rhs(const double* const* d, const double* const* w1, const double* w2
           pixtmp.as<double>() + j * n, n);
       CMBWS_LAUNCH_CHECK();
     }
-    CMBWS_TRY(ringfft_analysis(g, ap, G.nmaps, pixtmp.as<double>(), 0, G.F.p, s));
+    CMBWS_TRY(ringfft_analysis(g, ap, G.nmaps, pixtmp.as<double>(), 0, G.F.p, part.p, s));
     CMBWS_TRY(legendre_adjoint(g, ap, G.nmaps, G.F.p, part.p, part.bytes, G.out.as<double>(), s));
   }
   // transposed variable mixing of B u_nu, then the epilogue without a prior term (x = NULL)

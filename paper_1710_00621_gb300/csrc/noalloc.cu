@@ -107,7 +107,7 @@ extern "C" int cmbws_sht_analysis_noalloc(cmbws_grid gh, cmbws_prec prec, const 
   void* part = p + fb;
   double* out = reinterpret_cast<double*>(p + fb + pb);
   cudaStream_t s = (cudaStream_t)stream;
-  CMBWS_TRY(ringfft_analysis(*g, prec, nmaps, map, weighted, F, s));
+  CMBWS_TRY(ringfft_analysis(*g, prec, nmaps, map, weighted, F, part, s));
   CMBWS_TRY(legendre_adjoint(*g, prec, nmaps, F, part, pb, out, s));
   CMBWS_TRY(unpack_alm(*g, nmaps, out, alm, s));
   return CMBWS_OK;

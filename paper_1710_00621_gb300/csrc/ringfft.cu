@@ -306,13 +306,16 @@ k_ringfft(typename V2<T>::t* __restrict__ F, int64_t F_stride, double* __restric
           const FftPlan* __restrict__ plans, const int* __restrict__ pair_plan,
           const int2* __restrict__ pring, const int* __restrict__ pphase,
           const int64_t* __restrict__ roff, const typename V2<T>::t* __restrict__ tab,
-          int64_t tw_off, int nmax, int L) {
+          int64_t tw_off, int nmax, int L, T* __restrict__ eo, int eo_nm, int k0, int nmaps,
+          int npair) {
   using T2 = typename V2<T>::t;
   using TP = typename PixT<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
 
-  const int p = blockIdx.x;
-  const int k = blockIdx.y;
+  // maps vary fastest across the grid, so the CTAs that fill the adjoint input of one ring
+  // pair (interleaved per m) run together
+  const int k = blockIdx.x;
+  const int p = blockIdx.y;
   const FftPlan P = plans[pair_plan[p]];
   const int lg = 31 - __clz(P.n2);
   const Sbuf<T2> buf{reinterpret_cast<T2*>(smem_raw), lg >= 8 ? lg - 4 : 31};
@@ -530,18 +533,35 @@ k_ringfft(typename V2<T>::t* __restrict__ F, int64_t F_stride, double* __restric
     const T cm = m == 0 ? T(1) : sq2;
     // G = (c - i s) X
     T gx = c * xnx + s * xny, gy = c * xny - s * xnx;
-    T2 o;
-    o.x = cm * gx;
-    o.y = -cm * gy;
-    if (m == 0) o.y = 0;
-    FN[m] = o;
+    T2 on, os;
+    on.x = cm * gx;
+    on.y = -cm * gy;
+    if (m == 0) on.y = 0;
     if (has_s) {
       gx = c * xsx + s * xsy;
       gy = c * xsy - s * xsx;
-      o.x = cm * gx;
-      o.y = m == 0 ? T(0) : -cm * gy;
-      FS[m] = o;
+      os.x = cm * gx;
+      os.y = m == 0 ? T(0) : -cm * gy;
     }
+    if (!eo) {
+      FN[m] = on;
+      if (has_s) FS[m] = os;
+      continue;
+    }
+    // the adjoint input: even-l part north + south, odd-l part north - south (a ring pair
+    // without a south ring counts its north ring in both)
+    T2 ev = on, od = on;
+    if (has_s) {
+      ev.x = on.x + os.x;
+      ev.y = on.y + os.y;
+      od.x = on.x - os.x;
+      od.y = on.y - os.y;
+    }
+    const int kg = k0 + k, ch = kg / eo_nm, j = kg - ch * eo_nm;
+    const int nmc = min(eo_nm, nmaps - ch * eo_nm), P = 2 * nmc;
+    T* e = eo + (int64_t)ch * eo_nm * (L + 1) * npair * 4 + ((int64_t)m * npair + p) * 2 * P;
+    *reinterpret_cast<T2*>(e + 2 * j) = ev;
+    *reinterpret_cast<T2*>(e + P + 2 * j) = od;
   }
 }
 
@@ -556,11 +576,11 @@ size_t smem_bytes(const Grid& g) {
 // ring have twice the warps to hide shared-memory latency with the same buffer per CTA.
 template <typename T, int MODE>
 int launch(const Grid& g, int nmaps, void* F, double* map_out, const double* map_in, int weighted,
-           const void* const* pix, cudaStream_t s);
+           const void* const* pix, void* eo, int eo_nm, cudaStream_t s);
 
 template <typename T, int MODE, int NT>
 int launch_nt(const Grid& g, int nmaps, void* F, double* map_out, const double* map_in,
-              int weighted, const void* const* pix, cudaStream_t s) {
+              int weighted, const void* const* pix, void* eo, int eo_nm, cudaStream_t s) {
   using T2 = typename V2<T>::t;
   const size_t sm = smem_bytes<T>(g);
   if (sm > 227 * 1024) {
@@ -581,7 +601,7 @@ int launch_nt(const Grid& g, int nmaps, void* F, double* map_out, const double* 
     PixPtrs<TP> pp{};
     if (MODE == MODE_FUSED)
       for (int i = 0; i < nm; ++i) pp.p[i] = (const TP*)pix[k0 + i];
-    dim3 grd(g.npair, nm);
+    dim3 grd(nm, g.npair);
     // algorithmic bytes: ring spectra read and/or written once, pixel factors (fused) or the
     // FP64 maps (synthesis output, analysis input) once
     const double fb = (double)g.nring * (g.lmax + 1) * sizeof(T2);
@@ -592,7 +612,7 @@ int launch_nt(const Grid& g, int nmaps, void* F, double* map_out, const double* 
                               map_in ? map_in + k0 * g.npix : nullptr, g.npix, rw, pp,
                               g.plans_d.as<FftPlan>(), g.pair_plan.as<int>(),
                               g.pair_ring.as<int2>(), g.pair_phase.as<int>(), g.ring_off.as<int64_t>(),
-                              tab, g.tw_off, g.nmax2, g.lmax);
+                              tab, g.tw_off, g.nmax2, g.lmax, (T*)eo, eo_nm, k0, nmaps, g.npair);
     CMBWS_LAUNCH_CHECK();
   }
   return CMBWS_OK;
@@ -600,10 +620,10 @@ int launch_nt(const Grid& g, int nmaps, void* F, double* map_out, const double* 
 
 template <typename T, int MODE>
 int launch(const Grid& g, int nmaps, void* F, double* map_out, const double* map_in, int weighted,
-           const void* const* pix, cudaStream_t s) {
+           const void* const* pix, void* eo, int eo_nm, cudaStream_t s) {
   if (g.nmax2 >= 4096)
-    return launch_nt<T, MODE, 256>(g, nmaps, F, map_out, map_in, weighted, pix, s);
-  return launch_nt<T, MODE, 128>(g, nmaps, F, map_out, map_in, weighted, pix, s);
+    return launch_nt<T, MODE, 256>(g, nmaps, F, map_out, map_in, weighted, pix, eo, eo_nm, s);
+  return launch_nt<T, MODE, 128>(g, nmaps, F, map_out, map_in, weighted, pix, eo, eo_nm, s);
 }
 
 }  // namespace
@@ -617,25 +637,31 @@ int ringfft_smem_ok(const Grid& g, int prec) {
 // Pixel factors: float (FP32 modes) or double.
 int ringfft_synth(const Grid& g, int prec, int nmaps, const void* F, double* map, cudaStream_t s) {
   void* f = const_cast<void*>(F);
-  if (prec == CMBWS_FP32X2) return launch<df, MODE_SYNTH>(g, nmaps, f, map, nullptr, 0, nullptr, s);
-  if (!is_f32(prec)) return launch<double, MODE_SYNTH>(g, nmaps, f, map, nullptr, 0, nullptr, s);
-  return launch<float, MODE_SYNTH>(g, nmaps, f, map, nullptr, 0, nullptr, s);
+  if (prec == CMBWS_FP32X2)
+    return launch<df, MODE_SYNTH>(g, nmaps, f, map, nullptr, 0, nullptr, nullptr, 0, s);
+  if (!is_f32(prec))
+    return launch<double, MODE_SYNTH>(g, nmaps, f, map, nullptr, 0, nullptr, nullptr, 0, s);
+  return launch<float, MODE_SYNTH>(g, nmaps, f, map, nullptr, 0, nullptr, nullptr, 0, s);
 }
 
 int ringfft_analysis(const Grid& g, int prec, int nmaps, const double* map, int weighted, void* F,
-                     cudaStream_t s) {
+                     void* eo, cudaStream_t s) {
   if (prec == CMBWS_FP32X2)
-    return launch<df, MODE_ANALYSIS>(g, nmaps, F, nullptr, map, weighted, nullptr, s);
+    return launch<df, MODE_ANALYSIS>(g, nmaps, F, nullptr, map, weighted, nullptr, eo,
+                                     eo_maps(prec), s);
   if (!is_f32(prec))
-    return launch<double, MODE_ANALYSIS>(g, nmaps, F, nullptr, map, weighted, nullptr, s);
-  return launch<float, MODE_ANALYSIS>(g, nmaps, F, nullptr, map, weighted, nullptr, s);
+    return launch<double, MODE_ANALYSIS>(g, nmaps, F, nullptr, map, weighted, nullptr, nullptr, 0, s);
+  return launch<float, MODE_ANALYSIS>(g, nmaps, F, nullptr, map, weighted, nullptr, eo,
+                                      eo_maps(prec), s);
 }
 
-int ringfft_fused(const Grid& g, int prec, int nmaps, void* F, const void* const* pix,
+int ringfft_fused(const Grid& g, int prec, int nmaps, void* F, const void* const* pix, void* eo,
                   cudaStream_t s) {
-  if (prec == CMBWS_FP32X2) return launch<df, MODE_FUSED>(g, nmaps, F, nullptr, nullptr, 0, pix, s);
-  if (!is_f32(prec)) return launch<double, MODE_FUSED>(g, nmaps, F, nullptr, nullptr, 0, pix, s);
-  return launch<float, MODE_FUSED>(g, nmaps, F, nullptr, nullptr, 0, pix, s);
+  if (prec == CMBWS_FP32X2)
+    return launch<df, MODE_FUSED>(g, nmaps, F, nullptr, nullptr, 0, pix, eo, eo_maps(prec), s);
+  if (!is_f32(prec))
+    return launch<double, MODE_FUSED>(g, nmaps, F, nullptr, nullptr, 0, pix, nullptr, 0, s);
+  return launch<float, MODE_FUSED>(g, nmaps, F, nullptr, nullptr, 0, pix, eo, eo_maps(prec), s);
 }
 
 }  // namespace cmbws
