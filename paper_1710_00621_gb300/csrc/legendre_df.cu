@@ -28,7 +28,9 @@ __global__ void __launch_bounds__(NT)
 k_leg_synth_df(const double2* __restrict__ alm, int64_t alm_stride, const float2* __restrict__ Acoef,
                const int* __restrict__ ls_tab, const double2* __restrict__ st,
                const double* __restrict__ yr, const int2* __restrict__ pring,
-               df2* __restrict__ F, int64_t F_stride, int L, int npair) {
+               df2* __restrict__ F, int64_t F_stride, int L, int npair,
+               const float4* __restrict__ ck, const int64_t* __restrict__ ck_base) {
+  static_assert(R == 1, "one ring pair per thread (its checkpoint column)");
   __shared__ __align__(16) float2 sA[CH];
   __shared__ __align__(16) float4 sa[NM][CH];
   __shared__ int s_lo;
@@ -68,6 +70,16 @@ k_leg_synth_df(const double2* __restrict__ alm, int64_t alm_stride, const float2
   const int lo = s_lo;
   int nxt = mylo;
   const int wlo = __reduce_min_sync(0xffffffffu, mylo);  // first start of this warp's pairs
+  // Checkpoints of the double-float adjoint: the FP64-computed pair (mu_l0, mu_l0+1) at every
+  // l0 = m + kChunkDf c (zero before the pair's start).  At those l the recurrence values are
+  // read instead of computed, so the recurrence runs for half of the steps; the column of the
+  // next chunk is loaded one chunk ahead.
+  const int nckd = (L - m + kChunkDf) / kChunkDf;
+  const float4* ckc = (pbase < npair) ? ck + ck_base[m] + (int64_t)pbase * nckd : nullptr;
+  static_assert(kChunkDf == 4, "one checkpoint every second step of two");
+  float4 pre = make_float4(0.f, 0.f, 0.f, 0.f);
+  int pre_l = -1;
+  bool pre_ok = false;
 
   for (int c0 = lo; c0 <= L; c0 += CH) {
     __syncthreads();
@@ -92,10 +104,21 @@ k_leg_synth_df(const double2* __restrict__ alm, int64_t alm_stride, const float2
       const float2 a0 = sA[j], a1 = sA[j + 1];
       const df A0 = {a0.x, a0.y}, A1 = {a1.x, a1.y};
       df ma[R], mb[R];
+      if (((l - m) & 3) == 0 && ckc) {  // a checkpoint at l (uniform but for the last pairs)
+        const float4 cv = pre_ok && pre_l == l ? pre : ckc[(l - m) >> 2];
+        ma[0] = {cv.x, cv.y};
+        mb[0] = {cv.z, cv.w};
+      } else {
+        if (ckc && l + 2 <= L) {  // the next checkpoint, read while this step computes
+          pre = ckc[(l + 2 - m) >> 2];
+          pre_l = l + 2;
+          pre_ok = true;
+        }
 #pragma unroll
-      for (int i = 0; i < R; ++i) {
-        ma[i] = df_recur(A0, y[i], mu1[i], mu2[i]);
-        mb[i] = df_recur(A1, y[i], ma[i], mu1[i]);
+        for (int i = 0; i < R; ++i) {
+          ma[i] = df_recur(A0, y[i], mu1[i], mu2[i]);
+          mb[i] = df_recur(A1, y[i], ma[i], mu1[i]);
+        }
       }
       if (l == nxt) {
         int nn = INT_MAX;
@@ -296,7 +319,8 @@ int launch_synth_df(const Grid& g, const void* alm, int64_t as, void* F, int64_t
   ProfScope ps(PROF_LEG_SYNTH, s, 2, leg_work(g, NM));
   k_leg_synth_df<NM, kSR, kSNT, kSCH><<<grd, kSNT, 0, s>>>(
       (const double2*)alm, as, g.A2f.as<float2>(), g.ls.as<int>(), g.st64.as<double2>(),
-      g.y64.as<double>(), g.pair_ring.as<int2>(), (df2*)F, fs, L, g.npair);
+      g.y64.as<double>(), g.pair_ring.as<int2>(), (df2*)F, fs, L, g.npair, g.ck64.as<float4>(),
+      g.ck64_base.as<int64_t>());
   CMBWS_LAUNCH_CHECK();
   return CMBWS_OK;
 }
@@ -324,6 +348,7 @@ int launch_adj_ck_df(const Grid& g, const float2* eo, double* out, cudaStream_t 
 
 
 int legendre_synth_df(const Grid& g, int nmaps, const void* alm, void* F, cudaStream_t s) {
+  CMBWS_TRY(grid_ensure_ck64(g));
   const int64_t as = nlm_of(g.lmax), fs = (int64_t)g.nring * (g.lmax + 1);
   for (int k0 = 0; k0 < nmaps; k0 += 4) {
     const int nm = nmaps - k0 < 4 ? nmaps - k0 : 4;
