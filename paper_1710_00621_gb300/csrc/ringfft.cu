@@ -284,7 +284,8 @@ struct PixPtrs {
 };
 
 // NT threads per CTA; the register cap keeps three CTAs of 256 threads (six of 128) resident
-// per SM, which is what the transform buffer of the largest rings allows.
+// per SM in FP32 and double-float, which is what the transform buffer of the largest rings
+// allows.
 //
 // Each ring pair's DFTs, in terms of the plan (n pixels; Bluestein plans convolve over n2):
 // * power of two: the inverse DFT is a DIT transform whose input (the folded spectrum) is
@@ -298,8 +299,13 @@ struct PixPtrs {
 // In the fused mode the pixel multiply and the chirp of the next transform happen in the last
 // pass of the inverse; in the synthesis mode that pass writes the pixel maps, and in the
 // analysis mode the first pass of the forward DFT reads them.
+// FP64 gets twice the register budget (two CTAs of 256 threads): under the FP32 cap its
+// transform spilled.
+template <typename T>
+constexpr int fft_min_blocks(int nt) { return (std::is_same<T, double>::value ? 512 : 768) / nt; }
+
 template <typename T, int MODE, int NT>
-__global__ void __launch_bounds__(NT, 768 / NT)
+__global__ void __launch_bounds__(NT, fft_min_blocks<T>(NT))
 k_ringfft(typename V2<T>::t* __restrict__ F, int64_t F_stride, double* __restrict__ map_out,
           const double* __restrict__ map_in, int64_t npix,
           const typename PixT<T>::t* __restrict__ ring_w, PixPtrs<typename PixT<T>::t> pix,
