@@ -598,7 +598,8 @@ def precision_report(nside=1024, nmaps=3, reps=3):
     out = {}
     ref = None
     precs = [("fp64", cw.CMBWS_FP64), ("fp32x2", cw.CMBWS_FP32X2), ("fp32", cw.CMBWS_FP32),
-             ("3xtf32", cw.CMBWS_3XTF32), ("tf32", cw.CMBWS_TF32)]
+             ("3xtf32", cw.CMBWS_3XTF32), ("tf32", cw.CMBWS_TF32), ("bf16x3", cw.CMBWS_BF16X3),
+             ("bf16", cw.CMBWS_BF16)]
     for name, p in precs:
         m = torch.empty((nmaps, g.npix), dtype=torch.float64, device="cuda")
         cw.cmbws_sht_synth(g, p, a, m, nmaps)  # warm-up (lazy tables)
@@ -614,8 +615,9 @@ def precision_report(nside=1024, nmaps=3, reps=3):
         err = float((m - ref).abs().max() / ref.abs().max())
         out[name] = {"ms": round(e0.elapsed_time(e1) / reps, 3), "max_rel_err_vs_fp64": err}
     out["case"] = f"synthesis, HEALPix Nside {nside}, L = {L}, {nmaps} maps, 1/(l+1) spectrum"
-    out["note"] = ("tf32 / 3xtf32: Legendre contraction on the tcgen05 tensor cores (the recurrence "
-                   "on the CUDA cores in FP32, as for fp32); fp32x2: double-float on the FP32 pipe")
+    out["note"] = ("tf32 / 3xtf32 / bf16 / bf16x3: Legendre contraction on the tcgen05 tensor cores "
+                   "(the recurrence on the CUDA cores in FP32, as for fp32); fp32x2: double-float on "
+                   "the FP32 pipe")
     return out
 
 
@@ -921,6 +923,51 @@ def main():
         except Exception as e:  # noqa: BLE001
             fp32x2 = {"error": f"{type(e).__name__}: {e}"[:300]}
 
+    # the step's solve with the Legendre synthesis on the tensor cores (TF32 / BF16, single or
+    # split), refined and certified like the FP32 solve
+    tc_solves = None
+    if not args.no_extras and args.prec == "fp32":
+        tc_solves = {}
+        inp = P["inp"]
+        for name, pc in (("tf32", cw.CMBWS_TF32), ("3xtf32", cw.CMBWS_3XTF32),
+                         ("bf16x3", cw.CMBWS_BF16X3), ("bf16", cw.CMBWS_BF16)):
+            try:
+                mt = cw.cmbws_model_create([c.lmax for c in work.comps], P["grids"], inp["beams"],
+                                           inp["cl"], P["ninv"], inp["q"], pc)
+                xt = torch.zeros(n, dtype=torch.float64, device=dev)
+                for _ in range(2):                  # the first solve allocates the workspaces
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    rt = solve_step(P, mt, args.tol, xt, b, cert)
+                    torch.cuda.synchronize()
+                    tt = time.perf_counter() - t0
+                tc_solves[name] = {"s": round(tt, 4), "iters": rt["iters"], "outer": rt["outer"],
+                                   "certified": rt["status"] == 0 and rt["rel_res"] <= args.tol,
+                                   "rel_diff_vs_fp32_solution": float(torch.linalg.vector_norm(xt - x)
+                                                                      / torch.linalg.vector_norm(x))}
+                mt.close()
+            except Exception as e:  # noqa: BLE001
+                tc_solves[name] = {"error": f"{type(e).__name__}: {e}"[:300]}
+        # FP32 A with the preconditioner's synthesis on the tensor cores
+        for name, pc in (("fp32_A_bf16_precond", cw.CMBWS_BF16), ("fp32_A_tf32_precond", cw.CMBWS_TF32)):
+            try:
+                cw.cmbws_model_set_precond_prec(model, pc)
+                xt = torch.zeros(n, dtype=torch.float64, device=dev)
+                for _ in range(2):
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    rt = solve_step(P, model, args.tol, xt, b, cert)
+                    torch.cuda.synchronize()
+                    tt = time.perf_counter() - t0
+                tc_solves[name] = {"s": round(tt, 4), "iters": rt["iters"], "outer": rt["outer"],
+                                   "certified": rt["status"] == 0 and rt["rel_res"] <= args.tol,
+                                   "rel_diff_vs_fp32_solution": float(torch.linalg.vector_norm(xt - x)
+                                                                      / torch.linalg.vector_norm(x))}
+            except Exception as e:  # noqa: BLE001
+                tc_solves[name] = {"error": f"{type(e).__name__}: {e}"[:300]}
+            finally:
+                cw.cmbws_model_set_precond_prec(model, -1)
+
     # the paper's comparison (Sec. 5): the same solve with the block-diagonal preconditioner
     mdiag = None
     if not args.no_extras:
@@ -1000,7 +1047,8 @@ def main():
                        "l2": "inputs larger than L2, no flush",
                        "synthesis_tiles": ["default", "heuristic", "autotuned"][args.autotune],
                        "parallelism": f"replicas x{world}"},
-            "solve": out, "fp64_plain": fp64, "fp32x2_plain": fp32x2, "batched": batched,
+            "solve": out, "fp64_plain": fp64, "fp32x2_plain": fp32x2,
+            "tensor_core_solves": tc_solves, "batched": batched,
             "masked_cr": masked_cr,
             "tiny": extras.get("tiny"), "differentiable": extras.get("differentiable"),
             "M_diag_comparison": mdiag,

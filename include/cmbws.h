@@ -71,13 +71,20 @@ typedef enum { CMBWS_GRID_GL = 0, CMBWS_GRID_HEALPIX = 1 } cmbws_grid_kind;
  *                 TF32 recurrence values and coefficients, FP32 accumulation; relative error
  *                 ~1e-4); the adjoint Legendre stage stays FP32 on the CUDA cores.
  *   CMBWS_3XTF32: as CMBWS_TF32 with split-TF32 products (hi/lo parts, three MMAs per
- *                 step), FP32-level accuracy. */
+ *                 step), FP32-level accuracy.
+ *   CMBWS_BF16:   as CMBWS_TF32 with BF16 recurrence values and coefficients (tcgen05
+ *                 kind::f16, FP32 accumulation; 8 significant bits per factor, relative
+ *                 error ~1e-3).
+ *   CMBWS_BF16X3: as CMBWS_BF16 with split-BF16 products (hi/lo parts, three MMAs per
+ *                 step; about 16 significant bits per factor). */
 typedef enum {
   CMBWS_FP64 = 0,
   CMBWS_FP32 = 1,
   CMBWS_FP32X2 = 2,
   CMBWS_TF32 = 3,
-  CMBWS_3XTF32 = 4
+  CMBWS_3XTF32 = 4,
+  CMBWS_BF16 = 5,
+  CMBWS_BF16X3 = 6
 } cmbws_prec;
 
 typedef struct cmbws_grid_s* cmbws_grid;    /* opaque, library-owned */
@@ -341,9 +348,10 @@ int cmbws_grid_tuning(cmbws_grid g, int prec, int nmaps, int* variant, float* ms
  * CUDA events on the launching stream.  Records are kept per slot = stage + 6 * arith,
  * stages 0 Legendre synthesis, 1 Legendre adjoint, 2 adjoint partial-sum reduction,
  * 3 ring FFT, 4 harmonic-space kernels, 5 CG vector kernels; arith 0 = FP32, 1 = FP64,
- * 2 = double-float (CMBWS_FP32X2), 3 = TF32 tensor cores, 4 = split TF32 tensor cores.
+ * 2 = double-float (CMBWS_FP32X2), 3 = TF32 tensor cores, 4 = split TF32 tensor cores,
+ * 5 = BF16 tensor cores, 6 = split BF16 tensor cores.
  * cmbws_profile_read synchronises the recorded events and writes, per slot (host arrays
- * of 30, any may be NULL), since the last reset:
+ * of 42, any may be NULL), since the last reset:
  *   ms: summed milliseconds; launches: launch count;
  *   flops: summed algorithmic flops (Legendre stages: 4 per (l, m, ring pair) for the
  *     recurrence plus 4 per map for the contraction, over the full (l, m) triangle);
@@ -391,6 +399,15 @@ typedef struct {
  */
 int cmbws_cg_solve(cmbws_model m, const double* b, double* x, const cmbws_cg_opts* opts,
                    cmbws_cg_report* report, void* stream);
+
+/*
+ * Arithmetic of the transforms of M_PI inside the solvers (cmbws_cg_solve and the solves
+ * built on it): any cmbws_prec, or -1 (default) for the model's own.  The preconditioner only
+ * has to approximate A^-1, so its transforms can run in a cheaper precision than those of A,
+ * e.g. the BF16 tensor-core synthesis in the FP32 inner solves; cmbws_apply_precond keeps the
+ * model's precision.  Errors: CMBWS_ERR_ARG.
+ */
+int cmbws_model_set_precond_prec(cmbws_model m, int prec);
 
 /*
  * Per-iteration record of the model's last solve (cmbws_cg_solve, cmbws_cg_resume, or one

@@ -21,6 +21,8 @@ CMBWS_FP32 = 1
 CMBWS_FP32X2 = 2
 CMBWS_TF32 = 3
 CMBWS_3XTF32 = 4
+CMBWS_BF16 = 5
+CMBWS_BF16X3 = 6
 
 _ERRORS = {-1: "CMBWS_ERR_ARG", -2: "CMBWS_ERR_CUDA", -3: "CMBWS_ERR_NOMEM",
            -4: "CMBWS_ERR_SINGULAR", -5: "CMBWS_ERR_BREAKDOWN", -6: "CMBWS_ERR_NOT_CONVERGED",
@@ -117,6 +119,7 @@ def load_library(path=None):
                                      ctypes.POINTER(i)]
     lib.cmbws_cg_track_error.argtypes = [vp, vp, vp]
     lib.cmbws_cg_checkpointing.argtypes = [vp, i]
+    lib.cmbws_model_set_precond_prec.argtypes = [vp, i]
     lib.cmbws_model_set_shard.argtypes = [vp, ctypes.POINTER(i), i]
     lib.cmbws_cg_solve_sharded.argtypes = [vp, vp, vp, ctypes.POINTER(CgOpts), vp, vp,
                                            ctypes.POINTER(CgReport), vp]
@@ -535,7 +538,7 @@ def cmbws_profile_enable(on=True):
     _check(load_library().cmbws_profile_enable(1 if on else 0))
 
 
-PROFILE_ARITH = ("fp32", "fp64", "fp32x2", "tf32", "3xtf32")
+PROFILE_ARITH = ("fp32", "fp64", "fp32x2", "tf32", "3xtf32", "bf16", "bf16x3")
 
 
 def cmbws_profile_read(reset=True):
@@ -567,6 +570,11 @@ def cmbws_cg_solve(model, b, x, tol=1e-6, maxiter=1000, precond=1, inner_tol=1e-
     out = rep.as_dict()
     out["code"] = code
     return out
+
+
+def cmbws_model_set_precond_prec(model, prec=-1):
+    """Arithmetic of M_PI's transforms inside the solvers (-1: the model's own)."""
+    _check(load_library().cmbws_model_set_precond_prec(model.handle, int(prec)))
 
 
 def cmbws_cg_history(model):

@@ -195,7 +195,7 @@ static int precondition(Model& M, int use_M, int prec, const double* r, double* 
     return CMBWS_OK;
   }
   if (use_M == 3) return M.apply_diag(r, z, s);
-  CMBWS_TRY(M.apply_precond(r, z, prec, s));
+  CMBWS_TRY(M.apply_precond(r, z, M.prec_M >= 0 ? M.prec_M : prec, s));
   if (use_M == 2)
     for (MaskMG* mg : M.masks) CMBWS_TRY(mask_mg_apply(*mg, M, r, z, s));
   return CMBWS_OK;
@@ -316,7 +316,7 @@ static int pcg_core(Solver& S, int prec, int use_M, double* d, double* r, double
       CMBWS_TRY(precondition(M, use_M, prec, r, z, n, S.s));
       return S.reduce(z);
     }
-    return run_op(M, OP_PRECOND + 16 * use_M, prec, r, z, S.s,
+    return run_op(M, OP_PRECOND + 16 * use_M, M.prec_M >= 0 ? M.prec_M : prec, r, z, S.s,
                   [&]() { return precondition(M, use_M, prec, r, z, n, S.s); });
   };
   double rr, rz;
@@ -777,4 +777,16 @@ extern "C" int cmbws_cg_solve_sharded(cmbws_model mh, const double* b, double* x
   rep.status = st;
   if (report) *report = rep;
   return st;
+}
+
+extern "C" int cmbws_model_set_precond_prec(cmbws_model mh, int prec) {
+  clear_error();
+  Model* M = as_model(mh);
+  if (!M || (prec != -1 && !valid_prec(prec))) {
+    set_error("cmbws_model_set_precond_prec: invalid arguments");
+    return CMBWS_ERR_ARG;
+  }
+  M->prec_M = prec;
+  M->drop_graphs();
+  return CMBWS_OK;
 }

@@ -241,10 +241,10 @@ int unpack_alm(const Grid& g, int nmaps, const double* lmc, double* packed, cuda
 
 // FP32 transforms use float buffers; FP64 and FP32X2 use the FP64 layouts.
 // FP32 buffers and CUDA-core FP32 stages (the TF32 modes differ in the Legendre synthesis only)
-inline bool is_f32(int prec) {
-  return prec == CMBWS_FP32 || prec == CMBWS_TF32 || prec == CMBWS_3XTF32;
+inline bool is_tc(int prec) {
+  return prec == CMBWS_TF32 || prec == CMBWS_3XTF32 || prec == CMBWS_BF16 || prec == CMBWS_BF16X3;
 }
-inline bool is_tc(int prec) { return prec == CMBWS_TF32 || prec == CMBWS_3XTF32; }
+inline bool is_f32(int prec) { return prec == CMBWS_FP32 || is_tc(prec); }
 inline size_t prec_size(int prec) { return is_f32(prec) ? 4 : 8; }
 inline bool valid_prec(int prec) {
   return prec == CMBWS_FP64 || prec == CMBWS_FP32 || prec == CMBWS_FP32X2 || is_tc(prec);
@@ -252,7 +252,7 @@ inline bool valid_prec(int prec) {
 
 // ---- double-float Legendre stage (legendre_df.cu) ----
 int legendre_synth_df(const Grid& g, int nmaps, const void* alm, void* F, cudaStream_t s);
-// ---- tensor-core Legendre synthesis (legendre_tc.cu), prec CMBWS_TF32 / CMBWS_3XTF32 ----
+// ---- tensor-core Legendre synthesis (legendre_tc.cu), prec TF32 / 3XTF32 / BF16 / BF16X3 ----
 int legendre_synth_tc(const Grid& g, int prec, int nmaps, const void* alm, void* F, cudaStream_t s);
 // reads and clears the device-side status of the tensor-core kernels of the current device
 // (synchronous): *timed_out is true if a bounded mbarrier wait ran out since the last read
@@ -279,7 +279,8 @@ int autotune_pick(const Grid& g, int key, int nvar, int heuristic,
 
 // ---- kernel timing (api.cu): CUDA events around launches while enabled ----
 // Stages; a record's slot is stage + PROF_N * arith, arith 0 = FP32, 1 = FP64,
-// 2 = double-float (FP32X2), 3 = TF32 tensor cores, 4 = split TF32 (PROF_ARITH kinds).
+// 2 = double-float (FP32X2), 3 = TF32 tensor cores, 4 = split TF32, 5 = BF16 tensor cores,
+// 6 = split BF16 (PROF_ARITH kinds).
 // Each launch records its algorithmic work (ProfWork): Legendre stages their flops over the
 // full (l, m) triangle (4 per (l, m, ring pair) for the recurrence plus 4 per map), the
 // elements (l, m, ring pair) and elements x maps; ring FFTs the bytes they must move (ring
@@ -292,7 +293,7 @@ enum {
   PROF_HARM = 4,
   PROF_CG = 5,
   PROF_N = 6,
-  PROF_ARITH = 5
+  PROF_ARITH = 7
 };
 struct ProfWork {
   double flops = 0, elems = 0, melems = 0, bytes = 0;

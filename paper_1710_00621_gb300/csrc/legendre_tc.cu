@@ -17,7 +17,10 @@
 //   one thread issues the MMAs (M = 128, N = 16, K = 8) and commits them to the stage's
 //   mbarrier, which the threads wait on (bounded) before overwriting the stage;
 // * SPLIT = 1 keeps FP32-level accuracy with the split-TF32 product
-//   A_hi B_hi + A_hi B_lo + A_lo B_hi (x = hi + lo, hi = tf32(x), lo = tf32(x - hi)).
+//   A_hi B_hi + A_hi B_lo + A_lo B_hi (x = hi + lo, hi = tf32(x), lo = tf32(x - hi));
+// * BF = 1 takes BF16 operands instead (kind::f16, K = 16 per MMA, two values of l packed per
+//   tensor-memory column, 8 significant bits per factor); with SPLIT the same hi / lo
+//   product in BF16 (about 16 significant bits).
 #include <climits>
 
 #include "common.h"
@@ -58,6 +61,28 @@ __device__ __forceinline__ void mma_tf32(uint32_t d, uint32_t a, uint64_t bdesc,
       "r"(a), "l"(bdesc), "r"(kIdesc), "r"(acc));
 }
 
+// Instruction descriptor of kind::f16 with both operands BF16: D FP32, A and B BF16 (both the
+// same 16-bit type), both K-major, N = 16, M = 128.
+constexpr uint32_t kIdescBf16 =
+    (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint32_t a, uint64_t bdesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(d),
+      "r"(a), "l"(bdesc), "r"(kIdescBf16), "r"(acc));
+}
+
+// Two FP32 values rounded to BF16 (nearest even) and packed: lo in bits 0-15, hi in 16-31.
+__device__ __forceinline__ uint32_t bf16x2_rn(float lo, float hi) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;\n" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+// the FP32 values of the two BF16 halves of a packed word
+__device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
+
 // Device-side status of this file's kernels (one word per device): bit 0 is set when a
 // bounded mbarrier wait ran out; cmbws_device_status reads and clears it.
 __device__ unsigned int g_tc_status = 0;
@@ -97,6 +122,14 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32
       "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31]));
 }
 
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15,%16};\n" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]),
+      "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]));
+}
+
 template <int SPLIT>
 struct TcLayout {
   static constexpr int kBStage = 4 * 512;                         // one 16 x 32 TF32 tile
@@ -112,12 +145,20 @@ struct TcLayout {
   static constexpr uint32_t kColA = 0, kColAlo = 64, kColD = SPLIT ? 128 : 64;
 };
 
-// Byte offset of B[n][k] (n < 16 output column, k < 32 within the block) in a stage tile.
+// Byte offset of B[n][k] (n < 16 output column, k < 32 within the block) in a stage tile:
+// core matrices of 8 rows x 16 bytes (4 TF32 or 8 BF16 values of k), two along K per MMA
+// (LBO 128 bytes), two along N (SBO 256 bytes), one 512-byte slice per MMA (K = 8 for TF32,
+// K = 16 for BF16).
 __device__ __forceinline__ int b_off(int n, int k) {
   return (k >> 3) * 512 + (n >> 3) * 256 + ((k >> 2) & 1) * 128 + (n & 7) * 16 + (k & 3) * 4;
 }
+__device__ __forceinline__ int b_off16(int n, int k) {
+  return (k >> 4) * 512 + (n >> 3) * 256 + ((k >> 3) & 1) * 128 + (n & 7) * 16 + (k & 7) * 2;
+}
 
-template <int NM, int SPLIT>
+// BF = 1: BF16 operands (kind::f16, K = 16 per MMA, two values of l per tensor-memory column)
+// instead of TF32 (kind::tf32, K = 8).
+template <int NM, int SPLIT, int BF>
 __global__ void __launch_bounds__(kTcNT)
 k_leg_synth_tc(const float2* __restrict__ alm, int64_t alm_stride, const float* __restrict__ Acoef,
                const float* __restrict__ brs, const int* __restrict__ ls_tab,
@@ -219,14 +260,25 @@ k_leg_synth_tc(const float2* __restrict__ alm, int64_t alm_stride, const float* 
     {
       unsigned char* bs = sm + s * LY::kStage;
       if (jj < NM) {
-        const uint32_t hr = tf32_rna(cnext.x), hi = tf32_rna(cnext.y);
-        *reinterpret_cast<uint32_t*>(bs + b_off(n_re, kk)) = hr;
-        *reinterpret_cast<uint32_t*>(bs + b_off(n_re + 1, kk)) = hi;
-        if constexpr (SPLIT) {
-          *reinterpret_cast<uint32_t*>(bs + LY::kBStage + b_off(n_re, kk)) =
-              tf32_bits(cnext.x - __uint_as_float(hr));
-          *reinterpret_cast<uint32_t*>(bs + LY::kBStage + b_off(n_re + 1, kk)) =
-              tf32_bits(cnext.y - __uint_as_float(hi));
+        if constexpr (BF) {
+          const uint32_t w = bf16x2_rn(cnext.x, cnext.y);
+          *reinterpret_cast<uint16_t*>(bs + b_off16(n_re, kk)) = (uint16_t)(w & 0xFFFFu);
+          *reinterpret_cast<uint16_t*>(bs + b_off16(n_re + 1, kk)) = (uint16_t)(w >> 16);
+          if constexpr (SPLIT) {
+            const uint32_t wl = bf16x2_rn(cnext.x - bf16_lo(w), cnext.y - bf16_hi(w));
+            *reinterpret_cast<uint16_t*>(bs + LY::kBStage + b_off16(n_re, kk)) = (uint16_t)(wl & 0xFFFFu);
+            *reinterpret_cast<uint16_t*>(bs + LY::kBStage + b_off16(n_re + 1, kk)) = (uint16_t)(wl >> 16);
+          }
+        } else {
+          const uint32_t hr = tf32_rna(cnext.x), hi = tf32_rna(cnext.y);
+          *reinterpret_cast<uint32_t*>(bs + b_off(n_re, kk)) = hr;
+          *reinterpret_cast<uint32_t*>(bs + b_off(n_re + 1, kk)) = hi;
+          if constexpr (SPLIT) {
+            *reinterpret_cast<uint32_t*>(bs + LY::kBStage + b_off(n_re, kk)) =
+                tf32_bits(cnext.x - __uint_as_float(hr));
+            *reinterpret_cast<uint32_t*>(bs + LY::kBStage + b_off(n_re + 1, kk)) =
+                tf32_bits(cnext.y - __uint_as_float(hi));
+          }
         }
       }
       sAc[s * 4 * kTcKB + tid] = anext;
@@ -240,7 +292,8 @@ k_leg_synth_tc(const float2* __restrict__ alm, int64_t alm_stride, const float* 
     uint32_t vh[kTcKB];
     uint32_t vl[kTcKB];
     const int jinj = ls - (lo + b * kTcKB);  // start of this thread's pair within the block
-    // one step pair (l, l + 1) of the recurrence, TF32 parts written to vh / vl
+    // one step pair (l, l + 1) of the recurrence, TF32 parts written to vh / vl (BF16: the
+    // pair packed into word j / 2, l in the low half)
     auto step = [&](int j, float2 a2) {
       const float ma = fmaf(fmaf(-a2.x, y, a2.x), mu1, -mu2);
       const float mb = fmaf(fmaf(-a2.y, y, a2.y), ma, -mu1);
@@ -248,7 +301,11 @@ k_leg_synth_tc(const float2* __restrict__ alm, int64_t alm_stride, const float* 
       mu1 = mb;
     };
     auto emit2 = [&](int j, float ma, float mb) {
-      if constexpr (SPLIT) {
+      if constexpr (BF) {
+        const uint32_t w = bf16x2_rn(ma, mb);
+        vh[j >> 1] = w;
+        if constexpr (SPLIT) vl[j >> 1] = bf16x2_rn(ma - bf16_lo(w), mb - bf16_hi(w));
+      } else if constexpr (SPLIT) {
         vh[j] = tf32_rna(ma);
         vh[j + 1] = tf32_rna(mb);
         vl[j] = tf32_bits(ma - __uint_as_float(vh[j]));
@@ -302,8 +359,14 @@ k_leg_synth_tc(const float2* __restrict__ alm, int64_t alm_stride, const float* 
         emit(j + 2);
       }
     }
-    tmem_st32(tb + lane_base + LY::kColA + 32 * s, vh);
-    if constexpr (SPLIT) tmem_st32(tb + lane_base + LY::kColAlo + 32 * s, vl);
+    if constexpr (BF) {
+      tmem_st16(tb + lane_base + LY::kColA + 16 * s, *reinterpret_cast<const uint32_t(*)[16]>(vh));
+      if constexpr (SPLIT)
+        tmem_st16(tb + lane_base + LY::kColAlo + 16 * s, *reinterpret_cast<const uint32_t(*)[16]>(vl));
+    } else {
+      tmem_st32(tb + lane_base + LY::kColA + 32 * s, vh);
+      if constexpr (SPLIT) tmem_st32(tb + lane_base + LY::kColAlo + 32 * s, vl);
+    }
     asm volatile("tcgen05.wait::st.sync.aligned;\n" ::);
     asm volatile("fence.proxy.async.shared::cta;\n" ::);
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
@@ -312,15 +375,29 @@ k_leg_synth_tc(const float2* __restrict__ alm, int64_t alm_stride, const float* 
     if (tid == 0 && !*s_bad) {
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
       const uint32_t bh = smem_addr(sm + s * LY::kStage);
+      if constexpr (BF) {
 #pragma unroll
-      for (int i = 0; i < kTcKB / 8; ++i) {
-        const uint32_t a_hi = tb + LY::kColA + 32 * s + 8 * i;
-        const uint64_t dh = smem_desc(bh + 512 * i, 128, 256);
-        mma_tf32(tb + LY::kColD, a_hi, dh, (b > 0 || i > 0) ? 1u : 0u);
-        if constexpr (SPLIT) {
-          const uint64_t dl = smem_desc(bh + LY::kBStage + 512 * i, 128, 256);
-          mma_tf32(tb + LY::kColD, a_hi, dl, 1u);
-          mma_tf32(tb + LY::kColD, tb + LY::kColAlo + 32 * s + 8 * i, dh, 1u);
+        for (int i = 0; i < kTcKB / 16; ++i) {  // K = 16: 8 columns of packed pairs per MMA
+          const uint32_t a_hi = tb + LY::kColA + 16 * s + 8 * i;
+          const uint64_t dh = smem_desc(bh + 512 * i, 128, 256);
+          mma_bf16(tb + LY::kColD, a_hi, dh, (b > 0 || i > 0) ? 1u : 0u);
+          if constexpr (SPLIT) {
+            const uint64_t dl = smem_desc(bh + LY::kBStage + 512 * i, 128, 256);
+            mma_bf16(tb + LY::kColD, a_hi, dl, 1u);
+            mma_bf16(tb + LY::kColD, tb + LY::kColAlo + 16 * s + 8 * i, dh, 1u);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < kTcKB / 8; ++i) {
+          const uint32_t a_hi = tb + LY::kColA + 32 * s + 8 * i;
+          const uint64_t dh = smem_desc(bh + 512 * i, 128, 256);
+          mma_tf32(tb + LY::kColD, a_hi, dh, (b > 0 || i > 0) ? 1u : 0u);
+          if constexpr (SPLIT) {
+            const uint64_t dl = smem_desc(bh + LY::kBStage + 512 * i, 128, 256);
+            mma_tf32(tb + LY::kColD, a_hi, dl, 1u);
+            mma_tf32(tb + LY::kColD, tb + LY::kColAlo + 32 * s + 8 * i, dh, 1u);
+          }
         }
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
@@ -358,20 +435,32 @@ k_leg_synth_tc(const float2* __restrict__ alm, int64_t alm_stride, const float* 
   }
 }
 
-template <int NM, int SPLIT>
+template <int NM, int SPLIT, int BF>
 int launch_synth_tc(const Grid& g, const void* alm, int64_t as, void* F, int64_t fs, cudaStream_t s) {
   using LY = TcLayout<SPLIT>;
   const int L = g.lmax;
   dim3 grd((g.npair + kTcNT - 1) / kTcNT, L + 1);
-  auto kern = k_leg_synth_tc<NM, SPLIT>;
+  auto kern = k_leg_synth_tc<NM, SPLIT, BF>;
   CMBWS_TRY(ensure_dyn_smem((const void*)kern, LY::kSmem));
-  ProfScope ps(PROF_LEG_SYNTH, s, SPLIT ? 4 : 3, leg_work(g, NM));
+  // profiling arithmetic kinds: 3 TF32, 4 split TF32, 5 BF16, 6 split BF16
+  ProfScope ps(PROF_LEG_SYNTH, s, 3 + SPLIT + 2 * BF, leg_work(g, NM));
   kern<<<grd, kTcNT, LY::kSmem, s>>>((const float2*)alm, as, g.A32.as<float>(), g.BRS32.as<float>(),
                                      g.ls.as<int>(),
                                      g.st32.as<float2>(), g.y32.as<float>(), g.pair_ring.as<int2>(),
                                      (float2*)F, fs, L, g.npair);
   CMBWS_LAUNCH_CHECK();
   return CMBWS_OK;
+}
+
+template <int SPLIT, int BF>
+int launch_synth_tc_nm(int nm, const Grid& g, const void* a, int64_t as, void* f, int64_t fs,
+                       cudaStream_t s) {
+  switch (nm) {
+    case 1: return launch_synth_tc<1, SPLIT, BF>(g, a, as, f, fs, s);
+    case 2: return launch_synth_tc<2, SPLIT, BF>(g, a, as, f, fs, s);
+    case 3: return launch_synth_tc<3, SPLIT, BF>(g, a, as, f, fs, s);
+    default: return launch_synth_tc<4, SPLIT, BF>(g, a, as, f, fs, s);
+  }
 }
 
 static_assert(TcLayout<0>::kUsed <= TcLayout<0>::kSmem && TcLayout<1>::kUsed <= TcLayout<1>::kSmem,
@@ -381,21 +470,16 @@ static_assert(TcLayout<0>::kUsed <= TcLayout<0>::kSmem && TcLayout<1>::kUsed <= 
 
 int legendre_synth_tc(const Grid& g, int prec, int nmaps, const void* alm, void* F, cudaStream_t s) {
   const int64_t as = nlm_of(g.lmax), fs = (int64_t)g.nring * (g.lmax + 1);
-  const bool split = prec == CMBWS_3XTF32;
   for (int k0 = 0; k0 < nmaps; k0 += 4) {
     const int nm = nmaps - k0 < 4 ? nmaps - k0 : 4;
     const void* a = (const float2*)alm + k0 * as;
     void* f = (float2*)F + k0 * fs;
     int st;
-    switch (nm * 2 + (split ? 1 : 0)) {
-      case 2: st = launch_synth_tc<1, 0>(g, a, as, f, fs, s); break;
-      case 3: st = launch_synth_tc<1, 1>(g, a, as, f, fs, s); break;
-      case 4: st = launch_synth_tc<2, 0>(g, a, as, f, fs, s); break;
-      case 5: st = launch_synth_tc<2, 1>(g, a, as, f, fs, s); break;
-      case 6: st = launch_synth_tc<3, 0>(g, a, as, f, fs, s); break;
-      case 7: st = launch_synth_tc<3, 1>(g, a, as, f, fs, s); break;
-      case 8: st = launch_synth_tc<4, 0>(g, a, as, f, fs, s); break;
-      default: st = launch_synth_tc<4, 1>(g, a, as, f, fs, s); break;
+    switch (prec) {
+      case CMBWS_TF32: st = launch_synth_tc_nm<0, 0>(nm, g, a, as, f, fs, s); break;
+      case CMBWS_3XTF32: st = launch_synth_tc_nm<1, 0>(nm, g, a, as, f, fs, s); break;
+      case CMBWS_BF16: st = launch_synth_tc_nm<0, 1>(nm, g, a, as, f, fs, s); break;
+      default: st = launch_synth_tc_nm<1, 1>(nm, g, a, as, f, fs, s); break;
     }
     if (st != CMBWS_OK) return st;
   }

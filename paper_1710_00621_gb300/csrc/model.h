@@ -176,6 +176,8 @@ struct Model {
   // mask-restricted preconditioners (Sec. 4), applied with M_PI when precond = 2
   std::vector<MaskMG*> masks;
   int vcycle = 0;  // V-cycle of the mask preconditioners: 0 basic, 1 optimized (J ~ I)
+  // arithmetic of the transforms of M_PI inside the solvers (-1: the model's own)
+  int prec_M = -1;
   ~Model();
 
   HarmDev harm() const;

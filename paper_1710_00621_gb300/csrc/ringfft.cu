@@ -204,16 +204,21 @@ __device__ __forceinline__ void dif_group(Sbuf<T2> buf, int g, int s1, const T2*
   }
 }
 
-// register group: 8 elements (3 stages per pass) in every arithmetic; 16-element FP32 groups
-// spilled under the register cap that keeps three CTAs resident per SM
-constexpr int kGroupStages = 3;
+// Register groups of 8 elements (3 stages per pass) in every arithmetic (16-element FP32
+// groups spilled under the register cap that keeps three CTAs resident per SM).  Transforms
+// too small to give every thread a group of 8 use groups of 4 or 2, more passes over more
+// threads: small rings are latency-bound (the two-component L = 63 solve: 6.1 -> 5.4 ms).
+__device__ __forceinline__ int group_stages(int N) {
+  const int nt = (int)blockDim.x;
+  return (N >> 3) >= nt ? 3 : (N >> 2) >= nt ? 2 : 1;
+}
 
 // Decimation-in-time transform of size N (bit-reversed in, natural out); the first pass loads
 // through ld, the last stores through st; ends with a barrier.
 template <typename T2, typename LD, typename ST>
 __device__ void fft_dit(Sbuf<T2> buf, int N, const T2* __restrict__ tw, int nmax, bool inv,
                         const LD& ld, const ST& st) {
-  constexpr int S = kGroupStages;
+  const int S = group_stages(N);
   const int n = 31 - __clz(N);
   if (n == 0) {
     if (threadIdx.x == 0) st(0, ld(0));
@@ -244,7 +249,7 @@ __device__ void fft_dit(Sbuf<T2> buf, int N, const T2* __restrict__ tw, int nmax
 template <typename T2, typename LD, typename ST>
 __device__ void fft_dif(Sbuf<T2> buf, int N, const T2* __restrict__ tw, int nmax, bool inv,
                         const LD& ld, const ST& st) {
-  constexpr int S = kGroupStages;
+  const int S = group_stages(N);
   const int n = 31 - __clz(N);
   if (n == 0) {
     if (threadIdx.x == 0) st(0, ld(0));

@@ -26,7 +26,8 @@ def main():
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--lmax", type=int, default=3071)
     ap.add_argument("--nmaps", type=int, default=3)
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "fp32x2", "tf32", "3xtf32"])
+    ap.add_argument("--prec", default="fp32",
+                    choices=["fp32", "fp64", "fp32x2", "tf32", "3xtf32", "bf16", "bf16x3"])
     ap.add_argument("--op", default="both", choices=["synth", "analysis", "both", "apply"],
                     help="apply: y = A x of a one-component model with nmaps bands on the grid "
                          "(synthesis, fused ring FFT with the N^-1 multiply, adjoint)")
@@ -35,7 +36,8 @@ def main():
     kind = cw.CMBWS_GRID_HEALPIX if a.grid == "healpix" else cw.CMBWS_GRID_GL
     g = cw.cmbws_plan_grid(kind, a.n if a.grid == "healpix" else a.n + 1, a.lmax)
     prec = {"fp32": cw.CMBWS_FP32, "fp64": cw.CMBWS_FP64, "fp32x2": cw.CMBWS_FP32X2,
-            "tf32": cw.CMBWS_TF32, "3xtf32": cw.CMBWS_3XTF32}[a.prec]
+            "tf32": cw.CMBWS_TF32, "3xtf32": cw.CMBWS_3XTF32, "bf16": cw.CMBWS_BF16,
+            "bf16x3": cw.CMBWS_BF16X3}[a.prec]
     nalm = (a.lmax + 1) ** 2
     dev = torch.device("cuda")
     gen = torch.Generator(device=dev).manual_seed(0)

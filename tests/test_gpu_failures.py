@@ -82,7 +82,7 @@ def test_destroyed_and_foreign_handles_are_rejected():
                                ctypes.c_void_p(mp.data_ptr()), 1, None) == -1
 
 
-@pytest.mark.parametrize("prec", [cw.CMBWS_TF32, cw.CMBWS_3XTF32])
+@pytest.mark.parametrize("prec", [cw.CMBWS_TF32, cw.CMBWS_3XTF32, cw.CMBWS_BF16, cw.CMBWS_BF16X3])
 def test_bounded_mbarrier_wait_runs_out_and_reports_a_timeout(prec):
     """The tensor-core synthesis waits (bounded) on an mbarrier phase that nothing completes:
     every CTA gives up after ~1e5 SM clocks, issues no MMA, frees its tensor memory and writes
@@ -105,8 +105,9 @@ def test_bounded_mbarrier_wait_runs_out_and_reports_a_timeout(prec):
     cw.cmbws_sht_synth(g, prec, to_dev(alm), out, 2)
     cw.cmbws_device_status()
     got = to_host(out)
+    bound = 1.5e-2 if prec == cw.CMBWS_BF16 else 4e-3
     for k in range(2):
-        assert rel_err(got[k], osht.synthesis(o, 23, alm[k])) < 4e-3
+        assert rel_err(got[k], osht.synthesis(o, 23, alm[k])) < bound
 
 
 def test_solver_reports_a_timed_out_device_wait_as_timeout():

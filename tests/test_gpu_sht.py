@@ -9,6 +9,7 @@ from tests._gpu import rel_err, to_dev, to_host
 pytestmark = pytest.mark.gpu
 
 EPS64, EPS48, EPS32 = 2.0 ** -53, 2.0 ** -48, 2.0 ** -24
+TC_PRECS = [cw.CMBWS_TF32, cw.CMBWS_3XTF32, cw.CMBWS_BF16, cw.CMBWS_BF16X3]
 
 
 def tol(prec, lmax, op="synth"):
@@ -27,11 +28,13 @@ def tol(prec, lmax, op="synth"):
     15 sqrt(L+1) eps32, adjoint 6 sqrt(L+1) eps32, floor 1e-6.
     TF32 (synthesis only): both factors rounded to 11 significant bits (relative 2^-11 each),
     so up to 2^-10 per term (measured up to 5.9e-4, for a single term at L = 0): 1.5e-3.
+    BF16: 8 significant bits per factor (2^-9 each; measured 1.8e-3 to 5.0e-3): 1.5e-2.
     3XTF32: split TF32 drops only the lo x lo product (2^-22); the recurrence is the FP32 one
-    and its accumulation order differs: twice the FP32 bound.  The tensor-core modes share the
-    FP32 adjoint.
+    and its accumulation order differs: twice the FP32 bound.  BF16X3: the split keeps about
+    16 significant bits per factor (measured 4.4e-6 to 1.2e-5): twice the FP32 bound, at
+    least 4e-5.  The tensor-core modes share the FP32 adjoint.
     """
-    if op == "adj" and prec in (cw.CMBWS_TF32, cw.CMBWS_3XTF32):
+    if op == "adj" and prec in TC_PRECS:
         prec = cw.CMBWS_FP32
     n = lmax + 1
     if prec == cw.CMBWS_FP64:
@@ -40,7 +43,11 @@ def tol(prec, lmax, op="synth"):
         return max(1e-13, (16 if op == "synth" else 2) * n * EPS48)
     if prec == cw.CMBWS_TF32:
         return 1.5e-3
+    if prec == cw.CMBWS_BF16:
+        return 1.5e-2
     f32 = max(1e-6, (15 if op == "synth" else 6) * np.sqrt(n) * EPS32)
+    if prec == cw.CMBWS_BF16X3:
+        return max(4e-5, 2 * f32)
     return 2 * f32 if prec == cw.CMBWS_3XTF32 else f32
 
 
@@ -81,8 +88,8 @@ def test_grid_geometry_matches_oracle(kind, n, lmax):
     assert g.npix == o.npix
 
 
-PRECS = [cw.CMBWS_FP64, cw.CMBWS_FP32, cw.CMBWS_FP32X2, cw.CMBWS_TF32, cw.CMBWS_3XTF32]
-TC_PRECS = [cw.CMBWS_TF32, cw.CMBWS_3XTF32]
+PRECS = [cw.CMBWS_FP64, cw.CMBWS_FP32, cw.CMBWS_FP32X2, cw.CMBWS_TF32, cw.CMBWS_3XTF32,
+         cw.CMBWS_BF16, cw.CMBWS_BF16X3]
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -200,7 +207,7 @@ def test_adjointness_large_healpix():
 
 
 @pytest.mark.parametrize("prec", [cw.CMBWS_FP64, cw.CMBWS_FP32X2, cw.CMBWS_FP32, cw.CMBWS_TF32,
-                                  cw.CMBWS_3XTF32])
+                                  cw.CMBWS_3XTF32, cw.CMBWS_BF16, cw.CMBWS_BF16X3])
 def test_full_size_sampled_rings_nside1024(prec):
     """Every precision against the oracle on rings from the pole to the equator.  Near the
     poles the FP32 recurrence runs in its difference form (an almost double characteristic
@@ -222,7 +229,7 @@ def test_full_size_sampled_rings_nside1024(prec):
     ref = osht.synthesis(sub, L, a)
     gsub = np.concatenate([got[o.offset[r]:o.offset[r + 1]] for r in rings])
     assert rel_err(gsub, ref) < tol(prec, L), rel_err(gsub, ref)
-    if prec in (cw.CMBWS_TF32, cw.CMBWS_3XTF32):
+    if prec in TC_PRECS:
         f32 = to_dev(np.zeros(g.npix))
         cw.cmbws_sht_synth(g, cw.CMBWS_FP32, to_dev(a), f32, 1)
         g32 = to_host(f32)

@@ -130,6 +130,37 @@ def test_wiener_solve_fp64_and_fp32_refined(models, name):
         assert rel_err(to_host(x), xo) < 1e-4, (prec, rep)
 
 
+@pytest.mark.parametrize("pc", [cw.CMBWS_BF16, cw.CMBWS_TF32, cw.CMBWS_FP64])
+def test_solve_with_preconditioner_in_another_precision(models, pc):
+    """The transforms of M_PI may run in their own arithmetic (here BF16 / TF32 tensor cores,
+    or FP64) inside the solve of an FP32 model: the preconditioner only shapes the Krylov space,
+    so the certified residual and the solution still reach the tolerance; cmbws_apply_precond
+    keeps the model's own precision."""
+    work, m, inp = models["multires64"]
+    d = [mp + n for mp, n in zip(om.project(m, inp["x_true"]), inp["noise"])]
+    b = om.rhs(m, d)
+    xo, _ = pcg(lambda v: om.apply_A(m, v), b, lambda v: opc.apply_precond(m, v), tol=1e-12,
+                maxiter=2000)
+    g, _ = gpu_model(work, inp, cw.CMBWS_FP32)
+    v = to_dev(np.random.default_rng(5).standard_normal(m.nvec()))
+    z0, z1 = to_dev(np.zeros(m.nvec())), to_dev(np.zeros(m.nvec()))
+    cw.cmbws_apply_precond(g, v, z0)
+    cw.cmbws_model_set_precond_prec(g, pc)
+    cw.cmbws_apply_precond(g, v, z1)
+    assert np.array_equal(to_host(z0), to_host(z1))
+    x = to_dev(np.zeros(m.nvec()))
+    rep = cw.cmbws_cg_solve(g, to_dev(b), x, tol=1e-6, maxiter=2000, inner_tol=1e-3,
+                            cert_prec=cw.CMBWS_FP64)
+    assert rep["code"] == 0 and rep["rel_res"] <= 1e-6, rep
+    r = b - om.apply_A(m, to_host(x))
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.01e-6
+    assert rel_err(to_host(x), xo) < 1e-4, rep
+    with pytest.raises(cw.CmbwsError) as e:
+        cw.cmbws_model_set_precond_prec(g, 99)
+    assert e.value.code == -1
+    cw.cmbws_model_set_precond_prec(g, -1)
+
+
 def test_multires_fp64_solve_matches_oracle_solution_to_1e6(models):
     """FP64 mode: the multi-resolution model at 1/16 of the benchmark's resolution (HEALPix
     Nside 16/32/64 bands, L_nu up to 191, three components) solved to a residual of 1e-10 lies
