@@ -254,6 +254,9 @@ inline bool valid_prec(int prec) {
 int legendre_synth_df(const Grid& g, int nmaps, const void* alm, void* F, cudaStream_t s);
 // ---- tensor-core Legendre synthesis (legendre_tc.cu), prec TF32 / 3XTF32 / BF16 / BF16X3 ----
 int legendre_synth_tc(const Grid& g, int prec, int nmaps, const void* alm, void* F, cudaStream_t s);
+// adjoint synthesis on the tensor cores from the FP32 adjoint input (eo layout), prec BF16 / BF16X3
+int legendre_adjoint_tc(const Grid& g, int prec, int nmaps, const float* eo, double* out,
+                        cudaStream_t s);
 // reads and clears the device-side status of the tensor-core kernels of the current device
 // (synchronous): *timed_out is true if a bounded mbarrier wait ran out since the last read
 int tc_status_take(bool* timed_out);

@@ -749,6 +749,8 @@ int legendre_adjoint(const Grid& g, int prec, int nmaps, const void* F, void* pa
     return CMBWS_OK;
   }
   if (prec == CMBWS_FP64) return adj_dispatch<double>(g, nmaps, F, part, out, s);
+  if (prec == CMBWS_BF16 || prec == CMBWS_BF16X3)
+    return legendre_adjoint_tc(g, prec, nmaps, (const float*)part, out, s);
   return adj_dispatch_ck(g, nmaps, (const float*)part, out, s);
 }
 

@@ -463,10 +463,451 @@ int launch_synth_tc_nm(int nm, const Grid& g, const void* a, int64_t as, void* f
   }
 }
 
+// ---- adjoint synthesis (analysis) on the tensor cores ----
+//
+// Per m the adjoint a_lm = sum over ring pairs of lambda_lm(theta) times the pair's even or
+// odd part (Sec. 2.1) is, for a tile of 128 values of l, the product
+// D[l][col] = sum_p Lambda[l][p] B[p][col] with B[p][h * 8 + part] the pair's even (h = 0,
+// north + south) and odd (h = 1, north - south) parts, so that row l reads its sum from the
+// columns of the parity of l - m.  The contraction runs over ring pairs (K), 64 per stage.
+// * Lambda^T (A operand, M = l, K = pairs) is generated by the recurrence: thread (chunk c,
+//   octet o) restarts each of 8 pairs at the FP64-computed checkpoint of its chunk of
+//   kChunk = 8 values of l (as the FP32 adjoint does) and writes the 8 x 8 BF16 values as one
+//   core matrix (8 rows of l x 16 bytes of pairs) of the K-major shared-memory layout; core
+//   matrices of consecutive chunks are 144 bytes apart, so that the 16-byte row stores of a
+//   warp fall on distinct banks;
+// * B (the pairs' parts, FP32 from the ring FFT) is rounded to BF16 into the K-major layout
+//   of the synthesis;
+// * SA = 2 splits both operands into hi + lo BF16 slices: A_hi [B_hi | B_lo] (N = 32) and
+//   A_lo B_hi accumulate into the same 32 columns, whose halves are summed at the end;
+// * two stages alternate; one thread issues the MMAs (M = 128, K = 16) after the stage's
+//   barrier and commits them to the stage's mbarrier, on which the producers wait (bounded)
+//   before overwriting it.
+constexpr int kAtM = 128;     // values of l per CTA (MMA M, threads) = 16 chunks of kChunk
+constexpr int kAtKS = 64;     // ring pairs per stage: 8 octets, 4 MMAs of K = 16
+constexpr int kAtCore = 144;  // bytes between the core matrices of consecutive chunks
+constexpr int kAtOct = (kAtM / 8) * kAtCore;  // bytes between the core matrices of consecutive octets
+constexpr int kAtASlice = (kAtKS / 8) * kAtOct;
+constexpr int kAtMaxStage = 128;  // stages of a launch (ring pairs <= 8192)
+
+template <int SA>
+struct AtLayout {
+  static constexpr int kBStep = 512 * SA;  // one K step of B: 16 SA rows x 16 pairs, BF16
+  static constexpr int kBTile = (kAtKS / 16) * kBStep;
+  static constexpr int kStage = SA * kAtASlice + kBTile;  // one stage, single-buffered
+  // inputs of one stage, copied (cp.async) one stage ahead: the stage's starts and y and its
+  // even / odd parts (up to 4 maps)
+  static constexpr int kPLs = 0;
+  static constexpr int kPY = kPLs + kAtKS * 4;
+  static constexpr int kPEo = kPY + kAtKS * 4;
+  static constexpr int kPre = kPEo + kAtKS * 16 * 4;
+  static constexpr int kOffPre = kStage;
+  static constexpr int kOffBar = kOffPre + 2 * kPre;  // uint64_t mbar[2]
+  static constexpr int kOffT = kOffBar + 16;          // uint32_t tensor-memory base, bad flag
+  static constexpr int kOffMask = kOffT + 16;         // uint32_t stage mask[kAtMaxStage / 32]
+  static constexpr int kSmem = kOffMask + kAtMaxStage / 8;
+  static constexpr uint32_t kCols = 32;
+};
+
+// kind::f16 instruction descriptor, BF16 A and B (K-major), FP32 D, M = 128, N = n
+__host__ __device__ constexpr uint32_t idesc_bf16(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((128u >> 4) << 24);
+}
+
+// D (+)= A B with both operands in shared memory (descriptors)
+__device__ __forceinline__ void mma_bf16_ss(uint32_t d, uint64_t adesc, uint64_t bdesc,
+                                            uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+}
+
+// byte offset of B[n][p] (output column n, pair p < 64 of the stage) in a stage's B tile
+template <int SA>
+__device__ __forceinline__ int at_boff(int n, int p) {
+  return (p >> 4) * AtLayout<SA>::kBStep + (n >> 3) * 256 + ((p >> 3) & 1) * 128 + (n & 7) * 16 +
+         (p & 7) * 2;
+}
+
+template <int NM, int SA>
+__global__ void __launch_bounds__(kAtM, SA == 1 ? 5 : 4)
+k_leg_adj_tc(const float* __restrict__ eo, const float* __restrict__ Acoef,
+             const int* __restrict__ ls_tab, const float2* __restrict__ st,
+             const float* __restrict__ yr, const float2* __restrict__ ck,
+             const int64_t* __restrict__ ck_base, const int* __restrict__ tmin,
+             const double* __restrict__ c64, double2* __restrict__ out, int64_t nlm, int L,
+             int npair) {
+  using LY = AtLayout<SA>;
+  static_assert(kChunk == 8, "one core matrix holds one chunk of 8 values of l");
+  static_assert(NM >= 1 && NM <= 4, "at most 4 maps (8 columns per parity)");
+  static_assert(kAtKS % kTileMinPT == 0, "a stage covers whole entries of the tile-start table");
+  constexpr int P = 2 * NM;
+  constexpr int NTM = kAtKS / kTileMinPT;
+  const int m = blockIdx.y;
+  const int lb0 = m + kAtM * (int)blockIdx.x;  // first l of the tile
+  if (lb0 > L) return;                         // CTA-uniform, before any barrier
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ci = tid & 15, oc = tid >> 4;  // chunk of the tile, octet of the stage
+  const int nck = (L - m + kChunk) / kChunk;
+  const int c = (int)blockIdx.x * (kAtM / kChunk) + ci;
+  const int l0 = m + kChunk * c;
+  const bool cval = c < nck;
+  const int64_t lmo = lm_off(L, m) - m;
+  const int llast = min(L, lb0 + kAtM - 1);
+  const int ntm = (npair + kTileMinPT - 1) / kTileMinPT;
+  const int nst = (npair + kAtKS - 1) / kAtKS;  // <= kAtMaxStage (checked by the host)
+
+  extern __shared__ __align__(1024) unsigned char sm[];
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + LY::kOffBar);
+  uint32_t* s_tb = reinterpret_cast<uint32_t*>(sm + LY::kOffT);
+  int* s_bad = reinterpret_cast<int*>(sm + LY::kOffT + 8);
+  uint32_t* s_mask = reinterpret_cast<uint32_t*>(sm + LY::kOffMask);
+  // stages with a pair that starts by the tile's last l (the others add nothing): lane s of
+  // a warp tests stage s against the smallest start of each of its tiles of pairs
+  {
+    const int* tm = tmin + (int64_t)m * ntm;
+    for (int s0 = warp * 32; s0 < kAtMaxStage; s0 += kAtM) {
+      const int s = s0 + lane;
+      bool any = false;
+      if (s < nst)
+#pragma unroll
+        for (int e = 0; e < NTM; ++e) {
+          const int t = s * NTM + e;
+          any |= t < ntm && tm[t] <= llast;
+        }
+      const uint32_t bal = __ballot_sync(0xffffffffu, any);
+      if (lane == 0) s_mask[s0 >> 5] = bal;
+    }
+  }
+  __syncthreads();
+  // first stage at or after s whose bit is set (nst if none)
+  auto next_stage = [&](int s) {
+    for (; s < nst; s = (s | 31) + 1) {
+      const uint32_t w = s_mask[s >> 5] >> (s & 31);
+      if (w) return min(nst, s + __ffs(w) - 1);
+    }
+    return nst;
+  };
+  int s = next_stage(0);
+  if (s >= nst) {  // no pair has a significant value in the tile: the sums are zero
+    const int l = lb0 + tid;
+    if (l <= L)
+#pragma unroll
+      for (int k = 0; k < NM; ++k) out[k * nlm + lmo + l] = make_double2(0.0, 0.0);
+    return;
+  }
+
+  if (tid == 0) *s_bad = 0;
+  // zero the stage (B columns of absent maps stay zero)
+  for (int i = tid; i < LY::kStage / 16; i += kAtM)
+    reinterpret_cast<float4*>(sm)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_addr(s_tb)),
+                 "r"(LY::kCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&mbar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&mbar[1])));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
+    // test support, as in the synthesis: a wait that nothing completes runs out
+    const long long stall = g_tc_stall_cycles;
+    if (stall > 0 && !mbar_wait(&mbar[1], 0, stall)) *s_bad = 1;
+  }
+
+  float Al[kChunk];
+#pragma unroll
+  for (int j = 0; j < kChunk; ++j) Al[j] = (cval && l0 + j <= L) ? Acoef[lmo + l0 + j] : 0.f;
+  const float2* ckc = ck + (cval ? ck_base[m] + c : 0);  // + p * nck
+  const int* lsm = ls_tab + (int64_t)m * npair;
+  const float2* stm = st + (int64_t)m * npair;
+  const float* eom = eo + (int64_t)m * npair * 2 * P;
+
+  // copy the starts, y and even / odd parts of stage s into prefetch buffer pb (one commit
+  // group); pairs past the last get start INT_MAX (never started) and y = 0
+  auto prefetch = [&](int s, int pb) {
+    unsigned char* pre = sm + LY::kOffPre + pb * LY::kPre;
+    const int p0 = s * kAtKS;
+    const int np = min(kAtKS, npair - p0);
+    if (tid < kAtKS) {
+      if (tid < np) {
+        cp_async4(pre + LY::kPLs + 4 * tid, lsm + p0 + tid);
+        cp_async4(pre + LY::kPY + 4 * tid, yr + p0 + tid);
+      } else {
+        reinterpret_cast<int*>(pre + LY::kPLs)[tid] = INT_MAX;
+        reinterpret_cast<float*>(pre + LY::kPY)[tid] = 0.f;
+      }
+    }
+    // the even / odd parts of the stage's pairs are contiguous (2P floats per pair)
+    for (int i = tid; i < np * P / 2; i += kAtM)
+      cp_async16(pre + LY::kPEo + 16 * i, eom + (int64_t)p0 * 2 * P + 4 * i);
+    cp_async_commit();
+  };
+  // this thread's 8 checkpoints of stage s
+  auto load_ck = [&](int s, float2 (&cv)[8]) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int p = s * kAtKS + 8 * oc + i;
+      cv[i] = (cval && p < npair) ? ckc[(int64_t)p * nck] : make_float2(0.f, 0.f);
+    }
+  };
+
+  float2 ckA[8], ckB[8];
+  load_ck(s, ckA);
+  prefetch(s, 0);
+  cp_async_wait<0>();
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+  const uint32_t tb = *s_tb;
+  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  unsigned char* As = sm;
+  unsigned char* Bs = As + SA * kAtASlice;
+
+  bool bad = false;
+  int k = 0;
+  // one stage: inputs of stage s in prefetch buffer k & 1 and in cv; the next stage's
+  // checkpoints are loaded into cvn
+  auto run_stage = [&](const float2 (&cv)[8], float2 (&cvn)[8]) {
+    const int sn = next_stage(s + 1);
+    if (sn < nst) {
+      load_ck(sn, cvn);
+      prefetch(sn, (k + 1) & 1);
+    }
+    const unsigned char* pre = sm + LY::kOffPre + (k & 1) * LY::kPre;
+    const int p0 = s * kAtKS;
+    const int np = min(kAtKS, npair - p0);
+    // B values and A start values into registers before waiting for the previous MMAs
+    const int n = tid & 15, q = n & 7, ob = tid >> 4;
+    float v[8];
+    {
+      const float* e = reinterpret_cast<const float*>(pre + LY::kPEo) + (n >> 3) * P + q;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) v[i] = (q < P && 8 * ob + i < np) ? e[(8 * ob + i) * 2 * P] : 0.f;
+    }
+    const int4* lsb = reinterpret_cast<const int4*>(pre + LY::kPLs) + 2 * oc;
+    const float4* yb = reinterpret_cast<const float4*>(pre + LY::kPY) + 2 * oc;
+    const int4 la = lsb[0], lb = lsb[1];
+    const float4 ya = yb[0], yb2 = yb[1];
+    const int jinj[8] = {la.x - l0, la.y - l0, la.z - l0, la.w - l0,
+                         lb.x - l0, lb.y - l0, lb.z - l0, lb.w - l0};
+    const float y[8] = {ya.x, ya.y, ya.z, ya.w, yb2.x, yb2.y, yb2.z, yb2.w};
+    float ma[8], mb[8];
+    bool mid = false, first = false;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      ma[i] = jinj[i] > 0 ? 0.f : cv[i].x;  // before its start a pair's values are zero
+      mb[i] = jinj[i] > 0 ? 0.f : cv[i].y;
+      first |= jinj[i] == 0;
+      mid |= (unsigned)(jinj[i] - 1) < (unsigned)(kChunk - 1);  // starts after the chunk's first l
+    }
+    if (first)
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        if (jinj[i] == 0) {
+          const float2 w = stm[p0 + 8 * oc + i];
+          ma[i] = w.x;
+          mb[i] = w.y;
+        }
+    // the previous stage's MMAs have read the tile
+    if (k >= 1 && !*s_bad && !mbar_wait(&mbar[0], (k - 1) & 1)) bad = true;
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+    if (q < P) {  // B: column n (parity n / 8, part q) of pair octet ob, one core-matrix row
+      uint4 w;
+      w.x = bf16x2_rn(v[0], v[1]);
+      w.y = bf16x2_rn(v[2], v[3]);
+      w.z = bf16x2_rn(v[4], v[5]);
+      w.w = bf16x2_rn(v[6], v[7]);
+      const int off = (ob >> 1) * LY::kBStep + (n >> 3) * 256 + (ob & 1) * 128 + q * 16;
+      *reinterpret_cast<uint4*>(Bs + off) = w;
+      if constexpr (SA == 2) {
+        uint4 u;
+        u.x = bf16x2_rn(v[0] - bf16_lo(w.x), v[1] - bf16_hi(w.x));
+        u.y = bf16x2_rn(v[2] - bf16_lo(w.y), v[3] - bf16_hi(w.y));
+        u.z = bf16x2_rn(v[4] - bf16_lo(w.z), v[5] - bf16_hi(w.z));
+        u.w = bf16x2_rn(v[6] - bf16_lo(w.w), v[7] - bf16_hi(w.w));
+        *reinterpret_cast<uint4*>(Bs + off + 512) = u;  // rows 16..31
+      }
+    }
+    // A: the chunk's 8 values of l for the octet's 8 pairs, one core matrix per slice
+    unsigned char* arow = As + oc * kAtOct + ci * kAtCore;
+    auto put = [&](int j, const float (&x)[8]) {
+      uint4 w;
+      w.x = bf16x2_rn(x[0], x[1]);
+      w.y = bf16x2_rn(x[2], x[3]);
+      w.z = bf16x2_rn(x[4], x[5]);
+      w.w = bf16x2_rn(x[6], x[7]);
+      *reinterpret_cast<uint4*>(arow + 16 * j) = w;
+      if constexpr (SA == 2) {
+        uint4 u;
+        u.x = bf16x2_rn(x[0] - bf16_lo(w.x), x[1] - bf16_hi(w.x));
+        u.y = bf16x2_rn(x[2] - bf16_lo(w.y), x[3] - bf16_hi(w.y));
+        u.z = bf16x2_rn(x[4] - bf16_lo(w.z), x[5] - bf16_hi(w.z));
+        u.w = bf16x2_rn(x[6] - bf16_lo(w.w), x[7] - bf16_hi(w.w));
+        *reinterpret_cast<uint4*>(arow + kAtASlice + 16 * j) = u;
+      }
+    };
+    put(0, ma);
+    put(1, mb);
+    if (__any_sync(0xffffffffu, mid)) {  // warp-uniform: some start is injected mid-chunk
+#pragma unroll
+      for (int j = 2; j < kChunk; j += 2) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          float na = fmaf(fmaf(-Al[j], y[i], Al[j]), mb[i], -ma[i]);
+          float nb = fmaf(fmaf(-Al[j + 1], y[i], Al[j + 1]), na, -mb[i]);
+          if (jinj[i] == j) {
+            const float2 w = stm[p0 + 8 * oc + i];
+            na = w.x;
+            nb = w.y;
+          }
+          ma[i] = na;
+          mb[i] = nb;
+        }
+        put(j, ma);
+        put(j + 1, mb);
+      }
+    } else {
+#pragma unroll
+      for (int j = 2; j < kChunk; j += 2) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const float na = fmaf(fmaf(-Al[j], y[i], Al[j]), mb[i], -ma[i]);
+          mb[i] = fmaf(fmaf(-Al[j + 1], y[i], Al[j + 1]), na, -mb[i]);
+          ma[i] = na;
+        }
+        put(j, ma);
+        put(j + 1, mb);
+      }
+    }
+    cp_async_wait<0>();  // the next stage's inputs, visible to all after the barrier
+    asm volatile("fence.proxy.async.shared::cta;\n" ::);
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+    if (bad) atomicOr(s_bad, 1);
+    __syncthreads();
+    if (tid == 0 && !*s_bad) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+      const uint32_t ab = smem_addr(As), bb = smem_addr(Bs);
+#pragma unroll
+      for (int ks = 0; ks < kAtKS / 16; ++ks) {
+        const uint64_t bd = smem_desc(bb + ks * LY::kBStep, 128, 256);
+#pragma unroll
+        for (int i = 0; i < SA; ++i) {
+          const uint64_t ad = smem_desc(ab + i * kAtASlice + ks * 2 * kAtOct, kAtOct, kAtCore);
+          mma_bf16_ss(tb + 16 * i, ad, bd, idesc_bf16(16 * (SA - i)),
+                      (k > 0 || ks > 0 || i > 0) ? 1u : 0u);
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+          smem_addr(&mbar[0])));
+    }
+    s = sn;
+    ++k;
+  };
+  // two stages per trip, so that the checkpoint registers alternate without copies
+  while (true) {
+    run_stage(ckA, ckB);
+    if (s >= nst) break;
+    run_stage(ckB, ckA);
+    if (s >= nst) break;
+  }
+  // accumulators after the last stage
+  if (!*s_bad && !mbar_wait(&mbar[0], (k - 1) & 1)) bad = true;
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+  uint32_t d[16 * SA];
+  if constexpr (SA == 1) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        : "=r"(d[0]), "=r"(d[1]), "=r"(d[2]), "=r"(d[3]), "=r"(d[4]), "=r"(d[5]), "=r"(d[6]), "=r"(d[7]),
+          "=r"(d[8]), "=r"(d[9]), "=r"(d[10]), "=r"(d[11]), "=r"(d[12]), "=r"(d[13]), "=r"(d[14]), "=r"(d[15])
+        : "r"(tb + lane_base));
+  } else {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+        : "=r"(d[0]), "=r"(d[1]), "=r"(d[2]), "=r"(d[3]), "=r"(d[4]), "=r"(d[5]), "=r"(d[6]), "=r"(d[7]),
+          "=r"(d[8]), "=r"(d[9]), "=r"(d[10]), "=r"(d[11]), "=r"(d[12]), "=r"(d[13]), "=r"(d[14]), "=r"(d[15]),
+          "=r"(d[16]), "=r"(d[17]), "=r"(d[18]), "=r"(d[19]), "=r"(d[20]), "=r"(d[21]), "=r"(d[22]),
+          "=r"(d[23]), "=r"(d[24]), "=r"(d[25]), "=r"(d[26]), "=r"(d[27]), "=r"(d[28]), "=r"(d[29]),
+          "=r"(d[30]), "=r"(d[31])
+        : "r"(tb + lane_base));
+  }
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
+  if (bad) atomicOr(s_bad, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+  __syncthreads();
+  const bool failed = *s_bad != 0;
+  if (failed && tid == 0) atomicOr(&g_tc_status, 1u);
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tb), "r"(LY::kCols));
+  const int l = lb0 + tid;  // row tid of D
+  if (l > L) return;
+  const int h = (l - m) & 1;
+  const double cc = c64[lmo + l];
+  const double nan = __longlong_as_double(0x7ff8000000000000ll);
+#pragma unroll
+  for (int q = 0; q < NM; ++q) {
+    // static register indices: the parity selects between the two column groups
+    double re = (double)__uint_as_float(h ? d[8 + 2 * q] : d[2 * q]);
+    double im = (double)__uint_as_float(h ? d[8 + 2 * q + 1] : d[2 * q + 1]);
+    if constexpr (SA == 2) {
+      re += (double)__uint_as_float(h ? d[24 + 2 * q] : d[16 + 2 * q]);
+      im += (double)__uint_as_float(h ? d[24 + 2 * q + 1] : d[16 + 2 * q + 1]);
+    }
+    // a timed-out wait leaves NaN in the output, which the solver reports as a breakdown
+    out[q * nlm + lmo + l] = failed ? make_double2(nan, nan) : make_double2(cc * re, cc * im);
+  }
+}
+
+template <int NM, int SA>
+int launch_adj_tc(const Grid& g, const float* eo, double* out, cudaStream_t s) {
+  using LY = AtLayout<SA>;
+  const int L = g.lmax;
+  if (g.npair > kAtMaxStage * kAtKS) {
+    set_error("tensor-core adjoint: more than 8192 ring pairs");
+    return CMBWS_ERR_ARG;
+  }
+  dim3 grd((L + kAtM) / kAtM, L + 1);
+  auto kern = k_leg_adj_tc<NM, SA>;
+  CMBWS_TRY(ensure_dyn_smem((const void*)kern, LY::kSmem));
+  // profiling arithmetic kinds: 5 BF16, 6 split BF16
+  ProfScope ps(PROF_LEG_ADJ, s, 4 + SA, leg_work(g, NM));
+  kern<<<grd, kAtM, LY::kSmem, s>>>(eo, g.A32.as<float>(), g.ls.as<int>(), g.st32.as<float2>(),
+                                    g.y32.as<float>(), g.ck32.as<float2>(), g.ck_base.as<int64_t>(),
+                                    g.ls_tmin.as<int>(), g.c64.as<double>(), (double2*)out,
+                                    nlm_of(L), L, g.npair);
+  CMBWS_LAUNCH_CHECK();
+  return CMBWS_OK;
+}
+
+template <int SA>
+int launch_adj_tc_nm(int nm, const Grid& g, const float* e, double* o, cudaStream_t s) {
+  switch (nm) {
+    case 1: return launch_adj_tc<1, SA>(g, e, o, s);
+    case 2: return launch_adj_tc<2, SA>(g, e, o, s);
+    case 3: return launch_adj_tc<3, SA>(g, e, o, s);
+    default: return launch_adj_tc<4, SA>(g, e, o, s);
+  }
+}
+
 static_assert(TcLayout<0>::kUsed <= TcLayout<0>::kSmem && TcLayout<1>::kUsed <= TcLayout<1>::kSmem,
               "shared-memory layout exceeds the request");
 
 }  // namespace
+
+int legendre_adjoint_tc(const Grid& g, int prec, int nmaps, const float* eo, double* out,
+                        cudaStream_t s) {
+  const int64_t nlm = nlm_of(g.lmax), cs = (int64_t)(g.lmax + 1) * g.npair * 4;
+  for (int k0 = 0; k0 < nmaps; k0 += 4) {
+    const int nm = nmaps - k0 < 4 ? nmaps - k0 : 4;
+    const float* e = eo + k0 * cs;
+    double* o = out + 2 * k0 * nlm;
+    const int st = prec == CMBWS_BF16 ? launch_adj_tc_nm<1>(nm, g, e, o, s)
+                                      : launch_adj_tc_nm<2>(nm, g, e, o, s);
+    if (st != CMBWS_OK) return st;
+  }
+  return CMBWS_OK;
+}
 
 int legendre_synth_tc(const Grid& g, int prec, int nmaps, const void* alm, void* F, cudaStream_t s) {
   const int64_t as = nlm_of(g.lmax), fs = (int64_t)g.nring * (g.lmax + 1);

@@ -32,10 +32,14 @@ def tol(prec, lmax, op="synth"):
     3XTF32: split TF32 drops only the lo x lo product (2^-22); the recurrence is the FP32 one
     and its accumulation order differs: twice the FP32 bound.  BF16X3: the split keeps about
     16 significant bits per factor (measured 4.4e-6 to 1.2e-5): twice the FP32 bound, at
-    least 4e-5.  The tensor-core modes share the FP32 adjoint.
+    least 4e-5.  TF32 and 3XTF32 share the FP32 adjoint; the BF16 and BF16X3 adjoints run on
+    the tensor cores (BF16 factors, the FP32 adjoint's checkpointed recurrence) and take the
+    synthesis bounds of their mode.
     """
-    if op == "adj" and prec in TC_PRECS:
+    if op == "adj" and prec in (cw.CMBWS_TF32, cw.CMBWS_3XTF32):
         prec = cw.CMBWS_FP32
+    if op == "adj" and prec in (cw.CMBWS_BF16, cw.CMBWS_BF16X3):
+        op = "synth"
     n = lmax + 1
     if prec == cw.CMBWS_FP64:
         return max(1e-14, 40 * n * EPS64)
@@ -245,8 +249,8 @@ SAMPLED_M = [0, 1, 2, 700, 1535, 3000, 3071]
 
 
 def full_size_adjoint_tol(prec):
-    """The adjoint bound of tol() at L = 3071 (FP64 1.4e-11, FP32X2 2.2e-11, FP32 1.8e-5;
-    measured on GB300: 1.3e-12, 2.5e-12, 1.9e-6)."""
+    """The adjoint bound of tol() at L = 3071 (FP64 1.4e-11, FP32X2 2.2e-11, FP32 1.8e-5,
+    BF16 1.5e-2, BF16X3 4e-5; measured on GB300: 1.3e-12, 2.5e-12, 1.9e-6)."""
     return tol(prec, 3071, "adj")
 
 
@@ -257,7 +261,8 @@ def nside1024():
 
 
 @pytest.mark.parametrize("weighted", [0, 1])
-@pytest.mark.parametrize("prec", [cw.CMBWS_FP64, cw.CMBWS_FP32X2, cw.CMBWS_FP32])
+@pytest.mark.parametrize("prec", [cw.CMBWS_FP64, cw.CMBWS_FP32X2, cw.CMBWS_FP32, cw.CMBWS_BF16,
+                                  cw.CMBWS_BF16X3])
 def test_full_size_adjoint_sampled_orders_nside1024(nside1024, prec, weighted):
     """Adjoint synthesis / analysis of three maps at HEALPix Nside 1024, L = 3071 (the
     bench's largest band grid, three bands per launch as in its solves) against the oracle on
@@ -278,3 +283,24 @@ def test_full_size_adjoint_sampled_orders_nside1024(nside1024, prec, weighted):
         errs.append(rel_err(gv, rv))
     print(f"full-size adjoint prec={prec} weighted={weighted}: max rel err {max(errs):.3e}")
     assert max(errs) < full_size_adjoint_tol(prec), errs
+
+
+@pytest.mark.parametrize("prec", [cw.CMBWS_BF16, cw.CMBWS_BF16X3])
+@pytest.mark.parametrize("nmaps", [1, 2, 3, 4, 5, 9])
+def test_tensor_core_adjoint_map_batches(nmaps, prec):
+    """Every map-count variant of the tensor-core adjoint (1..4 maps per launch) on a grid
+    with several 128-l tiles per m and a ragged last stage of ring pairs (Nside 40: 80 ring
+    pairs, 64 per stage), against the oracle and against the FP32 CUDA-core adjoint."""
+    g = cw.cmbws_plan_grid(cw.CMBWS_GRID_HEALPIX, 40, 150)
+    o = og.healpix(40)
+    maps = np.random.default_rng(70 + nmaps).standard_normal((nmaps, g.npix))
+    out = to_dev(np.zeros((nmaps, 151 ** 2)))
+    ref32 = to_dev(np.zeros((nmaps, 151 ** 2)))
+    cw.cmbws_sht_analysis(g, prec, to_dev(maps), out, nmaps, 1)
+    cw.cmbws_sht_analysis(g, cw.CMBWS_FP32, to_dev(maps), ref32, nmaps, 1)
+    got, g32 = to_host(out), to_host(ref32)
+    for k in range(nmaps):
+        ref = osht.adjoint(o, 150, maps[k], weighted=True)
+        assert rel_err(got[k], ref) < tol(prec, 150, "adj"), (k, rel_err(got[k], ref))
+        assert rel_err(got[k], g32[k]) < tol(prec, 150, "adj"), k
+
