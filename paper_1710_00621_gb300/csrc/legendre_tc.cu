@@ -495,11 +495,12 @@ struct AtLayout {
   static constexpr int kBStep = 512 * SA;  // one K step of B: 16 SA rows x 16 pairs, BF16
   static constexpr int kBTile = (kAtKS / 16) * kBStep;
   static constexpr int kStage = SA * kAtASlice + kBTile;  // one stage, single-buffered
-  // inputs of one stage, copied (cp.async) one stage ahead: the stage's starts and y and its
-  // even / odd parts (up to 4 maps)
+  // inputs of one stage, copied (cp.async) one stage ahead: the stage's starts, y, start
+  // values and even / odd parts (up to 4 maps)
   static constexpr int kPLs = 0;
   static constexpr int kPY = kPLs + kAtKS * 4;
-  static constexpr int kPEo = kPY + kAtKS * 4;
+  static constexpr int kPSt = kPY + kAtKS * 4;
+  static constexpr int kPEo = kPSt + kAtKS * 8;
   static constexpr int kPre = kPEo + kAtKS * 16 * 4;
   static constexpr int kOffPre = kStage;
   static constexpr int kOffBar = kOffPre + 2 * kPre;  // uint64_t mbar[2]
@@ -634,6 +635,7 @@ k_leg_adj_tc(const float* __restrict__ eo, const float* __restrict__ Acoef,
       if (tid < np) {
         cp_async4(pre + LY::kPLs + 4 * tid, lsm + p0 + tid);
         cp_async4(pre + LY::kPY + 4 * tid, yr + p0 + tid);
+        cp_async8(pre + LY::kPSt + 8 * tid, stm + p0 + tid);
       } else {
         reinterpret_cast<int*>(pre + LY::kPLs)[tid] = INT_MAX;
         reinterpret_cast<float*>(pre + LY::kPY)[tid] = 0.f;
@@ -688,6 +690,7 @@ k_leg_adj_tc(const float* __restrict__ eo, const float* __restrict__ Acoef,
     }
     const int4* lsb = reinterpret_cast<const int4*>(pre + LY::kPLs) + 2 * oc;
     const float4* yb = reinterpret_cast<const float4*>(pre + LY::kPY) + 2 * oc;
+    const float2* stb = reinterpret_cast<const float2*>(pre + LY::kPSt) + 8 * oc;
     const int4 la = lsb[0], lb = lsb[1];
     const float4 ya = yb[0], yb2 = yb[1];
     const int jinj[8] = {la.x - l0, la.y - l0, la.z - l0, la.w - l0,
@@ -706,7 +709,7 @@ k_leg_adj_tc(const float* __restrict__ eo, const float* __restrict__ Acoef,
 #pragma unroll
       for (int i = 0; i < 8; ++i)
         if (jinj[i] == 0) {
-          const float2 w = stm[p0 + 8 * oc + i];
+          const float2 w = stb[i];
           ma[i] = w.x;
           mb[i] = w.y;
         }
@@ -758,7 +761,7 @@ k_leg_adj_tc(const float* __restrict__ eo, const float* __restrict__ Acoef,
           float na = fmaf(fmaf(-Al[j], y[i], Al[j]), mb[i], -ma[i]);
           float nb = fmaf(fmaf(-Al[j + 1], y[i], Al[j + 1]), na, -mb[i]);
           if (jinj[i] == j) {
-            const float2 w = stm[p0 + 8 * oc + i];
+            const float2 w = stb[i];
             na = w.x;
             nb = w.y;
           }
