@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--no-fp64-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--precond-prec", choices=["model", "bf16", "tf32", "fp32"], default="bf16",
+                    help="arithmetic of the M_PI transforms of the FP32 solve (model: the model's own)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the tiny-problem and differentiable-solve measurements")
     ap.add_argument("--no-masked-cr", action="store_true",
@@ -820,6 +822,9 @@ def main():
     P = build_problem(work, args.prec, seed_offset=rank)
     model = P["model"]
     n = model.nvec
+    PREC_CODES = {"model": -1, "bf16": cw.CMBWS_BF16, "tf32": cw.CMBWS_TF32, "fp32": cw.CMBWS_FP32}
+    pc_main = PREC_CODES[args.precond_prec] if args.prec == "fp32" else -1
+    cw.cmbws_model_set_precond_prec(model, pc_main)
     dev = torch.device("cuda")
     x = torch.zeros(n, dtype=torch.float64, device=dev)
     b = torch.zeros(n, dtype=torch.float64, device=dev)
@@ -948,8 +953,10 @@ def main():
                 mt.close()
             except Exception as e:  # noqa: BLE001
                 tc_solves[name] = {"error": f"{type(e).__name__}: {e}"[:300]}
-        # FP32 A with the preconditioner's synthesis on the tensor cores
-        for name, pc in (("fp32_A_bf16_precond", cw.CMBWS_BF16), ("fp32_A_tf32_precond", cw.CMBWS_TF32)):
+        # FP32 A with the preconditioner's transforms in FP32, on the tensor cores in TF32
+        # (synthesis only) or in BF16 (synthesis and adjoint)
+        for name, pc in (("fp32_A_fp32_precond", -1), ("fp32_A_tf32_precond", cw.CMBWS_TF32),
+                         ("fp32_A_bf16_precond", cw.CMBWS_BF16)):
             try:
                 cw.cmbws_model_set_precond_prec(model, pc)
                 xt = torch.zeros(n, dtype=torch.float64, device=dev)
@@ -966,7 +973,7 @@ def main():
             except Exception as e:  # noqa: BLE001
                 tc_solves[name] = {"error": f"{type(e).__name__}: {e}"[:300]}
             finally:
-                cw.cmbws_model_set_precond_prec(model, -1)
+                cw.cmbws_model_set_precond_prec(model, pc_main)
 
     # the paper's comparison (Sec. 5): the same solve with the block-diagonal preconditioner
     mdiag = None
@@ -1036,11 +1043,17 @@ def main():
     line = {"metric": "Wiener solve time to 1e-6 residual", "value": round(t_step, 4), "unit": "s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(t_step * 1e3, 2), "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+f64" if args.prec == "fp32" else "f64",
+            "vs_baseline": None,
+            "dtype": ("f32+bf16+f64" if args.precond_prec == "bf16" else "f32+f64")
+                     if args.prec == "fp32" else "f64",
             "data": "synthetic",
             "config": {"workload": work.name, "ncomp": len(work.comps), "nobs": len(work.bands),
                        "band_nside": [b.n for b in work.bands], "lmax_comp": [c.lmax for c in work.comps],
                        "tol": args.tol, "inner_tol": args.inner_tol, "precond": "M_PI",
+                       "precond_arith": ({"model": "fp32", "bf16": "bf16 (tcgen05 synthesis and adjoint)",
+                                          "tf32": "tf32 synthesis (tcgen05), fp32 adjoint",
+                                          "fp32": "fp32"}[args.precond_prec]
+                                         if args.prec == "fp32" else "fp64"),
                        "arithmetic": ("FP32 transforms, FP64 vectors/scalars, iterative refinement "
                                       f"certified by FP64-accurate ({cert}) applies"
                                       if args.prec == "fp32" else "FP64"),
