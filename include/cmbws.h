@@ -307,15 +307,38 @@ int cmbws_rhs(cmbws_model m, const double* const* d, const double* const* omega1
  *   x, lambda: device stacked vectors.  d, omega1: host arrays [nobs] of device maps
  *   (omega1 may be NULL); omega2: device stacked vector or NULL.
  *   out: device array of nobs * ncomp + ncomp doubles, written.
+ * For a pair (nu, k) with a spatially variable mixing map (Eq. Q), out[nu * ncomp + k]
+ * is the derivative in a uniform offset added to the map: the sum over its pixels of
+ * cmbws_grad_mix_maps.
  * The transforms run FP64-accurate (FP64 for FP64 models, CMBWS_FP32X2 otherwise);
  * the sums are reduced in a fixed order.  Uses the model's workspaces: calls on one
  * model must not overlap.
- * Errors: CMBWS_ERR_ARG for models with spatially variable mixing (the gradient with
- * respect to a mixing map is not provided) or NULL arguments.
+ * Errors: CMBWS_ERR_ARG for NULL arguments or a sharded model.
  */
 int cmbws_grad_terms(cmbws_model m, const double* x, const double* lambda,
                      const double* const* d, const double* const* omega1, const double* omega2,
                      double* out, void* stream);
+
+/*
+ * Gradient of a loss of the solution with respect to the pixel values of the spatially
+ * variable mixing maps (Eq. Q: Q~_{nu,k} = Y_nu^T W diag(q_{nu,k}) Y_k on the pair's
+ * mixing grid).  With the same lambda, u_nu = B_nu Y_nu^T (N^-1 d + N^-1/2 omega1 - N^-1 P x)
+ * and v_nu = B_nu Y_nu^T N^-1 P lambda as in cmbws_grad_terms,
+ *   dL/dq_{nu,k}(p) = w_p [ (Y lambda_k)(p) (Y u_nu)(p) - (Y x_k)(p) (Y v_nu)(p) ],
+ * the syntheses on the mixing grid (band-limits L_k and L_nu), w_p its pixel weight.  A
+ * spectral-index map beta_k(p) with q = (nu / nu_0)^beta follows by the chain rule.
+ *   x, lambda: device stacked vectors.  d, omega1: host arrays [nobs] of device maps
+ *   (omega1 may be NULL).
+ *   out: host array [nobs * ncomp] of device pointers; entry nu * ncomp + k receives the
+ *   gradient map of a variable pair (npix of its mixing grid, in the grid's pixel order);
+ *   NULL entries and entries of scalar pairs are not written.
+ * FP64-accurate transforms as in cmbws_grad_terms; the model's workspaces are used.
+ * Errors: CMBWS_ERR_ARG for NULL arguments, a sharded model or a model without variable
+ * mixing.
+ */
+int cmbws_grad_mix_maps(cmbws_model m, const double* x, const double* lambda,
+                        const double* const* d, const double* const* omega1, double* const* out,
+                        void* stream);
 
 /*
  * Data-model projection d_nu = P_nu x = Y_nu B_nu sum_k Q~_{nu,k} x_k (Eq. P), e.g. to

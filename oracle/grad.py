@@ -185,7 +185,8 @@ def grad_mix_maps_dense(model, x, lam, d, omega1=None):
     - P^T N^-1 dP_p x)."""
     if model.mix_map is None:
         return {}
-    P = _model.dense_P(model)
+    px = _model.project(model, x)      # P x and P lambda (the model itself, not its derivative)
+    pl = _model.project(model, lam)
     r = _data_maps(model, d, omega1)
     o = model.comp_offsets()
     out = {}
@@ -193,7 +194,7 @@ def grad_mix_maps_dense(model, x, lam, d, omega1=None):
         Ln = model.lmax_band[nu]
         tau = model.tau[nu]
         Yb = _sht.dense_Y(model.grids[nu], Ln) * model.beam[nu][_alm.ell_of_index(Ln)][None, :]
-        Px, Pl = P[nu] @ x, P[nu] @ lam
+        Px, Pl = px[nu], pl[nu]
         for k in range(model.ncomp):
             if not model.variable(nu, k):
                 continue

@@ -98,6 +98,8 @@ def load_library(path=None):
     lib.cmbws_rhs.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp, vp, vp]
     lib.cmbws_project.argtypes = [vp, vp, ctypes.POINTER(vp), vp]
     lib.cmbws_grad_terms.argtypes = [vp, vp, vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp, vp, vp]
+    lib.cmbws_grad_mix_maps.argtypes = [vp, vp, vp, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                        ctypes.POINTER(vp), vp]
     lib.cmbws_model_add_mask_precond.argtypes = [vp, i, i, vp, i, vp]
     lib.cmbws_apply_M_add.argtypes = [vp, vp, vp, vp]
     lib.cmbws_apply_M_diag.argtypes = [vp, vp, vp, vp]
@@ -334,7 +336,10 @@ def cmbws_model_create(lmax_comp, band_grids, beams, cls, ninv, mix_scalar, prec
     h = ctypes.c_void_p()
     _check(load_library().cmbws_model_create(ctypes.byref(desc), int(prec), _stream(stream),
                                              ctypes.byref(h)))
-    return Model(h, list(band_grids) + extra_grids, lmax_comp, nobs=nobs)
+    mdl = Model(h, list(band_grids) + extra_grids, lmax_comp, nobs=nobs)
+    mdl.mix_grids = ([[None if mix_maps[nu][k] is None else mix_grids[nu][k] for k in range(ncomp)]
+                      for nu in range(nobs)] if mix_maps is not None else None)
+    return mdl
 
 
 def cmbws_model_destroy(model):
@@ -488,6 +493,32 @@ def cmbws_grad_terms(model, x, lam, d, out, omega1=None, omega2=None, stream=Non
     _check(load_library().cmbws_grad_terms(model.handle, _dptr(x, model.nvec, "x"),
                                            _dptr(lam, model.nvec, "lam"), dp, w1, w2,
                                            _dptr(out, nobs * ncomp + ncomp, "out"), _stream(stream)))
+
+
+def cmbws_grad_mix_maps(model, x, lam, d, out, omega1=None, stream=None):
+    """out[nu][k] (CUDA float64 of the mixing grid's npix, or None) <- dL/dq_{nu,k}(p) of every
+    variable pair, given the solution x and the adjoint solution lam (A lam = dL/dx)."""
+    nobs, ncomp = model.nobs, len(model.lmax_comp)
+    mg = getattr(model, "mix_grids", None)
+    dp = (ctypes.c_void_p * nobs)(*[_dptr(d[nu], model.grids[nu].npix, f"d[{nu}]").value
+                                    for nu in range(nobs)])
+    if omega1 is not None:
+        w1 = (ctypes.c_void_p * nobs)(*[_dptr(omega1[nu], model.grids[nu].npix, f"omega1[{nu}]").value
+                                        for nu in range(nobs)])
+    else:
+        w1 = ctypes.POINTER(ctypes.c_void_p)()
+    op = (ctypes.c_void_p * (nobs * ncomp))()
+    for nu in range(nobs):
+        for k in range(ncomp):
+            t = out[nu][k]
+            if t is None:
+                continue
+            if mg is None or mg[nu][k] is None:
+                raise ValueError(f"out[{nu}][{k}]: pair ({nu}, {k}) has scalar mixing")
+            op[nu * ncomp + k] = _dptr(t, mg[nu][k].npix, f"out[{nu}][{k}]").value
+    _check(load_library().cmbws_grad_mix_maps(model.handle, _dptr(x, model.nvec, "x"),
+                                              _dptr(lam, model.nvec, "lam"), dp, w1, op,
+                                              _stream(stream)))
 
 
 def cmbws_model_add_mask_precond(model, comp, nside, mask, max_bottom=400, stream=None):

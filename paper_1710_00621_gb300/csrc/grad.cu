@@ -14,6 +14,15 @@
 // Cost: two projections (Nobs syntheses each) and two adjoint passes (Nobs each), all
 // FP64-accurate (FP64 transforms for FP64 models, double-float otherwise), plus
 // harmonic-space dot products reduced in a fixed order.
+//
+// Spatially variable mixing (Eq. Q, Q~ = Y_nu^T W diag(q) Y_k on the pair's mixing grid):
+// the derivative in the map value at pixel p is
+//
+//   dq_{nu,k}(p) = w_p [ (Y lambda_k)(p) (Y B_nu u_nu)(p) - (Y x_k)(p) (Y B_nu v_nu)(p) ]
+//
+// with u_nu, v_nu the band outputs of the two adjoint passes above, so each pass adds two
+// syntheses per variable pair on its mixing grid and a pixel product.  The scalar entry of a
+// variable pair is the derivative in a uniform offset of its map, the sum over its pixels.
 #include "model.h"
 
 namespace cmbws {
@@ -102,6 +111,43 @@ k_grad_prior(HarmDev h, int k, const double* __restrict__ lam, const double* __r
   if (threadIdx.x == 0) part[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = s;
 }
 
+// Mixing-map gradient of group pair j: out[j][i] (+)= sign w_ring a[j][i] b[j][i] over the
+// pixels of ring blockIdx.x, and the ring's partial sum of the result
+__global__ void __launch_bounds__(256)
+k_grad_mixmap(const double* __restrict__ a, const double* __restrict__ b,
+              const int64_t* __restrict__ roff, const double* __restrict__ rw, int64_t npix,
+              int nring, double sign, int accumulate, double* __restrict__ out,
+              double* __restrict__ part) {
+  __shared__ double sh[256 / 32];
+  const int r = blockIdx.x, j = blockIdx.y;
+  const double w = rw[r];
+  double sum = 0.0;
+  for (int64_t i = roff[r] + threadIdx.x; i < roff[r + 1]; i += blockDim.x) {
+    const int64_t q = (int64_t)j * npix + i;
+    double v = sign * w * a[q] * b[q];
+    if (accumulate) v += out[q];
+    out[q] = v;
+    sum += v;
+  }
+  const double s = block_sum(sum, sh);
+  if (threadIdx.x == 0) part[(int64_t)j * nring + r] = s;
+}
+
+struct MixOut {
+  int idx[kMaxMaps];  // entry of the pair in the gradient terms (nu ncomp + k)
+};
+
+// terms[idx[j]] = sum over rings of part[j][r], in a fixed order
+__global__ void k_grad_mixsum(const double* __restrict__ part, int nring, MixOut mo,
+                              double* __restrict__ terms) {
+  __shared__ double sh[256 / 32];
+  const int j = blockIdx.x;
+  double v = 0.0;
+  for (int r = threadIdx.x; r < nring; r += blockDim.x) v += part[(int64_t)j * nring + r];
+  const double s = block_sum(v, sh);
+  if (threadIdx.x == 0) terms[mo.idx[j]] = s;
+}
+
 // out[k] (+)= sign * sum_b part[b * stride + k], k < nk, in a fixed order
 __global__ void k_grad_finish(const double* __restrict__ part, int64_t nblk, int stride, int nk,
                               double sign, int accumulate, double* __restrict__ out) {
@@ -116,14 +162,27 @@ __global__ void k_grad_finish(const double* __restrict__ part, int64_t nblk, int
 
 }  // namespace
 
-static int grad_terms(Model& M, const double* x, const double* lam, const double* const* d,
-                      const double* const* w1, const double* w2, double* out, cudaStream_t s) {
-  if (M.nmix) {
-    set_error("cmbws_grad_terms: the model has spatially variable mixing; the gradient terms "
-              "are defined for scalar mixing");
-    return CMBWS_ERR_ARG;
-  }
+// out: the gradient terms (nobs ncomp + ncomp) or nullptr; maps: per pair nu ncomp + k the
+// mixing-map gradient of a variable pair (nullptr entries, or maps == nullptr, are skipped)
+static int grad_run(Model& M, const double* x, const double* lam, const double* const* d,
+                    const double* const* w1, const double* w2, double* out, double* const* maps,
+                    cudaStream_t s) {
   const int ap = M.prec == CMBWS_FP64 ? CMBWS_FP64 : CMBWS_FP32X2;
+  // mixing groups: two scratch map sets of the largest group, the accumulated gradient of
+  // every variable pair and the per-ring partial sums
+  std::vector<int64_t> moff(M.mgroups.size() + 1, 0);
+  size_t scratch = 0, part_mix = 1;
+  for (size_t gi = 0; gi < M.mgroups.size(); ++gi) {
+    const Group& G = M.mgroups[gi];
+    moff[gi + 1] = moff[gi] + (int64_t)G.nmaps * G.grid->npix;
+    scratch = std::max(scratch, (size_t)G.nmaps * G.grid->npix);
+    part_mix = std::max(part_mix, (size_t)G.nmaps * G.grid->nring);
+  }
+  if (M.nmix) {
+    CMBWS_TRY(M.gradmix.ensure(2 * scratch * 8));
+    CMBWS_TRY(M.gradmixout.ensure((size_t)moff.back() * 8));
+    CMBWS_TRY(M.gradmixpart.ensure(part_mix * 8));
+  }
   const HarmDev h = M.harm();
   // band maps, laid out group by group so that a group's maps are contiguous
   std::vector<double*> mp(M.nobs, nullptr);
@@ -167,18 +226,48 @@ static int grad_terms(Model& M, const double* x, const double* lam, const double
     }
     M.n_sht += M.nobs;
     const double* other = pass == 0 ? lam : x;
-    for (int nu = 0; nu < M.nobs; ++nu) {
-      const int Ln = bd.L[nu];
-      dim3 grd((Ln + kDotNT) / kDotNT, Ln + 1);
+    if (out)
+      for (int nu = 0; nu < M.nobs; ++nu) {
+        const int Ln = bd.L[nu];
+        dim3 grd((Ln + kDotNT) / kDotNT, Ln + 1);
+        ProfScope ps(PROF_HARM, s, 1);
+        k_grad_dot<<<grd, kDotNT, 0, s>>>(h, bd.out[nu], Ln, M.d_beam.as<double>() + M.beam_off_h[nu],
+                                          other, part);
+        CMBWS_LAUNCH_CHECK();
+        k_grad_finish<<<M.ncomp, 256, 0, s>>>(part, (int64_t)grd.x * grd.y, M.ncomp, M.ncomp,
+                                              pass == 0 ? 1.0 : -1.0, pass, out + nu * M.ncomp);
+        CMBWS_LAUNCH_CHECK();
+      }
+    // variable pairs: w (Y other_k) (Y B_nu u_nu), added (pass 0) or subtracted (pass 1); after
+    // the last pass each map is final, its sum replaces the scalar formula's entry
+    for (size_t gi = 0; gi < M.mgroups.size(); ++gi) {
+      Group& G = M.mgroups[gi];
+      const Grid& g = *G.grid;
+      double* ma = M.gradmix.as<double>();
+      double* mb = ma + scratch;
+      CMBWS_TRY(M.mixvar_maps_comp(G, ap, other, ma, s));
+      CMBWS_TRY(M.mixvar_maps_band(G, ap, mb, s));
       ProfScope ps(PROF_HARM, s, 1);
-      k_grad_dot<<<grd, kDotNT, 0, s>>>(h, bd.out[nu], Ln, M.d_beam.as<double>() + M.beam_off_h[nu],
-                                        other, part);
+      k_grad_mixmap<<<dim3(g.nring, G.nmaps), 256, 0, s>>>(
+          ma, mb, g.ring_off.as<int64_t>(), g.ring_w64.as<double>(), g.npix, g.nring,
+          pass == 0 ? 1.0 : -1.0, pass, M.gradmixout.as<double>() + moff[gi], M.gradmixpart.as<double>());
       CMBWS_LAUNCH_CHECK();
-      k_grad_finish<<<M.ncomp, 256, 0, s>>>(part, (int64_t)grd.x * grd.y, M.ncomp, M.ncomp,
-                                            pass == 0 ? 1.0 : -1.0, pass, out + nu * M.ncomp);
-      CMBWS_LAUNCH_CHECK();
+      if (pass == 0) continue;
+      if (out) {
+        MixOut mo{};
+        for (int j = 0; j < G.nmaps; ++j) mo.idx[j] = G.bands[j];  // pair id nu ncomp + k
+        k_grad_mixsum<<<G.nmaps, 256, 0, s>>>(M.gradmixpart.as<double>(), g.nring, mo, out);
+        CMBWS_LAUNCH_CHECK();
+      }
+      if (maps)
+        for (int j = 0; j < G.nmaps; ++j)
+          if (maps[G.bands[j]])
+            CMBWS_CUDA(cudaMemcpyAsync(maps[G.bands[j]],
+                                       M.gradmixout.as<double>() + moff[gi] + (int64_t)j * g.npix,
+                                       (size_t)g.npix * 8, cudaMemcpyDeviceToDevice, s));
     }
   }
+  if (!out) return CMBWS_OK;
   for (int k = 0; k < M.ncomp; ++k) {
     dim3 grd((M.Lk[k] + kDotNT) / kDotNT, M.Lk[k] + 1);
     ProfScope ps(PROF_HARM, s, 1);
@@ -210,5 +299,27 @@ extern "C" int cmbws_grad_terms(cmbws_model mh, const double* x, const double* l
       set_error("cmbws_grad_terms: missing map for band %d", nu);
       return CMBWS_ERR_ARG;
     }
-  return grad_terms(*M, x, lambda, d, omega1, omega2, out, (cudaStream_t)stream);
+  return grad_run(*M, x, lambda, d, omega1, omega2, out, nullptr, (cudaStream_t)stream);
+}
+
+extern "C" int cmbws_grad_mix_maps(cmbws_model mh, const double* x, const double* lambda,
+                                   const double* const* d, const double* const* omega1,
+                                   double* const* out, void* stream) {
+  clear_error();
+  Model* M = as_model(mh);
+  if (refuse_sharded(M, "cmbws_grad_mix_maps")) return CMBWS_ERR_ARG;
+  if (!M || !x || !lambda || !d || !out) {
+    set_error("cmbws_grad_mix_maps: invalid arguments");
+    return CMBWS_ERR_ARG;
+  }
+  for (int nu = 0; nu < M->nobs; ++nu)
+    if (!d[nu] || (omega1 && !omega1[nu])) {
+      set_error("cmbws_grad_mix_maps: missing map for band %d", nu);
+      return CMBWS_ERR_ARG;
+    }
+  if (!M->nmix) {
+    set_error("cmbws_grad_mix_maps: the model has no spatially variable mixing");
+    return CMBWS_ERR_ARG;
+  }
+  return grad_run(*M, x, lambda, d, omega1, nullptr, nullptr, out, (cudaStream_t)stream);
 }

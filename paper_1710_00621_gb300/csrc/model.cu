@@ -527,6 +527,39 @@ int Model::mixvar_adjoint(int prec, cudaStream_t s) {
   return CMBWS_OK;
 }
 
+int Model::mixvar_maps_comp(Group& G, int prec, const double* x, double* maps, cudaStream_t s) {
+  const HarmDev h = harm();
+  const MixGroupDev mg = mix_dev(G, ncomp);
+  dim3 grd((mg.L + 1 + 127) / 128, mg.L + 1);
+  {
+    ProfScope ps(PROF_HARM, s, is_f32(prec) ? 0 : 1);
+    if (!is_f32(prec)) k_mixvar_fwd_in<double2><<<grd, 128, 0, s>>>(h, mg, x);
+    else k_mixvar_fwd_in<float2><<<grd, 128, 0, s>>>(h, mg, x);
+    CMBWS_LAUNCH_CHECK();
+  }
+  CMBWS_TRY(legendre_synth(*G.grid, prec, G.nmaps, G.alm.p, G.F.p, s));
+  CMBWS_TRY(ringfft_synth(*G.grid, prec, G.nmaps, G.F.p, maps, s));
+  n_sht += G.nmaps;
+  return CMBWS_OK;
+}
+
+int Model::mixvar_maps_band(Group& G, int prec, double* maps, cudaStream_t s) {
+  const HarmDev h = harm();
+  const BandDev bd = bands_dev(prec);
+  const MixGroupDev mg = mix_dev(G, ncomp);
+  dim3 grd((mg.L + 1 + 127) / 128, mg.L + 1);
+  {
+    ProfScope ps(PROF_HARM, s, is_f32(prec) ? 0 : 1);
+    if (!is_f32(prec)) k_mixvar_adj_in<double2><<<grd, 128, 0, s>>>(h, bd, mg);
+    else k_mixvar_adj_in<float2><<<grd, 128, 0, s>>>(h, bd, mg);
+    CMBWS_LAUNCH_CHECK();
+  }
+  CMBWS_TRY(legendre_synth(*G.grid, prec, G.nmaps, G.alm.p, G.F.p, s));
+  CMBWS_TRY(ringfft_synth(*G.grid, prec, G.nmaps, G.F.p, maps, s));
+  n_sht += G.nmaps;
+  return CMBWS_OK;
+}
+
 int Model::mix_forward(Group& G, int prec, const double* x, cudaStream_t s) {
   const HarmDev h = harm();
   GroupDev gd{};

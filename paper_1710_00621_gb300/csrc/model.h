@@ -104,6 +104,7 @@ struct Model {
 
   // gradient-term workspace (grad.cu): band maps and per-block partial sums
   DevMem gradmaps, gradpart;
+  DevMem gradmix, gradmixout, gradmixpart;  // mixing-map gradients (grad.cu)
 
   // CG workspace (cg.cu)
   DevMem cg_r, cg_z, cg_p, cg_q, cg_d, cg_x, cg_red;
@@ -186,6 +187,10 @@ struct Model {
   int mix_chain(Group& G, int prec, cudaStream_t s);
   int mixvar_forward(int prec, const double* x, cudaStream_t s);
   int mixvar_adjoint(int prec, cudaStream_t s);
+  // pixel maps on mixing group G's grid ([pair][npix], FP64) of x_{k_j} (comp) or of the band
+  // outputs times the beam, B_nu u_nu (band), synthesized in arithmetic prec
+  int mixvar_maps_comp(Group& G, int prec, const double* x, double* maps, cudaStream_t s);
+  int mixvar_maps_band(Group& G, int prec, double* maps, cudaStream_t s);
   int mix_forward(Group& G, int prec, const double* x, cudaStream_t s);
   int project(const double* x, double* const* d, int prec, cudaStream_t s);
   int apply_A(const double* x, double* y, int prec, cudaStream_t s);

@@ -51,23 +51,110 @@ def test_grad_terms_parity(L, cr, prec):
     assert rel_err(g[m.nobs * m.ncomp:], dt0) < 1e-13
 
 
-def test_grad_terms_rejects_variable_mixing():
+def _var_inputs(L, Lmix, cr=False):
+    """The differentiable workload with the dust pair of every band on a variable mixing map
+    (a smooth pattern around the scalar value) on a Gauss-Legendre mixing grid of band-limit
+    Lmix, and band maps drawn from that model."""
+    from oracle import grids as og
+    w, m0, inp, _, o1, o2 = _inputs(L, cr)
+    g = og.gauss_legendre(Lmix)
+    th, ph = g.pixel_angles()
+    k = 2
+    lm = [[None] * m0.ncomp for _ in range(m0.nobs)]
+    maps = [[None] * m0.ncomp for _ in range(m0.nobs)]
+    for nu in range(m0.nobs):
+        maps[nu][k] = m0.q[nu, k] * (1.0 + 0.4 * np.cos(th) + 0.2 * np.sin(th) * np.cos(ph + nu))
+        lm[nu][k] = Lmix
+    grids = [[g if maps[nu][j] is not None else None for j in range(m0.ncomp)] for nu in range(m0.nobs)]
+    m = omodel.Model(**{**m0.__dict__, "mix_map": maps, "mix_grid": grids})
+    d = [a + n for a, n in zip(omodel.project(m, inp["x_true"]), inp["noise"])]
+    return w, m, inp, d, o1, o2, (lm, maps)
+
+
+@pytest.mark.parametrize("cr", [False, True])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_grad_variable_mixing_parity(prec, cr):
+    """cmbws_grad_terms (offset entries of the variable pairs) and cmbws_grad_mix_maps against
+    the oracle's operator forms on the same x, lambda, d."""
     import paper_1710_00621_gb300 as cw
     import torch
-    w = skygen.tiny_plain()
-    for b in w.bands:
-        b.n = b.lmax = 15
-    for c in w.comps:
-        c.lmax = 15
-    m, inp = oracle_model(w)
-    maps = [[None, np.ones(16 * 31)] for _ in w.bands]
-    lm = [[None, 15] for _ in w.bands]
-    gm, _ = gpu_model(w, inp, cw.CMBWS_FP64, mix=(lm, maps))
-    x = torch.zeros(m.nvec(), dtype=torch.float64, device="cuda")
+    w, m, inp, d, o1, o2, mix = _var_inputs(15, 20, cr)
+    p = cw.CMBWS_FP64 if prec == "fp64" else cw.CMBWS_FP32
+    gm, _ = gpu_model(w, inp, p, mix=mix)
+    rng = np.random.default_rng(19)
+    x = rng.standard_normal(m.nvec())
+    lam = rng.standard_normal(m.nvec())
+    dq0, dt0 = ograd.grad_terms(m, x, lam, d, o1, o2)
+    maps0 = ograd.grad_mix_maps(m, x, lam, d, o1)
     out = torch.empty(m.nobs * m.ncomp + m.ncomp, dtype=torch.float64, device="cuda")
-    d = [torch.zeros(t.size, dtype=torch.float64, device="cuda") for t in m.tau]
-    with pytest.raises(cw.CmbwsError):
-        cw.cmbws_grad_terms(gm, x, x, d, out)
+    dd = [to_dev(a) for a in d]
+    w1 = [to_dev(a) for a in o1] if cr else None
+    cw.cmbws_grad_terms(gm, to_dev(x), to_dev(lam), dd, out, w1, to_dev(o2) if cr else None)
+    g = to_host(out)
+    assert rel_err(g[:m.nobs * m.ncomp].reshape(m.nobs, m.ncomp), dq0) < 1e-11
+    assert rel_err(g[m.nobs * m.ncomp:], dt0) < 1e-13
+    outm = [[None if (nu, k) not in maps0 else torch.zeros(maps0[(nu, k)].size, dtype=torch.float64,
+                                                          device="cuda")
+             for k in range(m.ncomp)] for nu in range(m.nobs)]
+    cw.cmbws_grad_mix_maps(gm, to_dev(x), to_dev(lam), dd, outm, w1)
+    for (nu, k), ref in maps0.items():
+        assert rel_err(to_host(outm[nu][k]), ref) < 1e-11, (nu, k)
+    # the sum of each map is its offset entry
+    for (nu, k), ref in maps0.items():
+        assert abs(to_host(outm[nu][k]).sum() - g[nu * m.ncomp + k]) <= 1e-12 * np.abs(ref).sum()
+    # a model without variable mixing is refused
+    gs, _ = gpu_model(w, inp, p)
+    with pytest.raises(cw.CmbwsError) as e:
+        cw.cmbws_grad_mix_maps(gs, to_dev(x), to_dev(lam), dd, [[None] * m.ncomp for _ in range(m.nobs)])
+    assert e.value.code == -1
+
+
+def test_mixing_map_gradient_l31_dense_oracle_and_central_differences():
+    """A variable-map model at L = 31 (mixing grid L = 40): the GPU solves x and lambda for the
+    loss ||W x||^2 in FP64; the mixing-map gradient equals the oracle's dense form on those
+    vectors, and central differences of the GPU loss in single map pixels (pole, equator, mid
+    latitudes; two bands, the model rebuilt each time) match it."""
+    import paper_1710_00621_gb300 as cw
+    import torch
+    w, m, inp, d, _, _, (lm, maps) = _var_inputs(31, 40)
+    wgt = skygen.harmonic_weight(m.lmax_comp)
+    dd = [to_dev(a) for a in d]
+    cache = GridCache()
+
+    def solve(mp):
+        gm, _ = gpu_model(w, inp, cw.CMBWS_FP64, cache=cache, mix=(lm, mp))
+        b = torch.zeros(m.nvec(), dtype=torch.float64, device="cuda")
+        cw.cmbws_rhs(gm, dd, b)
+        x = torch.zeros_like(b)
+        rep = cw.cmbws_cg_solve(gm, b, x, tol=1e-13, maxiter=5000)
+        assert rep["rel_res"] <= 1e-13
+        xh = to_host(x)
+        return gm, xh, float(np.sum((wgt * xh) ** 2))
+
+    gm, x, L0 = solve(maps)
+    gl = to_dev(2.0 * wgt * wgt * x)
+    lam = torch.zeros_like(gl)
+    cw.cmbws_cg_solve(gm, gl, lam, tol=1e-13, maxiter=5000)
+    lam = to_host(lam)
+    outm = [[None if maps[nu][k] is None else torch.zeros(maps[nu][k].size, dtype=torch.float64,
+                                                         device="cuda")
+             for k in range(m.ncomp)] for nu in range(m.nobs)]
+    cw.cmbws_grad_mix_maps(gm, to_dev(x), to_dev(lam), dd, outm)
+    ref = ograd.grad_mix_maps_dense(m, x, lam, d)
+    for (nu, k), r in ref.items():
+        assert rel_err(to_host(outm[nu][k]), r) < 1e-10, (nu, k, rel_err(to_host(outm[nu][k]), r))
+    npix = maps[0][2].size
+    for nu in (0, 3):
+        gmap = to_host(outm[nu][2])
+        for p in (0, npix // 2, npix // 3 + 7, npix - 1):
+            h = 1e-4 * abs(maps[nu][2][p])
+            vals = []
+            for sgn in (+1, -1):
+                mp = [[None if q is None else q.copy() for q in row] for row in maps]
+                mp[nu][2][p] += sgn * h
+                vals.append(solve(mp)[2])
+            fd = (vals[0] - vals[1]) / (2 * h)
+            assert abs(fd - gmap[p]) <= 1e-5 * max(abs(fd), 1e-3 * np.abs(gmap).max()), (nu, p, fd, gmap[p])
 
 
 def _problem(w, inp, d, prec, tol, cache):
