@@ -1,7 +1,9 @@
 """Differentiable Wiener / CR solve: a torch.autograd.Function over the library's solver.
 
 The solution x of A(theta) x = b(theta) (Eq. A) is a function of the scalar mixing
-matrix q_{nu,k} (Eq. P with constant mixing) and of the prior spectra; here the prior
+matrix q_{nu,k} (Eq. P with constant mixing), of spatially variable mixing maps q_{nu,k}(p)
+(Eq. Q, ``wiener_solution_maps``, gradients by ``cmbws_grad_mix_maps``) and of the prior
+spectra; here the prior
 of component k is parametrised by a log-scale t_k, C_{k,l} = exp(t_k) C0_{k,l}.  The
 backward pass runs one more solve, A lambda = dL/dx (A is symmetric), and evaluates
 lambda^T (db/dtheta - dA/dtheta x) with ``cmbws_grad_terms``.  Spectral indices and
@@ -41,6 +43,7 @@ class WienerProblem:
     maxiter: int = 2000
     inner_tol: float = 1e-3
     cert_prec: Optional[int] = None
+    mix_grids: Optional[list] = None   # [nobs][ncomp] mixing Grid of a variable pair, or None
 
     @property
     def nobs(self):
@@ -50,12 +53,15 @@ class WienerProblem:
     def ncomp(self):
         return len(self.lmax_comp)
 
-    def model(self, q, t):
-        """cmbws model for mixing q [nobs, ncomp] and prior log-scales t [ncomp] (host arrays)."""
+    def model(self, q, t, mix_maps=None):
+        """cmbws model for mixing q [nobs, ncomp] and prior log-scales t [ncomp] (host arrays),
+        with the variable pairs' maps mix_maps [nobs][ncomp] (CUDA float64 or None)."""
         cls = [None if c is None else np.asarray(c, dtype=np.float64) * float(np.exp(t[k]))
                for k, c in enumerate(self.cl0)]
         return B.cmbws_model_create(list(self.lmax_comp), self.grids, self.beams, cls, self.ninv,
-                                    np.asarray(q, dtype=np.float64), prec=self.prec)
+                                    np.asarray(q, dtype=np.float64), prec=self.prec,
+                                    mix_grids=self.mix_grids if mix_maps is not None else None,
+                                    mix_maps=mix_maps)
 
     def solve(self, model, b, tol):
         x = torch.zeros_like(b)
@@ -98,6 +104,60 @@ class WienerSolution(torch.autograd.Function):
         qd, qdev, qs = ctx.q_meta
         td, tdev, ts = ctx.t_meta
         return gq.to(device=qdev, dtype=qd).reshape(qs), gt.to(device=tdev, dtype=td).reshape(ts), None
+
+
+class WienerSolutionMaps(torch.autograd.Function):
+    """x = A(q, t, maps)^-1 b(q, t, maps); differentiable in q, t and the mixing maps of the
+    variable pairs (one tensor per pair, in the order of ``pairs``)."""
+
+    @staticmethod
+    def forward(ctx, q, t, prob, pairs, *maps):
+        qh = q.detach().double().cpu().numpy().reshape(prob.nobs, prob.ncomp)
+        th = t.detach().double().cpu().numpy().reshape(prob.ncomp)
+        mm = [[None] * prob.ncomp for _ in range(prob.nobs)]
+        for (nu, k), mp in zip(pairs, maps):
+            mm[nu][k] = mp.detach().to(dtype=torch.float64).contiguous()
+        model = prob.model(qh, th, mm)
+        dev = prob.d[0].device
+        b = torch.empty(model.nvec, dtype=torch.float64, device=dev)
+        B.cmbws_rhs(model, prob.d, b, prob.omega1, prob.omega2)
+        x, rep = prob.solve(model, b, prob.tol)
+        ctx.prob, ctx.model, ctx.report, ctx.pairs = prob, model, rep, pairs
+        ctx.save_for_backward(x)
+        ctx.q_meta = (q.dtype, q.device, q.shape)
+        ctx.t_meta = (t.dtype, t.device, t.shape)
+        ctx.m_meta = [(mp.dtype, mp.device, mp.shape) for mp in maps]
+        return x
+
+    @staticmethod
+    def backward(ctx, gx):
+        (x,) = ctx.saved_tensors
+        prob, model = ctx.prob, ctx.model
+        lam, rep = prob.solve(model, gx.contiguous().double(), prob.adjoint_tol or prob.tol)
+        ctx.adjoint_report = rep
+        out = torch.empty(prob.nobs * prob.ncomp + prob.ncomp, dtype=torch.float64, device=x.device)
+        B.cmbws_grad_terms(model, x, lam, prob.d, out, prob.omega1, prob.omega2)
+        gm = [[None] * prob.ncomp for _ in range(prob.nobs)]
+        for (nu, k), (dt, dv, sh) in zip(ctx.pairs, ctx.m_meta):
+            gm[nu][k] = torch.empty(sh, dtype=torch.float64, device=x.device).reshape(-1)
+        B.cmbws_grad_mix_maps(model, x, lam, prob.d, gm, prob.omega1)
+        gq = out[:prob.nobs * prob.ncomp].reshape(prob.nobs, prob.ncomp).clone()
+        for nu, k in ctx.pairs:  # the scalar entry of a variable pair is not a parameter here
+            gq[nu, k] = 0.0
+        gt = out[prob.nobs * prob.ncomp:]
+        qd, qdev, qs = ctx.q_meta
+        td, tdev, ts = ctx.t_meta
+        gmaps = [gm[nu][k].to(device=dv, dtype=dt).reshape(sh)
+                 for (nu, k), (dt, dv, sh) in zip(ctx.pairs, ctx.m_meta)]
+        return (gq.to(device=qdev, dtype=qd).reshape(qs), gt.to(device=tdev, dtype=td).reshape(ts),
+                None, None, *gmaps)
+
+
+def wiener_solution_maps(q, t, maps, prob: WienerProblem):
+    """Differentiable solution x(q, t, maps); maps: [nobs][ncomp] CUDA tensors on the pairs'
+    mixing grids (prob.mix_grids) or None for scalar pairs (which take q)."""
+    pairs = [(nu, k) for nu in range(prob.nobs) for k in range(prob.ncomp) if maps[nu][k] is not None]
+    return WienerSolutionMaps.apply(q, t, prob, pairs, *[maps[nu][k] for nu, k in pairs])
 
 
 def wiener_solution(q, t, prob: WienerProblem):

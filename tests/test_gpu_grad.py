@@ -157,6 +157,53 @@ def test_mixing_map_gradient_l31_dense_oracle_and_central_differences():
             assert abs(fd - gmap[p]) <= 1e-5 * max(abs(fd), 1e-3 * np.abs(gmap).max()), (nu, p, fd, gmap[p])
 
 
+def test_spectral_index_map_autograd_central_differences():
+    """A spectral-index map beta(p) of the dust on its mixing grid, q_{nu,dust}(p) =
+    (nu / nu_0)^beta(p) in torch, through wiener_solution_maps: d||W x||^2 / dbeta(p) by
+    autograd against central differences of the same FP64 solves in single pixels."""
+    import paper_1710_00621_gb300 as cw
+    import torch
+    from paper_1710_00621_gb300.autodiff import WienerProblem, wiener_solution_maps
+    from oracle import grids as og
+    w, m, inp, d, _, _, (lm, maps) = _var_inputs(15, 20)
+    cache = GridCache()
+    g = og.gauss_legendre(20)
+    th, _ = g.pixel_angles()
+    mgrid = cw.cmbws_plan_grid(cw.CMBWS_GRID_GL, 21, 20)
+    k = 2
+    mix_grids = [[mgrid if j == k else None for j in range(m.ncomp)] for _ in range(m.nobs)]
+    prob = WienerProblem([c.lmax for c in w.comps], [cache.get(b) for b in w.bands], inp["beams"],
+                         inp["cl"], [to_dev(t) for t in inp["tau"]], [to_dev(a) for a in d],
+                         prec=cw.CMBWS_FP64, tol=1e-13, maxiter=5000, mix_grids=mix_grids)
+    freqs = torch.tensor([b.freq for b in w.bands], dtype=torch.float64, device="cuda")
+    nu0 = w.comps[k].nu0
+    beta0 = torch.as_tensor(w.comps[k].beta + 0.1 * np.cos(th), device="cuda")
+    wgt = to_dev(skygen.harmonic_weight(m.lmax_comp))
+    q = torch.as_tensor(m.q, device="cuda")
+    t = torch.zeros(m.ncomp, dtype=torch.float64, device="cuda")
+
+    def loss_of(beta):
+        mp = [[(freqs[nu] / nu0) ** beta if j == k else None for j in range(m.ncomp)]
+              for nu in range(m.nobs)]
+        x = wiener_solution_maps(q, t, mp, prob)
+        return ((wgt * x) ** 2).sum()
+
+    beta = beta0.clone().requires_grad_(True)
+    loss = loss_of(beta)
+    loss.backward()
+    gb = beta.grad.cpu().numpy()
+    h = 1e-5
+    with torch.no_grad():
+        for p in (0, th.size // 2, th.size // 3 + 4, th.size - 1):
+            vals = []
+            for sgn in (+1, -1):
+                bb = beta0.clone()
+                bb[p] += sgn * h
+                vals.append(float(loss_of(bb)))
+            fd = (vals[0] - vals[1]) / (2 * h)
+            assert abs(fd - gb[p]) <= 1e-5 * max(abs(fd), 1e-3 * np.abs(gb).max()), (p, fd, gb[p])
+
+
 def _problem(w, inp, d, prec, tol, cache):
     import paper_1710_00621_gb300 as cw
     from paper_1710_00621_gb300.autodiff import WienerProblem
