@@ -50,11 +50,17 @@ __global__ void k_dot_partial(const double* __restrict__ a, const double* __rest
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
-// x += alpha p; r -= alpha q; partial sums of r.r
-__global__ void k_update_xr(double* __restrict__ x, double* __restrict__ r,
-                            const double* __restrict__ p, const double* __restrict__ q, double alpha,
-                            int64_t n, double* __restrict__ partial) {
+// x += alpha p; r -= alpha q; partial sums of r.r, with alpha = rz / pq read from the device
+// (the PCG scalars stay on the device between the host's one read per iteration); alpha = 0
+// when p.q is not a positive finite number or r.z is not finite, and the host then reports the
+// breakdown with x, r unchanged.
+__global__ void k_update_xr_dev(double* __restrict__ x, double* __restrict__ r,
+                                const double* __restrict__ p, const double* __restrict__ q,
+                                const double* __restrict__ rz, const double* __restrict__ pq,
+                                int64_t n, double* __restrict__ partial) {
   __shared__ double sh[32];
+  const double a = *rz, b = *pq;
+  const double alpha = (b > 0.0 && isfinite(b) && isfinite(a)) ? a / b : 0.0;
   double s = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -67,8 +73,11 @@ __global__ void k_update_xr(double* __restrict__ x, double* __restrict__ r,
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
-// p = z + beta p
-__global__ void k_xpby(const double* __restrict__ z, double* __restrict__ p, double beta, int64_t n) {
+// p = z + (rz_new / rz_old) p, the ratio read from the device
+__global__ void k_xpby_dev(const double* __restrict__ z, double* __restrict__ p,
+                           const double* __restrict__ rz_new, const double* __restrict__ rz_old,
+                           int64_t n) {
+  const double beta = *rz_new / *rz_old;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     p[i] = z[i] + beta * p[i];
@@ -132,13 +141,35 @@ struct Comm {
   void* ctx;
 };
 
+// Device scalar slots after the reduction partials (red + kRedBlocks): 0 the last finished
+// sum, 1 p.q, 2 r.r, 3 + (it & 1) r.z of iteration it.
+constexpr int kScal = 8;
+constexpr int kSlotPQ = 1, kSlotRR = 2, kSlotRZ = 3;
+
 struct Solver {
   Model& M;
   cudaStream_t s;
   int64_t n;
-  double* red;     // [kRedBlocks + 1]
-  double* hscal;   // pinned host scalar
+  double* red;     // [kRedBlocks + kScal]
+  double* hscal;   // pinned host copy of the kScal scalar slots
   const Comm* comm = nullptr;
+
+  double* slot(int i) { return red + kRedBlocks + i; }
+  // sum of a . b into a device slot (no host synchronisation)
+  int dot_dev(const double* a, const double* b, double* out) {
+    ProfScope ps_(PROF_CG, s);
+    k_dot_partial<<<kRedBlocks, kRedThreads, 0, s>>>(a, b, n, red);
+    CMBWS_LAUNCH_CHECK();
+    k_finish<<<1, kRedThreads, 0, s>>>(red, kRedBlocks, out);
+    CMBWS_LAUNCH_CHECK();
+    return CMBWS_OK;
+  }
+  // the scalar slots, read back once (one host synchronisation)
+  int read_slots() {
+    CMBWS_CUDA(cudaMemcpyAsync(hscal, red + kRedBlocks, kScal * 8, cudaMemcpyDeviceToHost, s));
+    CMBWS_CUDA(cudaStreamSynchronize(s));
+    return CMBWS_OK;
+  }
 
   // sum a device vector of n doubles over the shards (no-op for unsharded solves)
   int reduce(double* v) {
@@ -339,15 +370,34 @@ static int pcg_core(Solver& S, int prec, int use_M, double* d, double* r, double
     CMBWS_TRY(S.dot(r, z, &rz));
     *rz_out = rz;
   }
-  for (int it = start.resume ? start.it0 : 0; it < maxit; ++it) {
+  // the PCG scalars stay on the device: r.z of iteration it in slot kSlotRZ + (it & 1), p.q
+  // and r.r in their slots; the host reads them once per iteration for the stopping test
+  const int it0 = start.resume ? start.it0 : 0;
+  S.hscal[kSlotRZ + (it0 & 1)] = rz;
+  CMBWS_CUDA(cudaMemcpyAsync(S.slot(kSlotRZ + (it0 & 1)), &S.hscal[kSlotRZ + (it0 & 1)], 8,
+                             cudaMemcpyHostToDevice, S.s));
+  for (int it = it0; it < maxit; ++it) {
     if (S.comm) {  // sharded: the partial A p, summed over the shards (no graphs)
       CMBWS_TRY(M.apply_A(p, q, prec, S.s));
       CMBWS_TRY(S.reduce(q));
     } else {
       CMBWS_TRY(run_op(M, OP_APPLY_A, prec, p, q, S.s, [&]() { return M.apply_A(p, q, prec, S.s); }));
     }
-    double pq;
-    CMBWS_TRY(S.dot(p, q, &pq));
+    double* rz_cur = S.slot(kSlotRZ + (it & 1));
+    double* rz_nxt = S.slot(kSlotRZ + ((it + 1) & 1));
+    CMBWS_TRY(S.dot_dev(p, q, S.slot(kSlotPQ)));
+    {
+      ProfScope ps_(PROF_CG, S.s);
+      k_update_xr_dev<<<kRedBlocks, kRedThreads, 0, S.s>>>(d, r, p, q, rz_cur, S.slot(kSlotPQ), n,
+                                                           S.red);
+      CMBWS_LAUNCH_CHECK();
+      k_finish<<<1, kRedThreads, 0, S.s>>>(S.red, kRedBlocks, S.slot(kSlotRR));
+      CMBWS_LAUNCH_CHECK();
+    }
+    CMBWS_TRY(S.read_slots());
+    const double pq = S.hscal[kSlotPQ];
+    rz = S.hscal[kSlotRZ + (it & 1)];
+    *rz_out = rz;
     if (!(pq > 0.0) || !std::isfinite(pq) || !std::isfinite(rz)) {
       // a bounded device-side wait that ran out leaves NaN in the operator's output
       bool timed_out = false;
@@ -358,13 +408,7 @@ static int pcg_core(Solver& S, int prec, int use_M, double* d, double* r, double
       set_error("CG breakdown: p.Ap = %g, r.z = %g at iteration %d", pq, rz, it);
       return CMBWS_ERR_BREAKDOWN;
     }
-    const double alpha = rz / pq;
-    {
-      ProfScope ps_(PROF_CG, S.s);
-      k_update_xr<<<kRedBlocks, kRedThreads, 0, S.s>>>(d, r, p, q, alpha, n, S.red);
-      CMBWS_LAUNCH_CHECK();
-    }
-    CMBWS_TRY(S.finish(&rr));
+    rr = S.hscal[kSlotRR];
     *iters = it + 1;
     *rr_out = rr;
     if (!std::isfinite(rr)) {
@@ -378,17 +422,16 @@ static int pcg_core(Solver& S, int prec, int use_M, double* d, double* r, double
       return CMBWS_ERR_TIMEOUT;
     }
     CMBWS_TRY(precond());
-    double rz_new;
-    CMBWS_TRY(S.dot(r, z, &rz_new));
-    const double beta = rz_new / rz;
-    rz = rz_new;
-    *rz_out = rz;
+    CMBWS_TRY(S.dot_dev(r, z, rz_nxt));
     {
       ProfScope ps_(PROF_CG, S.s);
-      k_xpby<<<kRedBlocks, kRedThreads, 0, S.s>>>(z, p, beta, n);
+      k_xpby_dev<<<kRedBlocks, kRedThreads, 0, S.s>>>(z, p, rz_nxt, rz_cur, n);
       CMBWS_LAUNCH_CHECK();
     }
   }
+  // the state of a run stopped at its cap carries the last r.z
+  CMBWS_TRY(S.read_slots());
+  *rz_out = S.hscal[kSlotRZ + (maxit & 1)];
   return CMBWS_ERR_NOT_CONVERGED;
 }
 
@@ -406,14 +449,9 @@ static int cg_solve_impl(Model& M, const double* b, double* x, const cmbws_cg_op
   CMBWS_TRY(M.cg_q.ensure(n * 8));
   CMBWS_TRY(M.cg_d.ensure(n * 8));
   CMBWS_TRY(M.cg_x.ensure(n * 8));
-  CMBWS_TRY(M.cg_red.ensure((kRedBlocks + 1) * 8));
-  double* hscal = nullptr;
-  CMBWS_CUDA(cudaMallocHost(&hscal, 8));
-  struct Free {
-    double* p;
-    ~Free() { cudaFreeHost(p); }
-  } fr{hscal};
-  Solver S{M, s, n, M.cg_red.as<double>(), hscal};
+  CMBWS_TRY(M.cg_red.ensure((kRedBlocks + kScal) * 8));
+  if (!M.cg_host) CMBWS_CUDA(cudaMallocHost(&M.cg_host, kScal * 8));
+  Solver S{M, s, n, M.cg_red.as<double>(), M.cg_host};
   S.cert = o.cert_prec == CMBWS_FP32X2 ? CMBWS_FP32X2 : CMBWS_FP64;
   S.comm = comm;
   const long long sht0 = M.n_sht;

@@ -159,6 +159,7 @@ void mask_mg_destroy(MaskMG* p) { delete p; }
 
 Model::~Model() {
   drop_graphs();
+  if (cg_host) cudaFreeHost(cg_host);
   for (MaskMG* p : masks) mask_mg_destroy(p);
 }
 

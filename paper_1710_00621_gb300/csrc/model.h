@@ -108,6 +108,7 @@ struct Model {
 
   // CG workspace (cg.cu)
   DevMem cg_r, cg_z, cg_p, cg_q, cg_d, cg_x, cg_red;
+  double* cg_host = nullptr;  // pinned: the PCG scalars read back once per iteration
   // per-iteration record of the last solve (cmbws_cg_history): ||r_i|| / ||b|| and, while a
   // reference solution is set (cmbws_cg_track_error), ||x_i - x_true|| / ||x_true||
   std::vector<double> hist_res, hist_err;
