@@ -19,8 +19,8 @@
 // * SPLIT = 1 keeps FP32-level accuracy with the split-TF32 product
 //   A_hi B_hi + A_hi B_lo + A_lo B_hi (x = hi + lo, hi = tf32(x), lo = tf32(x - hi));
 // * BF = 1 takes BF16 operands instead (kind::f16, K = 16 per MMA, two values of l packed per
-//   tensor-memory column, 8 significant bits per factor); with SPLIT the same hi / lo
-//   product in BF16 (about 16 significant bits).
+//   tensor-memory column, 8 significant bits per factor); the split BF16 mode runs the
+//   checkpointed kernel k_leg_synth_tc2 below.
 #include <climits>
 
 #include "common.h"
@@ -167,6 +167,7 @@ k_leg_synth_tc(const float2* __restrict__ alm, int64_t alm_stride, const float* 
                int64_t F_stride, int L, int npair) {
   using LY = TcLayout<SPLIT>;
   static_assert(NM >= 1 && NM <= 4, "at most 4 maps (16 output columns)");
+  static_assert(!(SPLIT && BF), "split BF16 runs k_leg_synth_tc2");
   extern __shared__ __align__(1024) unsigned char sm[];
   float* sAc = reinterpret_cast<float*>(sm + LY::kOffA);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + LY::kOffBar);
@@ -264,11 +265,6 @@ k_leg_synth_tc(const float2* __restrict__ alm, int64_t alm_stride, const float* 
           const uint32_t w = bf16x2_rn(cnext.x, cnext.y);
           *reinterpret_cast<uint16_t*>(bs + b_off16(n_re, kk)) = (uint16_t)(w & 0xFFFFu);
           *reinterpret_cast<uint16_t*>(bs + b_off16(n_re + 1, kk)) = (uint16_t)(w >> 16);
-          if constexpr (SPLIT) {
-            const uint32_t wl = bf16x2_rn(cnext.x - bf16_lo(w), cnext.y - bf16_hi(w));
-            *reinterpret_cast<uint16_t*>(bs + LY::kBStage + b_off16(n_re, kk)) = (uint16_t)(wl & 0xFFFFu);
-            *reinterpret_cast<uint16_t*>(bs + LY::kBStage + b_off16(n_re + 1, kk)) = (uint16_t)(wl >> 16);
-          }
         } else {
           const uint32_t hr = tf32_rna(cnext.x), hi = tf32_rna(cnext.y);
           *reinterpret_cast<uint32_t*>(bs + b_off(n_re, kk)) = hr;
@@ -302,9 +298,7 @@ k_leg_synth_tc(const float2* __restrict__ alm, int64_t alm_stride, const float* 
     };
     auto emit2 = [&](int j, float ma, float mb) {
       if constexpr (BF) {
-        const uint32_t w = bf16x2_rn(ma, mb);
-        vh[j >> 1] = w;
-        if constexpr (SPLIT) vl[j >> 1] = bf16x2_rn(ma - bf16_lo(w), mb - bf16_hi(w));
+        vh[j >> 1] = bf16x2_rn(ma, mb);
       } else if constexpr (SPLIT) {
         vh[j] = tf32_rna(ma);
         vh[j + 1] = tf32_rna(mb);
@@ -361,8 +355,6 @@ k_leg_synth_tc(const float2* __restrict__ alm, int64_t alm_stride, const float* 
     }
     if constexpr (BF) {
       tmem_st16(tb + lane_base + LY::kColA + 16 * s, *reinterpret_cast<const uint32_t(*)[16]>(vh));
-      if constexpr (SPLIT)
-        tmem_st16(tb + lane_base + LY::kColAlo + 16 * s, *reinterpret_cast<const uint32_t(*)[16]>(vl));
     } else {
       tmem_st32(tb + lane_base + LY::kColA + 32 * s, vh);
       if constexpr (SPLIT) tmem_st32(tb + lane_base + LY::kColAlo + 32 * s, vl);
@@ -381,11 +373,6 @@ k_leg_synth_tc(const float2* __restrict__ alm, int64_t alm_stride, const float* 
           const uint32_t a_hi = tb + LY::kColA + 16 * s + 8 * i;
           const uint64_t dh = smem_desc(bh + 512 * i, 128, 256);
           mma_bf16(tb + LY::kColD, a_hi, dh, (b > 0 || i > 0) ? 1u : 0u);
-          if constexpr (SPLIT) {
-            const uint64_t dl = smem_desc(bh + LY::kBStage + 512 * i, 128, 256);
-            mma_bf16(tb + LY::kColD, a_hi, dl, 1u);
-            mma_bf16(tb + LY::kColD, tb + LY::kColAlo + 16 * s + 8 * i, dh, 1u);
-          }
         }
       } else {
 #pragma unroll
@@ -893,6 +880,381 @@ int launch_adj_tc_nm(int nm, const Grid& g, const float* e, double* o, cudaStrea
   }
 }
 
+// ---- synthesis on the tensor cores from checkpoints (BF16 / split BF16) ----
+//
+// The same product as k_leg_synth_tc, D[pair][col] = sum_l Lambda[pair][l] B[l][col], with the
+// A operand built the way the tensor-core adjoint builds it: thread (octet of 8 ring pairs,
+// chunk of kChunk = 8 values of l) restarts each pair's recurrence at the chunk's
+// FP64-computed checkpoint and writes the 8 x 8 BF16 values as one core matrix (8 rows of
+// ring pairs x 16 bytes of l) of the K-major shared-memory tile.  Eight independent chains
+// per thread replace the single chain of k_leg_synth_tc, the recurrence never runs more than
+// 8 steps in FP32 (no difference form near the poles), and consecutive threads take
+// consecutive chunks of a pair, so the checkpoint loads are contiguous.  Core matrices of
+// consecutive chunks sit 144 bytes apart (LBO 144, SBO 1152), so that a warp's 16-byte row
+// stores fall on distinct banks.  Stages of 64 values of l: the coefficients and A_l of the
+// next stage arrive by cp.async, the checkpoints in two alternating register sets; the tile
+// is single-buffered (5 CTAs per SM).
+constexpr int kSt2M = 128;                        // ring pairs per CTA (MMA M, threads)
+constexpr int kSt2KS = 64;                        // values of l per stage: 8 chunks
+constexpr int kSt2Core = 144;                     // bytes between core matrices of consecutive chunks
+constexpr int kSt2Oct = (kSt2KS / 8) * kSt2Core;  // bytes between consecutive octets of pairs
+constexpr int kSt2ASlice = (kSt2M / 8) * kSt2Oct;
+
+template <int SA>
+struct St2Layout {
+  static constexpr int kBStep = 512 * SA;  // one K step of B: 16 SA rows x 16 values of l
+  static constexpr int kBTile = (kSt2KS / 16) * kBStep;
+  static constexpr int kStage = SA * kSt2ASlice + kBTile;
+  // per-stage inputs (two buffers): the coefficients of up to 4 maps and A_l
+  static constexpr int kPAlm = 0;
+  static constexpr int kPA = kPAlm + 4 * kSt2KS * 8;
+  static constexpr int kPre = kPA + kSt2KS * 4;
+  static constexpr int kOffPre = kStage;
+  // per-pair data of the CTA: start values, starts, y
+  static constexpr int kOffSt = kOffPre + 2 * kPre;
+  static constexpr int kOffLs = kOffSt + kSt2M * 8;
+  static constexpr int kOffY = kOffLs + kSt2M * 4;
+  static constexpr int kOffBar = kOffY + kSt2M * 4;  // uint64_t mbar[2]
+  static constexpr int kOffT = kOffBar + 16;          // tensor-memory base, bad flag, min start
+  static constexpr int kSmem = kOffT + 16;
+  static constexpr uint32_t kCols = 32;
+};
+
+template <int NM, int SA>
+__global__ void __launch_bounds__(kSt2M, SA == 1 ? 5 : 4)
+k_leg_synth_tc2(const float2* __restrict__ alm, int64_t alm_stride, const float* __restrict__ Acoef,
+                const int* __restrict__ ls_tab, const float2* __restrict__ st,
+                const float* __restrict__ yr, const float2* __restrict__ ck,
+                const int64_t* __restrict__ ck_base, const int2* __restrict__ pring,
+                float2* __restrict__ F, int64_t F_stride, int L, int npair) {
+  using LY = St2Layout<SA>;
+  static_assert(kChunk == 8, "one core matrix holds one chunk of 8 values of l");
+  static_assert(NM >= 1 && NM <= 4, "at most 4 maps (8 columns per parity)");
+  constexpr int P = 2 * NM;
+  extern __shared__ __align__(1024) unsigned char sm[];
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + LY::kOffBar);
+  uint32_t* s_tb = reinterpret_cast<uint32_t*>(sm + LY::kOffT);
+  int* s_bad = reinterpret_cast<int*>(sm + LY::kOffT + 4);
+  int* s_lo = reinterpret_cast<int*>(sm + LY::kOffT + 8);
+  float2* s_st = reinterpret_cast<float2*>(sm + LY::kOffSt);
+  int* s_ls = reinterpret_cast<int*>(sm + LY::kOffLs);
+  float* s_y = reinterpret_cast<float*>(sm + LY::kOffY);
+
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int m = blockIdx.y;
+  const int p0 = blockIdx.x * kSt2M;
+  const int64_t lmo = lm_off(L, m) - m;
+  const int nck = (L - m + kChunk) / kChunk;
+  // this CTA's pairs: start values, starts (INT_MAX past the last pair), y
+  {
+    const int p = p0 + tid;
+    const bool ok = p < npair;
+    const int ls = ok ? ls_tab[(int64_t)m * npair + p] : INT_MAX;
+    s_ls[tid] = ls;
+    s_y[tid] = ok ? yr[p] : 0.f;
+    s_st[tid] = ok ? st[(int64_t)m * npair + p] : make_float2(0.f, 0.f);
+    if (tid == 0) {
+      *s_lo = INT_MAX;
+      *s_bad = 0;
+    }
+    __syncthreads();
+    atomicMin(s_lo, ls);
+    __syncthreads();
+  }
+  const int lo = *s_lo;
+  if (lo > L) {  // no pair of the tile has a significant value at this m
+    const int p = p0 + tid;
+    if (p < npair) {
+      const int2 rr = pring[p];
+#pragma unroll
+      for (int k = 0; k < NM; ++k) {
+        F[k * F_stride + (int64_t)rr.x * (L + 1) + m] = make_float2(0.f, 0.f);
+        if (rr.y >= 0) F[k * F_stride + (int64_t)rr.y * (L + 1) + m] = make_float2(0.f, 0.f);
+      }
+    }
+    return;
+  }
+  const int nst = (L - m + kSt2KS) / kSt2KS;
+  int s = (lo - m) / kSt2KS;  // stages before the first start add nothing
+
+  // zero the tile (B columns of absent maps and of the other parity stay zero)
+  for (int i = tid; i < LY::kStage / 16; i += kSt2M)
+    reinterpret_cast<float4*>(sm)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_addr(s_tb)),
+                 "r"(LY::kCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&mbar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&mbar[1])));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
+    // test support, as in the other tensor-core kernels: a wait that nothing completes runs out
+    const long long stall = g_tc_stall_cycles;
+    if (stall > 0 && !mbar_wait(&mbar[1], 0, stall)) *s_bad = 1;
+  }
+
+  const int ch = tid & 7, oc = tid >> 3;  // chunk of the stage, octet of pairs
+  // the octet's starts and y, kept in registers
+  int lsr[8];
+  float y[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    lsr[i] = s_ls[8 * oc + i];
+    y[i] = s_y[8 * oc + i];
+  }
+  const int64_t ckb = ck_base[m];
+
+  // copy the coefficients and A_l of stage s into prefetch buffer pb (one commit group);
+  // values past L are zero
+  auto prefetch = [&](int s, int pb) {
+    unsigned char* pre = sm + LY::kOffPre + pb * LY::kPre;
+    const int ls0 = m + s * kSt2KS;
+    for (int i = tid; i < (NM + 1) * kSt2KS; i += kSt2M) {
+      const int q = i / kSt2KS, j = i % kSt2KS;
+      const int l = ls0 + j;
+      if (q < NM) {
+        float2* dst = reinterpret_cast<float2*>(pre + LY::kPAlm) + q * kSt2KS + j;
+        if (l <= L) cp_async8(dst, alm + q * alm_stride + lmo + l);
+        else *dst = make_float2(0.f, 0.f);
+      } else {
+        float* dst = reinterpret_cast<float*>(pre + LY::kPA) + j;
+        if (l <= L) cp_async4(dst, Acoef + lmo + l);
+        else *dst = 0.f;
+      }
+    }
+    cp_async_commit();
+  };
+  // this thread's 8 checkpoints of stage s (chunk 8 s + ch of its 8 pairs)
+  auto load_ck = [&](int s, float2 (&cv)[8]) {
+    const int c = s * (kSt2KS / kChunk) + ch;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int p = p0 + 8 * oc + i;
+      cv[i] = (c < nck && p < npair) ? ck[ckb + (int64_t)p * nck + c] : make_float2(0.f, 0.f);
+    }
+  };
+
+  float2 ckA[8], ckB[8];
+  load_ck(s, ckA);
+  prefetch(s, 0);
+  cp_async_wait<0>();
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+  const uint32_t tb = *s_tb;
+  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  unsigned char* As = sm;
+  unsigned char* Bs = As + SA * kSt2ASlice;
+
+  bool bad = false;
+  int k = 0;
+  auto run_stage = [&](const float2 (&cv)[8], float2 (&cvn)[8]) {
+    const int sn = s + 1;
+    if (sn < nst) {
+      load_ck(sn, cvn);
+      prefetch(sn, (k + 1) & 1);
+    }
+    const unsigned char* pre = sm + LY::kOffPre + (k & 1) * LY::kPre;
+    const int ls0 = m + s * kSt2KS;
+    const int l0 = ls0 + kChunk * ch;
+    // B values (column n = tid % 16: parity n / 8, part n % 8, of the l-octet tid / 16)
+    const int n = tid & 15, q = n & 7, ob = tid >> 4;
+    float v[8];
+    {
+      const float* a = reinterpret_cast<const float*>(pre + LY::kPAlm) + (q >> 1) * 2 * kSt2KS + (q & 1);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int j = 8 * ob + i;
+        v[i] = (q < P && ((ls0 + j - m) & 1) == (n >> 3)) ? a[2 * j] : 0.f;
+      }
+    }
+    float Al[kChunk];
+    {
+      const float4* ap = reinterpret_cast<const float4*>(pre + LY::kPA) + 2 * ch;
+      const float4 a0 = ap[0], a1 = ap[1];
+      Al[0] = a0.x; Al[1] = a0.y; Al[2] = a0.z; Al[3] = a0.w;
+      Al[4] = a1.x; Al[5] = a1.y; Al[6] = a1.z; Al[7] = a1.w;
+    }
+    // the previous stage's MMAs have read the tile
+    if (k >= 1 && !*s_bad && !mbar_wait(&mbar[0], (k - 1) & 1)) bad = true;
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+    if (q < P) {  // B: one 16-byte row of a core matrix per slice
+      uint4 w;
+      w.x = bf16x2_rn(v[0], v[1]);
+      w.y = bf16x2_rn(v[2], v[3]);
+      w.z = bf16x2_rn(v[4], v[5]);
+      w.w = bf16x2_rn(v[6], v[7]);
+      const int off = (ob >> 1) * LY::kBStep + (n >> 3) * 256 + (ob & 1) * 128 + q * 16;
+      *reinterpret_cast<uint4*>(Bs + off) = w;
+      if constexpr (SA == 2) {
+        uint4 u;
+        u.x = bf16x2_rn(v[0] - bf16_lo(w.x), v[1] - bf16_hi(w.x));
+        u.y = bf16x2_rn(v[2] - bf16_lo(w.y), v[3] - bf16_hi(w.y));
+        u.z = bf16x2_rn(v[4] - bf16_lo(w.z), v[5] - bf16_hi(w.z));
+        u.w = bf16x2_rn(v[6] - bf16_lo(w.w), v[7] - bf16_hi(w.w));
+        *reinterpret_cast<uint4*>(Bs + off + 512) = u;  // rows 16..31
+      }
+    }
+    // A: for each pair of the octet its 8 values of the chunk, one 16-byte row per slice;
+    // two passes of four interleaved chains
+    unsigned char* arow = As + oc * kSt2Oct + ch * kSt2Core;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      float x[4][kChunk];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = 4 * h + u;
+        const int jinj = lsr[i] - l0;  // where the pair starts, relative to the chunk
+        float ma = jinj > 0 ? 0.f : cv[i].x;  // before its start a pair's values are zero
+        float mb = jinj > 0 ? 0.f : cv[i].y;
+        if (jinj == 0) {
+          ma = s_st[8 * oc + i].x;
+          mb = s_st[8 * oc + i].y;
+        }
+        x[u][0] = ma;
+        x[u][1] = mb;
+#pragma unroll
+        for (int j = 2; j < kChunk; j += 2) {
+          float na = fmaf(fmaf(-Al[j], y[i], Al[j]), mb, -ma);
+          float nb = fmaf(fmaf(-Al[j + 1], y[i], Al[j + 1]), na, -mb);
+          if (jinj == j) {
+            na = s_st[8 * oc + i].x;
+            nb = s_st[8 * oc + i].y;
+          }
+          ma = na;
+          mb = nb;
+          x[u][j] = ma;
+          x[u][j + 1] = mb;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        uint4 w;
+        w.x = bf16x2_rn(x[u][0], x[u][1]);
+        w.y = bf16x2_rn(x[u][2], x[u][3]);
+        w.z = bf16x2_rn(x[u][4], x[u][5]);
+        w.w = bf16x2_rn(x[u][6], x[u][7]);
+        *reinterpret_cast<uint4*>(arow + 16 * (4 * h + u)) = w;
+        if constexpr (SA == 2) {
+          uint4 z;
+          z.x = bf16x2_rn(x[u][0] - bf16_lo(w.x), x[u][1] - bf16_hi(w.x));
+          z.y = bf16x2_rn(x[u][2] - bf16_lo(w.y), x[u][3] - bf16_hi(w.y));
+          z.z = bf16x2_rn(x[u][4] - bf16_lo(w.z), x[u][5] - bf16_hi(w.z));
+          z.w = bf16x2_rn(x[u][6] - bf16_lo(w.w), x[u][7] - bf16_hi(w.w));
+          *reinterpret_cast<uint4*>(arow + kSt2ASlice + 16 * (4 * h + u)) = z;
+        }
+      }
+    }
+    cp_async_wait<0>();  // the next stage's inputs, visible to all after the barrier
+    asm volatile("fence.proxy.async.shared::cta;\n" ::);
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+    if (bad) atomicOr(s_bad, 1);
+    __syncthreads();
+    if (tid == 0 && !*s_bad) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+      const uint32_t ab = smem_addr(As), bb = smem_addr(Bs);
+#pragma unroll
+      for (int ks = 0; ks < kSt2KS / 16; ++ks) {
+        const uint64_t bd = smem_desc(bb + ks * LY::kBStep, 128, 256);
+#pragma unroll
+        for (int i = 0; i < SA; ++i) {
+          const uint64_t ad = smem_desc(ab + i * kSt2ASlice + ks * 2 * kSt2Core, kSt2Core, kSt2Oct);
+          mma_bf16_ss(tb + 16 * i, ad, bd, idesc_bf16(16 * (SA - i)),
+                      (k > 0 || ks > 0 || i > 0) ? 1u : 0u);
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+          smem_addr(&mbar[0])));
+    }
+    s = sn;
+    ++k;
+  };
+  // two stages per trip, so that the checkpoint registers alternate without copies
+  while (true) {
+    run_stage(ckA, ckB);
+    if (s >= nst) break;
+    run_stage(ckB, ckA);
+    if (s >= nst) break;
+  }
+  // accumulators after the last stage
+  if (!*s_bad && !mbar_wait(&mbar[0], (k - 1) & 1)) bad = true;
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+  uint32_t d[16 * SA];
+  if constexpr (SA == 1) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        : "=r"(d[0]), "=r"(d[1]), "=r"(d[2]), "=r"(d[3]), "=r"(d[4]), "=r"(d[5]), "=r"(d[6]), "=r"(d[7]),
+          "=r"(d[8]), "=r"(d[9]), "=r"(d[10]), "=r"(d[11]), "=r"(d[12]), "=r"(d[13]), "=r"(d[14]), "=r"(d[15])
+        : "r"(tb + lane_base));
+  } else {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+        : "=r"(d[0]), "=r"(d[1]), "=r"(d[2]), "=r"(d[3]), "=r"(d[4]), "=r"(d[5]), "=r"(d[6]), "=r"(d[7]),
+          "=r"(d[8]), "=r"(d[9]), "=r"(d[10]), "=r"(d[11]), "=r"(d[12]), "=r"(d[13]), "=r"(d[14]), "=r"(d[15]),
+          "=r"(d[16]), "=r"(d[17]), "=r"(d[18]), "=r"(d[19]), "=r"(d[20]), "=r"(d[21]), "=r"(d[22]),
+          "=r"(d[23]), "=r"(d[24]), "=r"(d[25]), "=r"(d[26]), "=r"(d[27]), "=r"(d[28]), "=r"(d[29]),
+          "=r"(d[30]), "=r"(d[31])
+        : "r"(tb + lane_base));
+  }
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
+  if (bad) atomicOr(s_bad, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+  __syncthreads();
+  const bool failed = *s_bad != 0;
+  if (failed && tid == 0) atomicOr(&g_tc_status, 1u);
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tb), "r"(LY::kCols));
+  const int p = p0 + tid;  // row tid of D
+  if (p >= npair) return;
+  const int2 rr = pring[p];
+  const float nan = __int_as_float(0x7fc00000);
+#pragma unroll
+  for (int q = 0; q < NM; ++q) {
+    float er = __uint_as_float(d[2 * q]), ei = __uint_as_float(d[2 * q + 1]);
+    float orr = __uint_as_float(d[8 + 2 * q]), oi = __uint_as_float(d[8 + 2 * q + 1]);
+    if constexpr (SA == 2) {
+      er += __uint_as_float(d[16 + 2 * q]);
+      ei += __uint_as_float(d[16 + 2 * q + 1]);
+      orr += __uint_as_float(d[24 + 2 * q]);
+      oi += __uint_as_float(d[24 + 2 * q + 1]);
+    }
+    // a timed-out wait leaves NaN in the output, which the solver reports as a breakdown
+    const float2 fn = failed ? make_float2(nan, nan) : make_float2(er + orr, ei + oi);
+    const float2 fsv = failed ? make_float2(nan, nan) : make_float2(er - orr, ei - oi);
+    F[q * F_stride + (int64_t)rr.x * (L + 1) + m] = fn;
+    if (rr.y >= 0) F[q * F_stride + (int64_t)rr.y * (L + 1) + m] = fsv;
+  }
+}
+
+template <int NM, int SA>
+int launch_synth_tc2(const Grid& g, const void* alm, int64_t as, void* F, int64_t fs, cudaStream_t s) {
+  using LY = St2Layout<SA>;
+  const int L = g.lmax;
+  dim3 grd((g.npair + kSt2M - 1) / kSt2M, L + 1);
+  auto kern = k_leg_synth_tc2<NM, SA>;
+  CMBWS_TRY(ensure_dyn_smem((const void*)kern, LY::kSmem));
+  // profiling arithmetic kinds: 5 BF16, 6 split BF16
+  ProfScope ps(PROF_LEG_SYNTH, s, 4 + SA, leg_work(g, NM));
+  kern<<<grd, kSt2M, LY::kSmem, s>>>((const float2*)alm, as, g.A32.as<float>(), g.ls.as<int>(),
+                                     g.st32.as<float2>(), g.y32.as<float>(), g.ck32.as<float2>(),
+                                     g.ck_base.as<int64_t>(), g.pair_ring.as<int2>(), (float2*)F, fs, L,
+                                     g.npair);
+  CMBWS_LAUNCH_CHECK();
+  return CMBWS_OK;
+}
+
+template <int SA>
+int launch_synth_tc2_nm(int nm, const Grid& g, const void* a, int64_t as, void* f, int64_t fs,
+                        cudaStream_t s) {
+  switch (nm) {
+    case 1: return launch_synth_tc2<1, SA>(g, a, as, f, fs, s);
+    case 2: return launch_synth_tc2<2, SA>(g, a, as, f, fs, s);
+    case 3: return launch_synth_tc2<3, SA>(g, a, as, f, fs, s);
+    default: return launch_synth_tc2<4, SA>(g, a, as, f, fs, s);
+  }
+}
+
 static_assert(TcLayout<0>::kUsed <= TcLayout<0>::kSmem && TcLayout<1>::kUsed <= TcLayout<1>::kSmem,
               "shared-memory layout exceeds the request");
 
@@ -922,8 +1284,10 @@ int legendre_synth_tc(const Grid& g, int prec, int nmaps, const void* alm, void*
     switch (prec) {
       case CMBWS_TF32: st = launch_synth_tc_nm<0, 0>(nm, g, a, as, f, fs, s); break;
       case CMBWS_3XTF32: st = launch_synth_tc_nm<1, 0>(nm, g, a, as, f, fs, s); break;
+      // BF16: the single-chain kernel (2.57 against 3.09 ms for the checkpointed one at
+      // Nside 1024, L = 3071, 3 maps); split BF16: the checkpointed kernel (3.88 against 5.45 ms)
       case CMBWS_BF16: st = launch_synth_tc_nm<0, 1>(nm, g, a, as, f, fs, s); break;
-      default: st = launch_synth_tc_nm<1, 1>(nm, g, a, as, f, fs, s); break;
+      default: st = launch_synth_tc2_nm<2>(nm, g, a, as, f, fs, s); break;
     }
     if (st != CMBWS_OK) return st;
   }
