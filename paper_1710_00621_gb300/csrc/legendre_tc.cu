@@ -130,7 +130,7 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16
       "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]));
 }
 
-template <int SPLIT>
+template <int SPLIT, int BF>
 struct TcLayout {
   static constexpr int kBStage = 4 * 512;                         // one 16 x 32 TF32 tile
   static constexpr int kStage = (SPLIT ? 2 : 1) * kBStage;        // hi (+ lo) per stage
@@ -139,10 +139,11 @@ struct TcLayout {
   static constexpr int kOffT = kOffBar + 24;                      // uint32_t tmem base, bad flag
   static constexpr int kUsed = kOffT + 16;
   // Shared memory requested per CTA: caps residency so that the CTAs of an SM never ask
-  // for more than its 512 tensor-memory columns (4 x 128 or 2 x 256).
-  static constexpr int kSmem = SPLIT ? 80 * 1024 : 48 * 1024;
-  static constexpr uint32_t kCols = SPLIT ? 256 : 128;
-  static constexpr uint32_t kColA = 0, kColAlo = 64, kColD = SPLIT ? 128 : 64;
+  // for more than its 512 tensor-memory columns (2 x 256 split TF32, 4 x 128 TF32, 8 x 64
+  // BF16, whose two A stages take 16 columns each).
+  static constexpr int kSmem = SPLIT ? 80 * 1024 : (BF ? 26 * 1024 : 48 * 1024);
+  static constexpr uint32_t kCols = SPLIT ? 256 : (BF ? 64 : 128);
+  static constexpr uint32_t kColA = 0, kColAlo = 64, kColD = SPLIT ? 128 : (BF ? 32 : 64);
 };
 
 // Byte offset of B[n][k] (n < 16 output column, k < 32 within the block) in a stage tile:
@@ -165,7 +166,7 @@ k_leg_synth_tc(const float2* __restrict__ alm, int64_t alm_stride, const float* 
                const float2* __restrict__ st,
                const float* __restrict__ yr, const int2* __restrict__ pring, float2* __restrict__ F,
                int64_t F_stride, int L, int npair) {
-  using LY = TcLayout<SPLIT>;
+  using LY = TcLayout<SPLIT, BF>;
   static_assert(NM >= 1 && NM <= 4, "at most 4 maps (16 output columns)");
   static_assert(!(SPLIT && BF), "split BF16 runs k_leg_synth_tc2");
   extern __shared__ __align__(1024) unsigned char sm[];
@@ -424,7 +425,7 @@ k_leg_synth_tc(const float2* __restrict__ alm, int64_t alm_stride, const float* 
 
 template <int NM, int SPLIT, int BF>
 int launch_synth_tc(const Grid& g, const void* alm, int64_t as, void* F, int64_t fs, cudaStream_t s) {
-  using LY = TcLayout<SPLIT>;
+  using LY = TcLayout<SPLIT, BF>;
   const int L = g.lmax;
   dim3 grd((g.npair + kTcNT - 1) / kTcNT, L + 1);
   auto kern = k_leg_synth_tc<NM, SPLIT, BF>;
@@ -1255,8 +1256,12 @@ int launch_synth_tc2_nm(int nm, const Grid& g, const void* a, int64_t as, void* 
   }
 }
 
-static_assert(TcLayout<0>::kUsed <= TcLayout<0>::kSmem && TcLayout<1>::kUsed <= TcLayout<1>::kSmem,
+static_assert(TcLayout<0, 0>::kUsed <= TcLayout<0, 0>::kSmem &&
+                  TcLayout<1, 0>::kUsed <= TcLayout<1, 0>::kSmem &&
+                  TcLayout<0, 1>::kUsed <= TcLayout<0, 1>::kSmem,
               "shared-memory layout exceeds the request");
+static_assert(TcLayout<0, 1>::kColD >= 32 && TcLayout<0, 1>::kColD + 16 <= TcLayout<0, 1>::kCols,
+              "BF16: two A stages of 16 columns, then 16 accumulator columns");
 
 }  // namespace
 
