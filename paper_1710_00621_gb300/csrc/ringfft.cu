@@ -582,9 +582,10 @@ size_t smem_bytes(const Grid& g) {
   return (size_t)(g.nmax2 + g.nmax2 / 16 + 16) * sizeof(typename V2<T>::t);
 }
 
-// Threads per CTA: a grid with large transforms (>= 2048 entries, e.g. the 4 Nside-point
-// equatorial rings from Nside 512 up) gets 512 threads, so that the butterfly passes of one
-// ring have twice the warps to hide shared-memory latency with the same buffer per CTA.
+// Threads per CTA: a grid with large transforms (>= 4096 entries, e.g. the Bluestein buffers
+// of the polar rings from Nside 512 up) gets 256 threads, so that the butterfly passes of one
+// ring have twice the warps to hide shared-memory latency with the same buffer per CTA; the
+// others 128.
 template <typename T, int MODE>
 int launch(const Grid& g, int nmaps, void* F, double* map_out, const double* map_in, int weighted,
            const void* const* pix, void* eo, int eo_nm, cudaStream_t s);
