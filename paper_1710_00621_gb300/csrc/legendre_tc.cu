@@ -13,9 +13,12 @@
 //   of the MMA never passes through shared memory;
 // * B (the block's coefficients, 16 x 32 TF32) is written to shared memory in the
 //   K-major core-matrix layout and described by a shared-memory descriptor;
-// * blocks of 32 values of l alternate between two tensor-memory / shared-memory stages;
-//   one thread issues the MMAs (M = 128, N = 16, K = 8) and commits them to the stage's
-//   mbarrier, which the threads wait on (bounded) before overwriting the stage;
+// * blocks of 32 values of l alternate between two shared-memory stages of B; one thread
+//   issues the MMAs (M = 128, N = 16, K = 8) and commits them to the block's mbarrier; the A
+//   operand (TF32) has one tensor-memory buffer, which the threads overwrite after a bounded
+//   wait for the previous block's MMAs, placed after the block's recurrence so that those
+//   MMAs run during it (64 tensor-memory columns per CTA: 8 CTAs per SM; BF16 packs two values
+//   of l per column and keeps two buffers in the same 64);
 // * SPLIT = 1 keeps FP32-level accuracy with the split-TF32 product
 //   A_hi B_hi + A_hi B_lo + A_lo B_hi (x = hi + lo, hi = tf32(x), lo = tf32(x - hi));
 // * BF = 1 takes BF16 operands instead (kind::f16, K = 16 per MMA, two values of l packed per
@@ -138,12 +141,13 @@ struct TcLayout {
   static constexpr int kOffBar = kOffA + 2 * 4 * kTcKB * 4;       // uint64_t mbar[3]
   static constexpr int kOffT = kOffBar + 24;                      // uint32_t tmem base, bad flag
   static constexpr int kUsed = kOffT + 16;
-  // Shared memory requested per CTA: caps residency so that the CTAs of an SM never ask
-  // for more than its 512 tensor-memory columns (2 x 256 split TF32, 4 x 128 TF32, 8 x 64
-  // BF16, whose two A stages take 16 columns each).
-  static constexpr int kSmem = SPLIT ? 80 * 1024 : (BF ? 26 * 1024 : 48 * 1024);
-  static constexpr uint32_t kCols = SPLIT ? 256 : (BF ? 64 : 128);
-  static constexpr uint32_t kColA = 0, kColAlo = 64, kColD = SPLIT ? 128 : (BF ? 32 : 64);
+  // Tensor memory: one A buffer of 32 columns of TF32 values of l (split TF32 adds the lo
+  // part) or two of 16 columns of packed BF16 pairs, then 16 accumulator columns.  Shared
+  // memory requested per CTA: caps residency so that the CTAs of an SM never ask for more
+  // than its 512 columns (4 x 128 split TF32, 8 x 64 TF32 or BF16).
+  static constexpr int kSmem = SPLIT ? 48 * 1024 : 26 * 1024;
+  static constexpr uint32_t kCols = SPLIT ? 128 : 64;
+  static constexpr uint32_t kColA = 0, kColAlo = 32, kColD = SPLIT ? 64 : 32;
 };
 
 // Byte offset of B[n][k] (n < 16 output column, k < 32 within the block) in a stage tile:
@@ -160,12 +164,12 @@ __device__ __forceinline__ int b_off16(int n, int k) {
 // BF = 1: BF16 operands (kind::f16, K = 16 per MMA, two values of l per tensor-memory column)
 // instead of TF32 (kind::tf32, K = 8).
 template <int NM, int SPLIT, int BF>
-__global__ void __launch_bounds__(kTcNT)
-k_leg_synth_tc(const float2* __restrict__ alm, int64_t alm_stride, const float* __restrict__ Acoef,
-               const float* __restrict__ brs, const int* __restrict__ ls_tab,
-               const float2* __restrict__ st,
-               const float* __restrict__ yr, const int2* __restrict__ pring, float2* __restrict__ F,
-               int64_t F_stride, int L, int npair) {
+__device__ __forceinline__ void
+synth_tc_body(const float2* __restrict__ alm, int64_t alm_stride, const float* __restrict__ Acoef,
+              const float* __restrict__ brs, const int* __restrict__ ls_tab,
+              const float2* __restrict__ st,
+              const float* __restrict__ yr, const int2* __restrict__ pring, float2* __restrict__ F,
+              int64_t F_stride, int L, int npair) {
   using LY = TcLayout<SPLIT, BF>;
   static_assert(NM >= 1 && NM <= 4, "at most 4 maps (16 output columns)");
   static_assert(!(SPLIT && BF), "split BF16 runs k_leg_synth_tc2");
@@ -256,7 +260,11 @@ k_leg_synth_tc(const float2* __restrict__ alm, int64_t alm_stride, const float* 
   for (int b = 0; b < nb; ++b) {
     const int s = b & 1;
     // once a wait has failed no more MMAs are issued, so later waits are skipped
-    if (b >= 2 && !*s_bad && !mbar_wait(&mbar[s], ((b - 2) >> 1) & 1)) bad = true;
+    // BF16 keeps two A buffers (16 columns each): wait here for the MMAs of block b - 2, which
+    // read this stage.  TF32 kinds have one A buffer and wait after the recurrence (below);
+    // their B stage was last read by the MMAs of block b - 2, waited for in block b - 1.
+    if constexpr (BF)
+      if (b >= 2 && !*s_bad && !mbar_wait(&mbar[s], ((b - 2) >> 1) & 1)) bad = true;
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
     // stage the block's coefficients (B) and recurrence coefficients A_l
     {
@@ -354,11 +362,18 @@ k_leg_synth_tc(const float2* __restrict__ alm, int64_t alm_stride, const float* 
         emit(j + 2);
       }
     }
+    // TF32 kinds: one A buffer in tensor memory, which the MMAs of block b - 1 (issued after
+    // the last barrier) have read by now (bounded wait; once a wait has failed no more MMAs
+    // are issued and later waits are skipped)
+    if constexpr (!BF) {
+      if (b >= 1 && !*s_bad && !mbar_wait(&mbar[(b - 1) & 1], ((b - 1) >> 1) & 1)) bad = true;
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+    }
     if constexpr (BF) {
       tmem_st16(tb + lane_base + LY::kColA + 16 * s, *reinterpret_cast<const uint32_t(*)[16]>(vh));
     } else {
-      tmem_st32(tb + lane_base + LY::kColA + 32 * s, vh);
-      if constexpr (SPLIT) tmem_st32(tb + lane_base + LY::kColAlo + 32 * s, vl);
+      tmem_st32(tb + lane_base + LY::kColA, vh);
+      if constexpr (SPLIT) tmem_st32(tb + lane_base + LY::kColAlo, vl);
     }
     asm volatile("tcgen05.wait::st.sync.aligned;\n" ::);
     asm volatile("fence.proxy.async.shared::cta;\n" ::);
@@ -378,13 +393,13 @@ k_leg_synth_tc(const float2* __restrict__ alm, int64_t alm_stride, const float* 
       } else {
 #pragma unroll
         for (int i = 0; i < kTcKB / 8; ++i) {
-          const uint32_t a_hi = tb + LY::kColA + 32 * s + 8 * i;
+          const uint32_t a_hi = tb + LY::kColA + 8 * i;
           const uint64_t dh = smem_desc(bh + 512 * i, 128, 256);
           mma_tf32(tb + LY::kColD, a_hi, dh, (b > 0 || i > 0) ? 1u : 0u);
           if constexpr (SPLIT) {
             const uint64_t dl = smem_desc(bh + LY::kBStage + 512 * i, 128, 256);
             mma_tf32(tb + LY::kColD, a_hi, dl, 1u);
-            mma_tf32(tb + LY::kColD, tb + LY::kColAlo + 32 * s + 8 * i, dh, 1u);
+            mma_tf32(tb + LY::kColD, tb + LY::kColAlo + 8 * i, dh, 1u);
           }
         }
       }
@@ -423,12 +438,32 @@ k_leg_synth_tc(const float2* __restrict__ alm, int64_t alm_stride, const float* 
   }
 }
 
+// The kernels: the BF16 instance keeps the compiler's own register choice (64, no spill:
+// 8 CTAs per SM, measured 1.84 ms at Nside 1024 against 2.05 ms when bounded to 8 CTAs,
+// which made it spill); the TF32 kinds are bounded to 8 (4 split) CTAs per SM.
+#define CMBWS_SYNTH_TC_ARGS                                                                    \
+  const float2 *__restrict__ alm, int64_t alm_stride, const float *__restrict__ Acoef,        \
+      const float *__restrict__ brs, const int *__restrict__ ls_tab,                          \
+      const float2 *__restrict__ st, const float *__restrict__ yr,                            \
+      const int2 *__restrict__ pring, float2 *__restrict__ F, int64_t F_stride, int L, int npair
+template <int NM>
+__global__ void __launch_bounds__(kTcNT) k_leg_synth_tc_bf16(CMBWS_SYNTH_TC_ARGS) {
+  synth_tc_body<NM, 0, 1>(alm, alm_stride, Acoef, brs, ls_tab, st, yr, pring, F, F_stride, L, npair);
+}
+template <int NM, int SPLIT>
+__global__ void __launch_bounds__(kTcNT, SPLIT ? 4 : 8) k_leg_synth_tc(CMBWS_SYNTH_TC_ARGS) {
+  synth_tc_body<NM, SPLIT, 0>(alm, alm_stride, Acoef, brs, ls_tab, st, yr, pring, F, F_stride, L,
+                              npair);
+}
+#undef CMBWS_SYNTH_TC_ARGS
+
 template <int NM, int SPLIT, int BF>
 int launch_synth_tc(const Grid& g, const void* alm, int64_t as, void* F, int64_t fs, cudaStream_t s) {
   using LY = TcLayout<SPLIT, BF>;
   const int L = g.lmax;
   dim3 grd((g.npair + kTcNT - 1) / kTcNT, L + 1);
-  auto kern = k_leg_synth_tc<NM, SPLIT, BF>;
+  static_assert(!(SPLIT && BF), "split BF16 runs k_leg_synth_tc2");
+  auto kern = BF ? k_leg_synth_tc_bf16<NM> : k_leg_synth_tc<NM, SPLIT>;
   CMBWS_TRY(ensure_dyn_smem((const void*)kern, LY::kSmem));
   // profiling arithmetic kinds: 3 TF32, 4 split TF32, 5 BF16, 6 split BF16
   ProfScope ps(PROF_LEG_SYNTH, s, 3 + SPLIT + 2 * BF, leg_work(g, NM));
@@ -1260,8 +1295,9 @@ static_assert(TcLayout<0, 0>::kUsed <= TcLayout<0, 0>::kSmem &&
                   TcLayout<1, 0>::kUsed <= TcLayout<1, 0>::kSmem &&
                   TcLayout<0, 1>::kUsed <= TcLayout<0, 1>::kSmem,
               "shared-memory layout exceeds the request");
-static_assert(TcLayout<0, 1>::kColD >= 32 && TcLayout<0, 1>::kColD + 16 <= TcLayout<0, 1>::kCols,
-              "BF16: two A stages of 16 columns, then 16 accumulator columns");
+static_assert(TcLayout<0, 0>::kColD >= 32 && TcLayout<0, 0>::kColD + 16 <= TcLayout<0, 0>::kCols &&
+                  TcLayout<1, 0>::kColD >= 64 && TcLayout<1, 0>::kColD + 16 <= TcLayout<1, 0>::kCols,
+              "an A buffer of 32 (hi + lo: 64) columns, then 16 accumulator columns");
 
 }  // namespace
 

@@ -110,6 +110,34 @@ def test_bounded_mbarrier_wait_runs_out_and_reports_a_timeout(prec):
         assert rel_err(got[k], osht.synthesis(o, 23, alm[k])) < bound
 
 
+@pytest.mark.parametrize("prec", [cw.CMBWS_BF16, cw.CMBWS_BF16X3])
+def test_tensor_core_adjoint_wait_runs_out_and_reports_a_timeout(prec):
+    """The same for the tensor-core adjoint (analysis): every CTA's bounded wait runs out, no
+    MMA is issued, the coefficients hold NaN and cmbws_device_status reports CMBWS_ERR_TIMEOUT;
+    the next call is correct."""
+    g = cw.cmbws_plan_grid(cw.CMBWS_GRID_HEALPIX, 8, 23)
+    o = og.healpix(8)
+    maps = np.random.default_rng(4).standard_normal((2, g.npix))
+    out = to_dev(np.zeros((2, 24 ** 2)))
+    cw.cmbws_device_status()
+    cw.cmbws_testing_stall_waits(100000)
+    try:
+        cw.cmbws_sht_analysis(g, prec, to_dev(maps), out, 2, 1)
+        with pytest.raises(cw.CmbwsError) as e:
+            cw.cmbws_device_status()
+        assert e.value.code == -7
+    finally:
+        cw.cmbws_testing_stall_waits(0)
+    assert np.isnan(to_host(out)).any()
+    cw.cmbws_device_status()
+    cw.cmbws_sht_analysis(g, prec, to_dev(maps), out, 2, 1)
+    cw.cmbws_device_status()
+    got = to_host(out)
+    bound = 1.5e-2 if prec == cw.CMBWS_BF16 else 4e-5
+    for k in range(2):
+        assert rel_err(got[k], osht.adjoint(o, 23, maps[k], weighted=True)) < bound
+
+
 def test_solver_reports_a_timed_out_device_wait_as_timeout():
     work = tiny_workload(15)
     m, inp = oracle_model(work)
