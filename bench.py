@@ -401,6 +401,64 @@ def batched_measure(nprob, tol, fmax=0.3, max_bottom=200):
                          "8 worker streams")}
 
 
+def variable_dust_measure(P, tol, inner_tol, cert, pc, iters_const):
+    """The benchmark model's variant with spatially variable dust mixing (Eq. Q): the dust pair
+    of every band (Nmix = 9) carries q(p) = q (1 + f(p)), f a seeded band-limited (l <= 8)
+    field rescaled to [0, 1] (max / min = 2), on the Nside-1024 band grid (L 3071 >= L_dust)
+    as the mixing grid.  Band maps d = P_var x_true + n; the step's solve (RHS, FP32 PCG with
+    the same preconditioner arithmetic, certified refinement)."""
+    import torch
+    import paper_1710_00621_gb300 as cw
+    dev = torch.device("cuda")
+    inp, grids = P["inp"], P["grids"]
+    lk = list(P["model"].lmax_comp)
+    nb, nc = len(grids), len(lk)
+    k = max(range(nc), key=lambda j: lk[j])      # the dust component (largest band-limit)
+    mg = max(grids, key=lambda g: g.lmax)        # the Nside-1024 band grid
+    z, ph = mg.pixel_coords()
+    f = skygen.smooth_field(z, ph, np.random.default_rng(skygen.SEED_BASE + 7))
+    q = np.asarray(inp["q"], dtype=np.float64)
+    maps = [[torch.as_tensor(q[nu, k] * (1.0 + f), device=dev) if j == k else None
+             for j in range(nc)] for nu in range(nb)]
+    mgs = [[mg if j == k else None for j in range(nc)] for _ in range(nb)]
+    m = cw.cmbws_model_create(lk, grids, inp["beams"], inp["cl"], P["ninv"], q, cw.CMBWS_FP32,
+                              mix_grids=mgs, mix_maps=maps)
+    try:
+        cw.cmbws_model_set_precond_prec(m, pc)
+        d = [torch.empty(g.npix, dtype=torch.float64, device=dev) for g in grids]
+        cw.cmbws_project(m, P["x_true"], d)
+        for nu in range(nb):
+            d[nu] += torch.as_tensor(inp["noise"][nu], device=dev)
+        b = torch.empty(m.nvec, dtype=torch.float64, device=dev)
+        x = torch.zeros(m.nvec, dtype=torch.float64, device=dev)
+        cp = cw.CMBWS_FP32X2 if cert == "fp32x2" else cw.CMBWS_FP64
+        res = {}
+        # M_PI, then the block-diagonal M_diag (the paper's comparison with variable dust maps)
+        for name, pcm in (("M_PI", 1), ("M_diag", 3)):
+            for _ in range(2):                      # the first solve allocates the workspaces
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                cw.cmbws_rhs(m, d, b)
+                x.zero_()
+                r = cw.cmbws_cg_solve(m, b, x, tol=tol, maxiter=3000, precond=pcm,
+                                      inner_tol=inner_tol, max_outer=30, cert_prec=cp, check=False,
+                                      timeout_s=120.0)
+                torch.cuda.synchronize()
+                ts = time.perf_counter() - t0
+            res[name] = {"s": round(ts, 4), "iters": r["iters"], "outer": r["outer"],
+                         "certified": r["status"] == 0 and r["rel_res"] <= tol,
+                         "rel_res": r["rel_res"], "n_sht": r["n_sht"]}
+        return {**res, "nsht_A": m.nsht_A, "nsht_M": m.nsht_M,
+                "iters_M_diag_over_M_PI": round(res["M_diag"]["iters"] / max(res["M_PI"]["iters"], 1), 2),
+                "time_M_diag_over_M_PI": round(res["M_diag"]["s"] / res["M_PI"]["s"], 2),
+                "iters_constant_mixing_M_PI": iters_const,
+                "workload": ("multires_fullsky_nside256-1024 with the dust pair of all 9 bands on "
+                             "q (1 + f), f a seeded l <= 8 field in [0, 1] (max/min 2, Nmix 9), "
+                             "mixing grid HEALPix Nside 1024 (L 3071); RHS + solve")}
+    finally:
+        m.close()
+
+
 def masked_cr_measure(tol=1e-6, scale=1, max_bottom=200):
     """Planck-shaped masked constrained realization at reduced resolution (skygen.masked_cr:
     4 components, 9 HEALPix bands at Nside 128/256, galactic band |b| < 20 deg and 200 disks
@@ -1027,6 +1085,12 @@ def main():
                 extras[key] = fn()
             except Exception as e:  # noqa: BLE001
                 extras[key] = {"error": f"{type(e).__name__}: {e}"[:300]}
+    variable = None
+    if not args.no_extras and args.prec == "fp32" and args.scale == 1:
+        try:
+            variable = variable_dust_measure(P, args.tol, args.inner_tol, cert, pc_main, out["iters"])
+        except Exception as e:  # noqa: BLE001 - reported in the line instead of losing it
+            variable = {"error": f"{type(e).__name__}: {e}"[:300]}
     masked_cr = None
     if not args.no_masked_cr and args.scale == 1:
         try:
@@ -1062,7 +1126,7 @@ def main():
                        "parallelism": f"replicas x{world}"},
             "solve": out, "fp64_plain": fp64, "fp32x2_plain": fp32x2,
             "tensor_core_solves": tc_solves, "batched": batched,
-            "masked_cr": masked_cr,
+            "masked_cr": masked_cr, "variable_dust": variable,
             "tiny": extras.get("tiny"), "differentiable": extras.get("differentiable"),
             "M_diag_comparison": mdiag,
             "cr_chain": crchain,
