@@ -62,7 +62,7 @@ def parse():
                     help="skip the per-precision synthesis time / error report")
     ap.add_argument("--inner-tol", type=float, default=1e-3,
                     help="relative residual reduction per refinement pass (FP32 solves)")
-    ap.add_argument("--with-batched", type=int, default=32, metavar="NPROB",
+    ap.add_argument("--with-batched", type=int, default=64, metavar="NPROB",
                     help="also time NPROB independent uneven masked problems (GL L 128..1024), "
                          "batched vs sequential, reported under 'batched'")
     ap.add_argument("--autotune", type=int, default=2, choices=[0, 1, 2],
