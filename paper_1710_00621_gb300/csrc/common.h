@@ -111,6 +111,27 @@ constexpr int kChunkDf = 4;  // l-chunk of the checkpointed double-float adjoint
 inline __host__ __device__ int64_t lm_off(int L, int m) {
   return (int64_t)m * (L + 1) - (int64_t)m * (m - 1) / 2;
 }
+
+// Thread -> (m, l) of a kernel over the triangle 0 <= m <= l <= L: grid row y holds the rows
+// m = y and m = L - y one after the other (L + 2 values of l together), so that no thread is
+// launched for the empty part of the triangle; false for the padding of the last CTA of a row.
+// Launch with tri_grid(L, threads per CTA).
+__device__ __forceinline__ bool tri_lm(int L, int& m, int& l) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y;
+  const int n0 = L - y + 1;  // length of row y
+  if (t < n0) {
+    m = y;
+    l = y + t;
+    return true;
+  }
+  const int m2 = L - y, t2 = t - n0;  // row L - y has y + 1 values of l
+  if (m2 == y || t2 > y) return false;
+  m = m2;
+  l = m2 + t2;
+  return true;
+}
+inline dim3 tri_grid(int L, int nt) { return dim3((unsigned)((L + 2 + nt - 1) / nt), (unsigned)(L / 2 + 1)); }
 inline __host__ __device__ int64_t nlm_of(int L) { return (int64_t)(L + 1) * (L + 2) / 2; }
 // offset of the m block in the packed CMBWS_ALM layout
 inline __host__ __device__ int64_t packed_off(int L, int m) {

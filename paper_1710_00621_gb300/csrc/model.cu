@@ -33,27 +33,31 @@ template <> struct V2<float> { using t = float2; };
 // ---- harmonic prologue: a_nu = c_lm * b_{nu,l} * sum_k q_{nu,k} x_k(l, m) ----
 template <typename T2>
 __global__ void k_mix_forward(HarmDev h, GroupDev gd, const double* __restrict__ x) {
-  const int m = blockIdx.y;
-  const int l = m + blockIdx.x * blockDim.x + threadIdx.x;
   const int L = gd.L;
-  if (l > L) return;
+  int m, l;
+  if (!tri_lm(L, m, l)) return;
   const int64_t i = lm_off(L, m) + (l - m);
   const double cc = gd.c[i];
+  // per-component values in registers: loops over kMaxComp unrolled (static indices), cut
+  // at ncomp
   double xr[kMaxComp], xi[kMaxComp];
-  for (int k = 0; k < h.ncomp; ++k) {
+#pragma unroll
+  for (int k = 0; k < kMaxComp; ++k) {
+    xr[k] = xi[k] = 0.0;
+    if (k >= h.ncomp) continue;
     const int Lk = h.compL[k];
     if (l <= Lk) {
       const double* xk = x + h.compOff[k] + packed_off(Lk, m);
       xr[k] = xk[l - m];
       xi[k] = m > 0 ? xk[(Lk - m + 1) + (l - m)] : 0.0;
-    } else {
-      xr[k] = xi[k] = 0.0;
     }
   }
   for (int j = 0; j < gd.nmaps; ++j) {
     const int nu = gd.bands[j];
     double ar = 0.0, ai = 0.0;
-    for (int k = 0; k < h.ncomp; ++k) {
+#pragma unroll
+    for (int k = 0; k < kMaxComp; ++k) {
+      if (k >= h.ncomp) break;
       const PairDev& pd = h.pairs[nu * h.ncomp + k];
       if (pd.var) {
         // Q~ x_k from the mixing chain (its output band-limit covers l <= L_nu)
@@ -77,10 +81,9 @@ __global__ void k_mix_forward(HarmDev h, GroupDev gd, const double* __restrict__
 // ---- harmonic epilogue: y_k = C_k^-1 x_k + sum_nu q_{nu,k} b_{nu,l} u_nu ----
 __global__ void k_mix_adjoint(HarmDev h, BandDev bd, int k, const double* __restrict__ x,
                               double* __restrict__ y) {
-  const int m = blockIdx.y;
   const int Lk = h.compL[k];
-  const int l = m + blockIdx.x * blockDim.x + threadIdx.x;
-  if (l > Lk) return;
+  int m, l;
+  if (!tri_lm(Lk, m, l)) return;
   double yr = 0.0, yi = 0.0;
   for (int nu = 0; nu < h.nobs; ++nu) {
     if (!((h.own >> nu) & 1)) continue;  // another shard's band
@@ -194,19 +197,20 @@ __global__ void k_mixq(const double* __restrict__ q, const int64_t* __restrict__
 template <typename T2>
 __global__ void k_pinv_T(HarmDev h, BandDev bd, const double* __restrict__ r,
                          double* __restrict__ tp, int Ltop) {
-  const int m = blockIdx.y;
-  const int l = m + blockIdx.x * blockDim.x + threadIdx.x;
-  if (l > Ltop) return;
+  int m, l;
+  if (!tri_lm(Ltop, m, l)) return;
   const int nc = h.ncomp, nr = h.nobs + h.ncomp;
+  // per-component values in registers (unrolled over kMaxComp, cut at nc)
   double rr[kMaxComp], ri[kMaxComp];
-  for (int k = 0; k < nc; ++k) {
+#pragma unroll
+  for (int k = 0; k < kMaxComp; ++k) {
+    rr[k] = ri[k] = 0.0;
+    if (k >= nc) continue;
     const int Lk = h.compL[k];
     if (l <= Lk) {
       const double* rk = r + h.compOff[k] + packed_off(Lk, m);
       rr[k] = rk[l - m];
       ri[k] = m > 0 ? rk[(Lk - m + 1) + (l - m)] : 0.0;
-    } else {
-      rr[k] = ri[k] = 0.0;
     }
   }
   const double* U = h.Up + (int64_t)min(l, h.Lup) * nc * nr;  // U^+[c][j]
@@ -216,7 +220,9 @@ __global__ void k_pinv_T(HarmDev h, BandDev bd, const double* __restrict__ r,
     if (l > Ln) continue;
     double tr = 0.0, ti = 0.0;
     if (inU) {
-      for (int c = 0; c < nc; ++c) {
+#pragma unroll
+      for (int c = 0; c < kMaxComp; ++c) {
+        if (c >= nc) break;
         const double u = U[c * nr + nu];
         tr += u * rr[c];
         ti += u * ri[c];
@@ -234,7 +240,9 @@ __global__ void k_pinv_T(HarmDev h, BandDev bd, const double* __restrict__ r,
     if (l > Lk) continue;
     double tr = 0.0, ti = 0.0;
     if (inU) {
-      for (int c = 0; c < nc; ++c) {
+#pragma unroll
+      for (int c = 0; c < kMaxComp; ++c) {
+        if (c >= nc) break;
         const double u = U[c * nr + h.nobs + k];
         tr += u * rr[c];
         ti += u * ri[c];
@@ -249,18 +257,21 @@ __global__ void k_pinv_T(HarmDev h, BandDev bd, const double* __restrict__ r,
 // ---- z = U^+ t' ----
 __global__ void k_pinv(HarmDev h, BandDev bd, const double* __restrict__ tp, double* __restrict__ z,
                        int Lcomp) {
-  const int m = blockIdx.y;
-  const int l = m + blockIdx.x * blockDim.x + threadIdx.x;
-  if (l > Lcomp) return;
+  int m, l;
+  if (!tri_lm(Lcomp, m, l)) return;
   const int nc = h.ncomp, nr = h.nobs + h.ncomp;
   const double* U = h.Up + (int64_t)min(l, h.Lup) * nc * nr;
+  // per-component sums in registers (unrolled over kMaxComp, cut at nc)
   double zr[kMaxComp], zi[kMaxComp];
-  for (int c = 0; c < nc; ++c) zr[c] = zi[c] = 0.0;
+#pragma unroll
+  for (int c = 0; c < kMaxComp; ++c) zr[c] = zi[c] = 0.0;
   for (int nu = 0; nu < h.nobs; ++nu) {
     const int Ln = bd.L[nu];
     if (l > Ln || !((h.own >> nu) & 1)) continue;
     const double2 u = bd.out[nu][lm_off(Ln, m) + (l - m)];
-    for (int c = 0; c < nc; ++c) {
+#pragma unroll
+    for (int c = 0; c < kMaxComp; ++c) {
+      if (c >= nc) break;
       const double w = U[c * nr + nu];
       zr[c] += w * u.x;
       zi[c] += w * u.y;
@@ -272,13 +283,17 @@ __global__ void k_pinv(HarmDev h, BandDev bd, const double* __restrict__ tp, dou
     const int64_t base = h.compOff[k] + packed_off(Lk, m);
     const double tr = tp[base + (l - m)];
     const double ti = m > 0 ? tp[base + (Lk - m + 1) + (l - m)] : 0.0;
-    for (int c = 0; c < nc; ++c) {
+#pragma unroll
+    for (int c = 0; c < kMaxComp; ++c) {
+      if (c >= nc) break;
       const double w = U[c * nr + h.nobs + k];
       zr[c] += w * tr;
       zi[c] += w * ti;
     }
   }
-  for (int c = 0; c < nc; ++c) {
+#pragma unroll
+  for (int c = 0; c < kMaxComp; ++c) {
+    if (c >= nc) break;
     const int Lc = h.compL[c];
     if (l > Lc) continue;
     const int64_t base = h.compOff[c] + packed_off(Lc, m);
@@ -343,10 +358,9 @@ __global__ void k_rhs_pixels(const double* __restrict__ d, const double* __restr
 
 __global__ void k_add_scaled_prior(HarmDev h, const double* __restrict__ w2, double* __restrict__ b,
                                    int k) {
-  const int m = blockIdx.y;
   const int Lk = h.compL[k];
-  const int l = m + blockIdx.x * blockDim.x + threadIdx.x;
-  if (l > Lk || !h.prior_on) return;  // the prior terms belong to one shard
+  int m, l;
+  if (!tri_lm(Lk, m, l) || !h.prior_on) return;  // the prior terms belong to one shard
   const int64_t base = h.compOff[k] + packed_off(Lk, m);
   const double s = h.cisq[h.clOff[k] + l];
   b[base + (l - m)] += s * w2[base + (l - m)];
@@ -569,7 +583,7 @@ int Model::mix_forward(Group& G, int prec, const double* x, cudaStream_t s) {
   gd.c = G.grid->c64.as<double>();
   gd.alm = G.alm.p;
   gd.nlm = nlm_of(gd.L);
-  dim3 grd((gd.L + 1 + 127) / 128, gd.L + 1);
+  const dim3 grd = tri_grid(gd.L, 128);
   ProfScope ps(PROF_HARM, s, is_f32(prec) ? 0 : 1);
   if (!is_f32(prec)) k_mix_forward<double2><<<grd, 128, 0, s>>>(h, gd, x);
   else k_mix_forward<float2><<<grd, 128, 0, s>>>(h, gd, x);
@@ -604,7 +618,7 @@ int Model::apply_A(const double* x, double* y, int prec, cudaStream_t s) {
   if (nmix) CMBWS_TRY(mixvar_adjoint(prec, s));
   const BandDev bd = bands_dev(prec);
   for (int k = 0; k < ncomp; ++k) {
-    dim3 grd((Lk[k] + 1 + 127) / 128, Lk[k] + 1);
+    const dim3 grd = tri_grid(Lk[k], 128);
     ProfScope ps(PROF_HARM, s, is_f32(prec) ? 0 : 1);
     k_mix_adjoint<<<grd, 128, 0, s>>>(h, bd, k, x, y);
     CMBWS_LAUNCH_CHECK();
@@ -629,7 +643,7 @@ int Model::apply_precond_merged(const double* r, double* z, int prec, cudaStream
     bd.alm[row] = (char*)G.alm.p + (size_t)j * nlm * 2 * prec_size(prec);
   }
   {
-    dim3 grd((Lall + 1 + 127) / 128, Lall + 1);
+    const dim3 grd = tri_grid(Lall, 128);
     ProfScope ps(PROF_HARM, s, is_f32(prec) ? 0 : 1);
     if (!is_f32(prec)) k_pinv_T<double2><<<grd, 128, 0, s>>>(h, bd, r, tprior.as<double>(), Lall);
     else k_pinv_T<float2><<<grd, 128, 0, s>>>(h, bd, r, tprior.as<double>(), Lall);
@@ -645,7 +659,7 @@ int Model::apply_precond_merged(const double* r, double* z, int prec, cudaStream
     CMBWS_TRY(legendre_adjoint(g, prec, G.nmaps, G.F.p, part.p, part.bytes, G.out.as<double>(), s));
   }
   {
-    dim3 grd((Lcomp + 1 + 127) / 128, Lcomp + 1);
+    const dim3 grd = tri_grid(Lcomp, 128);
     ProfScope ps(PROF_HARM, s, is_f32(prec) ? 0 : 1);
     k_pinv<<<grd, 128, 0, s>>>(h, bd, tprior.as<double>(), z, Lcomp);
     CMBWS_LAUNCH_CHECK();
@@ -659,7 +673,7 @@ int Model::apply_precond(const double* r, double* z, int prec, cudaStream_t s) {
   const HarmDev h = harm();
   const BandDev bd = bands_dev(prec);
   {
-    dim3 grd((Lall + 1 + 127) / 128, Lall + 1);
+    const dim3 grd = tri_grid(Lall, 128);
     ProfScope ps(PROF_HARM, s, is_f32(prec) ? 0 : 1);
     if (!is_f32(prec)) k_pinv_T<double2><<<grd, 128, 0, s>>>(h, bd, r, tprior.as<double>(), Lall);
     else k_pinv_T<float2><<<grd, 128, 0, s>>>(h, bd, r, tprior.as<double>(), Lall);
@@ -668,7 +682,7 @@ int Model::apply_precond(const double* r, double* z, int prec, cudaStream_t s) {
   for (Group& G : groups)
     if (group_owned(G)) CMBWS_TRY(group_chain(G, prec, 1, s));
   {
-    dim3 grd((Lcomp + 1 + 127) / 128, Lcomp + 1);
+    const dim3 grd = tri_grid(Lcomp, 128);
     ProfScope ps(PROF_HARM, s, is_f32(prec) ? 0 : 1);
     k_pinv<<<grd, 128, 0, s>>>(h, bd, tprior.as<double>(), z, Lcomp);
     CMBWS_LAUNCH_CHECK();
@@ -702,7 +716,7 @@ int Model::rhs(const double* const* d, const double* const* w1, const double* w2
   if (nmix) CMBWS_TRY(mixvar_adjoint(ap, s));
   const BandDev bd = bands_dev(ap);
   for (int k = 0; k < ncomp; ++k) {
-    dim3 grd((Lk[k] + 1 + 127) / 128, Lk[k] + 1);
+    const dim3 grd = tri_grid(Lk[k], 128);
     ProfScope ps(PROF_HARM, s, 1);
     k_mix_adjoint<<<grd, 128, 0, s>>>(h, bd, k, nullptr, b);
     CMBWS_LAUNCH_CHECK();
