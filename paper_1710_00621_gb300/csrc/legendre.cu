@@ -613,9 +613,9 @@ int adj_nblk(const Grid& g) {
 
 template <int NM>
 int launch_adj_ck(const Grid& g, const float* eo, double* out, cudaStream_t s) {
-  // one warp per CTA: the warps are independent tasks (no CTA barrier), and at 130 registers
-  // single-warp CTAs pack 15 warps per SM where 4-warp CTAs pack 12 (3.29 against 3.77 ms per
-  // Nside-1024 launch of 3 maps)
+  // one warp per CTA: the warps are independent tasks (no CTA barrier), so an SM holds as
+  // many as its registers allow (16 at 120 registers) instead of whole 4-warp CTAs (12 at 130):
+  // 3.29 against 3.77 ms per Nside-1024 launch of 3 maps
   constexpr int NT = 32, PT = 16;
   const int L = g.lmax;
   const int64_t nlm = nlm_of(L);
