@@ -585,7 +585,7 @@ size_t smem_bytes(const Grid& g) {
 // Threads per CTA: a grid with large transforms (>= 4096 entries, e.g. the Bluestein buffers
 // of the polar rings from Nside 512 up) gets 256 threads, so that the butterfly passes of one
 // ring have twice the warps to hide shared-memory latency with the same buffer per CTA; the
-// others 128.
+// others 128; 16-byte values with 8192-entry buffers (one CTA per SM) 512.
 template <typename T, int MODE>
 int launch(const Grid& g, int nmaps, void* F, double* map_out, const double* map_in, int weighted,
            const void* const* pix, void* eo, int eo_nm, cudaStream_t s);
@@ -633,6 +633,11 @@ int launch_nt(const Grid& g, int nmaps, void* F, double* map_out, const double* 
 template <typename T, int MODE>
 int launch(const Grid& g, int nmaps, void* F, double* map_out, const double* map_in, int weighted,
            const void* const* pix, void* eo, int eo_nm, cudaStream_t s) {
+  // 16-byte values (double-float, FP64) with 8192-entry buffers: about 140 KB per CTA, one CTA
+  // per SM, so that CTA gets 512 threads (16 warps instead of 8)
+  if constexpr (!std::is_same<T, float>::value)
+    if (g.nmax2 >= 8192)
+      return launch_nt<T, MODE, 512>(g, nmaps, F, map_out, map_in, weighted, pix, eo, eo_nm, s);
   if (g.nmax2 >= 4096)
     return launch_nt<T, MODE, 256>(g, nmaps, F, map_out, map_in, weighted, pix, eo, eo_nm, s);
   return launch_nt<T, MODE, 128>(g, nmaps, F, map_out, map_in, weighted, pix, eo, eo_nm, s);
