@@ -290,7 +290,7 @@ struct PixPtrs {
 
 // NT threads per CTA; the register cap keeps three CTAs of 256 threads (six of 128) resident
 // per SM in FP32 and double-float, which is what the transform buffer of the largest rings
-// allows.
+// allows (double-float and FP64 grids with 8192-entry buffers: one CTA of 512).
 //
 // Each ring pair's DFTs, in terms of the plan (n pixels; Bluestein plans convolve over n2):
 // * power of two: the inverse DFT is a DIT transform whose input (the folded spectrum) is
